@@ -1,0 +1,147 @@
+"""Seeded T-doped random Clifford brickwork circuits (the paper's benchmark family, Sec. 4).
+
+The paper's benchmark circuits interleave random Cliffords with T gates (Sec. 4, Fig. 4).
+Here a circuit on ``n`` qudits has ``layers`` brickwork layers of random two-qudit Cliffords
+and ``t`` diagonal non-Clifford gates placed between layers.
+
+Layout (all deterministic in the seed):
+
+* PRNG: SplitMix64, one stream per circuit, seeded with ``seed``.
+* Layer ``l`` acts on the pairs ``(i, i+1)`` with ``i = l (mod 2)`` and ``i+1 < n``
+  (open boundary), in increasing ``i``.  For each pair, in this order: one uniform index
+  into the lexicographically sorted list of the |Sp(4, F_d)| symplectic 4x4 matrices, then
+  four uniform shift exponents ``(a0, b0, a1, b1)`` in Z_d.  The gate these name is
+  ``X^a0 Z^b0 (x) X^a1 Z^b1`` times the standard-phase Clifford of the symplectic matrix.
+* Non-Clifford gate ``k = 0..t-1`` follows layer ``ceil((k+1) * layers / t) - 1``; its
+  site is drawn uniformly right after that layer's gates, in increasing ``k``.
+
+The module only draws integers and places gates.  It never interprets a symplectic index.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Tuple, Union
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea, Flood 2014): 64-bit state, golden-ratio increment."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform_int(self, n: int) -> int:
+        """Uniform integer in [0, n) by rejection (no modulo bias)."""
+        if n <= 0:
+            raise ValueError("n must be positive")
+        limit = (1 << 64) - ((1 << 64) % n)
+        while True:
+            z = self.next_u64()
+            if z < limit:
+                return z % n
+
+    def uniform_float(self) -> float:
+        """Uniform double in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+
+def sp4_order(d: int) -> int:
+    """|Sp(4, F_d)| = d^4 (d^2 - 1)(d^4 - 1): 720 for d = 2, 51840 for d = 3."""
+    return d ** 4 * (d ** 2 - 1) * (d ** 4 - 1)
+
+
+def t_gate_phases(d: int) -> Tuple[float, ...]:
+    """Phases (radians) of the qudit T gate used by the benchmarks.
+
+    d = 2: diag(1, e^{i pi/4}) (Sec. 2.3.2).  d = 3: diag(1, e^{2 pi i/9}, e^{-2 pi i/9}), the
+    third-level-of-the-hierarchy qutrit T; the matrix printed in Sec. 2.3.2 is a different
+    diagonal and can be passed explicitly instead.
+    """
+    if d == 2:
+        return (0.0, math.pi / 4)
+    if d == 3:
+        return (0.0, 2 * math.pi / 9, -2 * math.pi / 9)
+    raise ValueError("d must be 2 or 3")
+
+
+@dataclass(frozen=True)
+class Clifford2:
+    """Random two-qudit Clifford on (q0, q0+1): symplectic index + Weyl shift (a0, b0, a1, b1)."""
+    q0: int
+    q1: int
+    sp_index: int
+    shift: Tuple[int, int, int, int]
+
+
+@dataclass(frozen=True)
+class Diag:
+    """Diagonal non-Clifford gate diag(e^{i phases[j]}) on one site."""
+    site: int
+    phases: Tuple[float, ...]
+    param: int = -1  # index of the parameter it carries, or -1
+
+
+Gate = Union[Clifford2, Diag]
+
+
+def _t_after_layer(k: int, layers: int, t: int) -> int:
+    return ((k + 1) * layers + t - 1) // t - 1
+
+
+def brickwork_circuit(n: int, d: int, layers: int, t: int, seed: int,
+                      phases: Tuple[float, ...] = None) -> List[Gate]:
+    """T-doped random Clifford brickwork circuit; see the module docstring for the layout."""
+    if n < 2:
+        raise ValueError("need n >= 2")
+    if phases is None:
+        phases = t_gate_phases(d)
+    rng = SplitMix64(seed)
+    order = sp4_order(d)
+    after = [[] for _ in range(layers)]
+    for k in range(t):
+        after[_t_after_layer(k, layers, t)].append(k)
+    out: List[Gate] = []
+    for layer in range(layers):
+        for i in range(layer % 2, n - 1, 2):
+            idx = rng.uniform_int(order)
+            shift = tuple(rng.uniform_int(d) for _ in range(4))
+            out.append(Clifford2(i, i + 1, idx, shift))
+        for _k in after[layer]:
+            out.append(Diag(rng.uniform_int(n), tuple(phases)))
+    return out
+
+
+def param_phase_circuit(n: int, d: int, layers: int, ngates: int, seed: int) -> Tuple[List[Gate], List[float]]:
+    """Brickwork circuit with ``ngates`` parametrised gates diag(1, e^{i th}, e^{-i th}) (d = 3)
+    or diag(1, e^{i th}) (d = 2), th ~ U(0, 2 pi) drawn from the same stream.
+
+    Returns the gate list and the parameter values; gate ``k`` carries ``param = k``.
+    """
+    rng = SplitMix64(seed)
+    order = sp4_order(d)
+    after = [[] for _ in range(layers)]
+    for k in range(ngates):
+        after[_t_after_layer(k, layers, ngates)].append(k)
+    out: List[Gate] = []
+    thetas: List[float] = []
+    for layer in range(layers):
+        for i in range(layer % 2, n - 1, 2):
+            idx = rng.uniform_int(order)
+            shift = tuple(rng.uniform_int(d) for _ in range(4))
+            out.append(Clifford2(i, i + 1, idx, shift))
+        for k in after[layer]:
+            site = rng.uniform_int(n)
+            th = 2 * math.pi * rng.uniform_float()
+            thetas.append(th)
+            ph = (0.0, th) if d == 2 else (0.0, th, -th)
+            out.append(Diag(site, ph, k))
+    return out, thetas
