@@ -1,0 +1,312 @@
+"""Benchmark: GCAMPS T-gates/s on seeded T-doped random Clifford brickwork circuits.
+
+Workload (one step = one pass of the whole hot path over one batch):
+  qubit and qutrit circuits (d = 2 and d = 3), n = 32 qudits, 24 brickwork layers of random
+  two-qudit Cliffords, 32 T gates (each followed by disentangling), chi_max = 256, SVD cutoff
+  1e-12, complex128; seeds 1..8 for each d (16 circuits per step, one CTA each).  Every step starts
+  from |0...0> with C = I (reset kernel) and runs the full gate list in one engine launch per d.
+
+value  : T gates of all circuits / device time of the timed steps (CUDA events on the engine's
+         stream; L2 flushed with a 512 MiB write before every step, outside the event pair).
+e2e    : same metric through the C ABI with the gate list in pinned host memory, copied to the
+         device inside the timed region, and per-circuit counters read back every step.
+Multi-GPU: circuits are independent; each rank runs the same per-rank batch with its own seeds
+(weak scaling, no collective on the data path).
+
+--impl reference runs the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N, LAYERS, T, CHI, CUTOFF = 32, 24, 32, 256, 1e-12
+SEEDS_PER_D = 8
+WORKLOAD = "gcamps-brickwork-n32-L24-T32-chi256-d2+d3-8seeds"
+METRIC = "T-gates/s"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the engine is FP64-ALU bound
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_ops(G, d, rank):
+    from synth import brickwork_circuit
+    import numpy as np
+    ops, begin = [], [0]
+    for s in range(SEEDS_PER_D):
+        seed = 1 + s + rank * SEEDS_PER_D
+        o = G.ops_from_gates(brickwork_circuit(N, d, LAYERS, T, seed), d)
+        ops.append(o)
+        begin.append(begin[-1] + len(o))
+    return np.concatenate(ops), np.array(begin, dtype=np.int32)
+
+
+def cpu_oracle_sample(budget_s: float = 20.0):
+    """Time the oracle (as it stands) on whole benchmark circuits, qubit then qutrit seeds in
+    turn, until ~budget_s of CPU time; single thread."""
+    from synth import brickwork_circuit
+    from oracle.gcamps import GCAMPS
+    t_gates = 0
+    circuits = []
+    t0 = time.perf_counter()
+    seed = 1
+    while True:
+        for d in (2, 3):
+            g = GCAMPS(N, d, chi_max=CHI, cutoff=CUTOFF)
+            for gt in brickwork_circuit(N, d, LAYERS, T, seed):
+                g.apply_gate(gt)
+                if not hasattr(gt, "sp_index"):
+                    g.disentangle()
+                    t_gates += 1
+            circuits.append(f"d{d}s{seed}")
+            if time.perf_counter() - t0 > budget_s:
+                el = time.perf_counter() - t0
+                return t_gates / el, el, circuits
+        seed += 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    per_step = []
+    tg_total = 0
+    samples = []
+    for i in range(args.warmup + args.steps):
+        rate, el, circ = cpu_oracle_sample(budget_s=args.ref_step_s)
+        if i >= args.warmup:
+            per_step.append(el)
+            tg_total += rate * el
+            samples.extend(circ)
+    el = sum(per_step)
+    value = tg_total / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "whole circuits d=2/d=3 alternating, seeds from 1"},
+        "cpu_baseline": {"value": value, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(samples)} whole circuits ({','.join(samples[:6])}...), ~{args.ref_step_s}s per step"},
+        "e2e": {"value": value, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+
+    stream = torch.cuda.Stream()
+    sims, ops_host, ops_dev, begin_dev = {}, {}, {}, {}
+    for d in (2, 3):
+        sims[d] = G.Simulator(N, d, chi_max=CHI, cutoff=CUTOFF, batch=SEEDS_PER_D, stream=stream)
+        o, b = workload_ops(G, d, rank)
+        ops_host[d] = (o, b)
+        ops_dev[d] = torch.from_numpy(o.view(np.uint8)).to(f"cuda:{local}")
+        begin_dev[d] = torch.from_numpy(b).to(f"cuda:{local}")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    lib = G._native.load()
+    import ctypes as C
+
+    def launch_all(events=None):
+        """One step: back to |0...0> and C = I, then the full gate list of every circuit (one
+        engine launch per d), all enqueued on `stream`.  `events`: optional list of
+        (start, end) CUDA-event pairs recorded around each engine launch."""
+        for i, d in enumerate((2, 3)):
+            s = sims[d]
+            rc = lib.gcamps_reset(s._h)
+            if events is not None:
+                events[i][0].record(stream)
+            if rc == 0:
+                rc = lib.gcamps_run_device(s._h, C.c_void_p(ops_dev[d].data_ptr()),
+                                           C.c_void_p(begin_dev[d].data_ptr()))
+            if events is not None:
+                events[i][1].record(stream)
+            if rc:
+                raise RuntimeError(lib.gcamps_last_error(s._h).decode())
+
+    # warm-up (also checks status)
+    for _ in range(args.warmup):
+        launch_all()
+        stream.synchronize()
+    for d in (2, 3):
+        sims[d].sync()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, engine_times = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        ev0, ev1 = mk(), mk()
+        inner = [(mk(), mk()), (mk(), mk())]
+        ev0.record(stream)
+        launch_all(inner)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+        engine_times.extend(a.elapsed_time(b) / 1e3 for a, b in inner)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([sum(times)], device=f"cuda:{local}", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_time = float(tt.item())
+    else:
+        total_time = sum(times)
+    stats = {d: [sims[d].stats(c) for c in range(SEEDS_PER_D)] for d in (2, 3)}
+    for d in (2, 3):
+        for st in stats[d]:
+            if st["status"] != 0:
+                raise RuntimeError(f"device status {st['status']}")
+    tg_per_step = sum(st["t_gates"] for d in (2, 3) for st in stats[d])
+    cand_per_step = sum(st["candidates_scored"] for d in (2, 3) for st in stats[d])
+    value = tg_per_step * args.steps * world / total_time
+    cand_rate = cand_per_step * args.steps * world / total_time
+    flops_per_launch = sum(st["scoring_flops"] for d in (2, 3) for st in stats[d]) / 2.0
+    launch_s = sum(engine_times) / len(engine_times)
+    achieved = flops_per_launch / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_run (engine, one launch per d)", "flops_per_launch": flops_per_launch,
+                "launch_ms": 1e3 * launch_s, "peak_source": "FP64 nominal, profiling recipe table"}
+
+    # end to end: host gate lists, copies and readback inside the timed region
+    torch.cuda.synchronize()
+    e2e_times = []
+    h2d = sum(ops_host[d][0].nbytes + ops_host[d][1].nbytes for d in (2, 3))
+    d2h = 0
+    for _ in range(max(2, args.steps)):
+        t0 = time.perf_counter()
+        for d in (2, 3):
+            sims[d].reset()
+            sims[d].run(*ops_host[d])
+        res = []
+        for d in (2, 3):
+            for c in range(SEEDS_PER_D):
+                res.append(sims[d].bond_dims(c))
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = sum(len(r) * 4 for r in res)
+    e2e_value = tg_per_step * world / (sum(e2e_times) / len(e2e_times))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "layers": LAYERS, "t_gates": T, "chi_max": CHI,
+                   "cutoff": CUTOFF, "d": [2, 3], "circuits_per_rank": 2 * SEEDS_PER_D,
+                   "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}"},
+        "candidates_per_s": cand_rate,
+        "e2e": {"value": e2e_value, "unit": "T-gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * 2 * args.steps,
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el, circ = cpu_oracle_sample(budget_s=15.0)
+        line["cpu_baseline"] = {"value": rate, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"whole circuits {','.join(circ)} ({el:.1f} s, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for d in (2, 3):
+        sims[d].close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

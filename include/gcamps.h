@@ -1,0 +1,184 @@
+/*
+ * gcamps.h -- C ABI of libgcamps, a GB300 (sm_103a) implementation of the per-non-Clifford-gate
+ * step of GCAMPS (Generalised Clifford Augmented Matrix Product States, arxiv 2511.06672).
+ *
+ * The state is psi = C |MPS> (Sec. 3): C is a Clifford kept as a mod-d stabilizer tableau
+ * (Sec. 2.3), |MPS> a matrix product state (Sec. 2.4, Eq. mps).  Everything lives in device
+ * memory owned by the handle; every step of a call runs in CUDA kernels of this library.
+ *
+ * Conventions (all calls):
+ *   - d is 2 or 3 (Gaussian elimination over Z_d needs a field, Sec. 2.3.1; d > 3 is out of
+ *     scope as in Sec. 3.1).  omega = exp(2 pi i/d), tau = exp(i pi/d).
+ *   - A Weyl operator with phase is tau^r (x)_j X_j^{x_j} Z_j^{z_j}, r mod 2d (Sec. 2.3: Y = XZ
+ *     for odd d, tau XZ for even d).
+ *   - Qudit 0 is the most significant digit of a basis index: index = sum_j s_j d^{n-1-j}.
+ *   - A Clifford on qudits (q0, q1) is given by the images of X_q0, Z_q0, X_q1, Z_q1 under
+ *     conjugation U g U^dag: img[5k .. 5k+4] = (x_q0, z_q0, x_q1, z_q1, r) for generator k.
+ *     One-qudit Clifford (q1 = -1): img[3k .. 3k+2] = (x, z, r), k = 0 (X), 1 (Z).
+ *     The images must be symplectic and have order d (r even for odd d; for d = 2 each image
+ *     Hermitian); otherwise the call returns GCAMPS_EINVAL and changes nothing.
+ *
+ * Ownership: input arrays are caller-owned host memory, read during the call only.  Output
+ * arrays are caller-owned host memory written before the call returns.  A handle is used by
+ * one host thread at a time and runs all its work on one CUDA stream (opts.cuda_stream, or a
+ * stream the handle creates).
+ *
+ * Errors: every int-returning call returns 0 (GCAMPS_OK) or a GCAMPS_E* code; the message is
+ * available from gcamps_last_error.  Calls that only enqueue device work (apply_*, disentangle,
+ * run) are asynchronous: a device-side failure they cause (GCAMPS_ENOCONV, an iteration cap hit
+ * inside a kernel, or GCAMPS_ECHI) is reported by the next call that synchronises
+ * (gcamps_sync and every getter).  After EINVAL or ENOCONV the handle stays valid.
+ */
+#ifndef GCAMPS_H
+#define GCAMPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCAMPS_OK 0
+#define GCAMPS_EINVAL 1  /* bad argument, non-symplectic images, unsupported d       */
+#define GCAMPS_ENOMEM 2  /* device or host allocation failed                         */
+#define GCAMPS_ECUDA 3   /* a CUDA runtime call failed                                */
+#define GCAMPS_ENOCONV 4 /* a device iteration (Jacobi SVD, eigenvalues) hit its cap  */
+#define GCAMPS_ECHI 5    /* chi_max bound while discarding weight above strict_weight */
+
+typedef struct gcamps gcamps_t;
+
+/* Run-time options (defaults from gcamps_default_opts). */
+typedef struct {
+  double cutoff;       /* keep singular values s_i > cutoff * s_0 (Sec. 2.4; default 1e-12)   */
+  int max_sweeps;      /* disentangling sweeps per call (default 8)                           */
+  int score_kind;      /* 0 = von Neumann entropy of the Schmidt spectrum (only kind now)      */
+  int precision;       /* 0 = FP64 everywhere (only mode now)                                  */
+  double tie_tol;      /* accept Q only if S(Q) < S(I) - tie_tol; ties -> lowest index (1e-10) */
+  double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
+  void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
+} gcamps_opts;
+
+/* Per-circuit counters since creation (or gcamps_reset). */
+typedef struct {
+  int64_t t_gates;            /* non-Clifford gates applied                                 */
+  int64_t clifford_gates;     /* Clifford gates applied to the tableau                      */
+  int64_t bonds_visited;      /* disentangler bond visits                                   */
+  int64_t candidates_scored;  /* (bond, class) entanglement scores evaluated                */
+  int64_t accepted;           /* disentanglers applied                                      */
+  int64_t sweeps;             /* disentangling sweeps                                       */
+  int32_t max_chi;            /* largest bond dimension seen after any truncation           */
+  int32_t status;             /* sticky device status: 0 or a GCAMPS_E* code                */
+  double discarded_weight;    /* sum of discarded s_i^2 over all truncations                */
+  double scoring_flops;       /* algorithmic FP64 flops of candidate scoring (see below)    */
+} gcamps_stats;
+/* scoring_flops counts, per scored class at a bond with R = chi_l d rows and C = d chi_r
+ * columns (m = min(R, C), M = max(R, C)): 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram)
+ * + (16/3) m^3 (Householder tridiagonalisation); the eigenvalue iteration is not counted. */
+
+/* One operation of a gate list (gcamps_run).  kind: */
+#define GCAMPS_OP_CLIFFORD 1     /* q0, q1 (-1 for one qudit), img as for apply_clifford   */
+#define GCAMPS_OP_NONCLIFFORD 2  /* q0 = site, phases[0..d-1]                             */
+#define GCAMPS_OP_DISENTANGLE 3  /* disentangle the span of the last non-Clifford gate     */
+typedef struct {
+  int32_t kind;
+  int32_t q0, q1;
+  int32_t img[20];
+  int32_t pad;
+  double phases[4];
+} gcamps_op;
+
+void gcamps_default_opts(gcamps_opts* o);
+
+/* Number of two-qudit disentangler classes searched per bond: d^2 (d^2 + 1), i.e. 20 for d = 2
+ * and 90 for d = 3 (Sec. 3).  Returns -1 for unsupported d. */
+int gcamps_num_candidates(int d);
+
+/* Images (img[20], layout as above) of the two-qudit Clifford  W(shift) U_S  where S is the
+ * sp_index-th element (0-based) of Sp(4, F_d) in lexicographic order of its row-major entries
+ * (column k = exponents of the image of generator k in coordinates (x_q0, z_q0, x_q1, z_q1)),
+ * U_S maps each generator to the standard-phase Weyl operator of its column (phase tau^0 for
+ * odd d, tau^{x_q0 z_q0 + x_q1 z_q1} for d = 2), and W(shift) = X^s0 Z^s1 (x) X^s2 Z^s3 acts after
+ * it.  This is how the seeded benchmark circuits name their gates.  EINVAL on bad arguments. */
+int gcamps_sp4_images(int d, int64_t sp_index, const int32_t* shift, int32_t* img);
+
+/* Host-only (no GPU needed): class k (0 <= k < gcamps_num_candidates(d)) of the disentangler set.
+ * img[20]: generator images of its representative (class 0 = identity; the others are the
+ * lexicographically smallest symplectic matrix of their class {(L_0 (+) L_1) S}, standard phases);
+ * u: its d^2 x d^2 unitary, row-major, interleaved (re, im), 2 d^4 doubles (may be NULL). */
+int gcamps_candidate(int d, int k, int32_t* img, double* u);
+
+/* Create a simulator of `batch` independent circuits of n qudits (n >= 2), local dimension d,
+ * bond dimension at most chi_max, all in |0...0> with C = I.  Device memory for the MPS is
+ * reserved up front for bond dimension d * chi_max (the MPO growth of Sec. 2.4).
+ * gcamps_create is gcamps_create_batch with batch = 1. */
+int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
+int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
+void gcamps_destroy(gcamps_t* h);
+
+/* C <- G C for a one- or two-qudit Clifford G (Sec. 3, top loop of Fig. 3): the tableau rows
+ * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every
+ * circuit of the handle. */
+int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img);
+
+/* Diagonal non-Clifford gate diag(exp(i phases[j])), j = 0..d-1, on `site` (Sec. 2.3.2, Sec. 3):
+ * P = C^dag Z_site C is read from the inverse tableau, the gate is expanded as
+ * sum_m c_m Z^m and applied to the MPS as the d-term MPO sum_m c_m P^m over the support span
+ * [f, l] of P, then [f, l] is recompressed (QR-equivalent sweep, then truncated SVD with
+ * cutoff and chi_max).  Applied to every circuit of the handle. */
+int gcamps_apply_nonclifford(gcamps_t* h, int site, const double* phases);
+
+/* Disentangle the span of the last non-Clifford gate (Sec. 3): alternating sweeps over its
+ * bonds; at each bond every class Q is scored by the entanglement entropy of Q theta, the best
+ * one is applied if it lowers the entropy by more than tie_tol, and C <- C Q^dag.  st may be
+ * NULL; if given it receives the counters of circuit 0 after the call (this synchronises).
+ * Applied to every circuit of the handle. */
+int gcamps_disentangle(gcamps_t* h, gcamps_stats* st);
+
+/* Run a gate list on every circuit of the handle.  ops: host array; circuit c runs
+ * ops[begin[c] .. begin[c+1]) (begin has batch+1 entries; NULL begin = all ops on every
+ * circuit).  One kernel launch for the whole list; asynchronous. */
+int gcamps_run(gcamps_t* h, const gcamps_op* ops, int nops, const int32_t* begin);
+/* Same, with `ops_dev` and `begin_dev` already in device memory (no host-to-device copy). */
+int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begin_dev);
+
+/* <psi| W |psi> for W = (x)_j X_j^{x_j} Z_j^{z_j} (phase 1), as C^dag W C is a product of inverse
+ * tableau rows and <MPS|.|MPS> a transfer-matrix contraction (Sec. 3).  O_sigma of Sec. 3 is
+ * the real part.  circuit selects the batch entry. */
+int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z,
+                       double* re, double* im);
+
+/* Dense C|MPS> (d^n amplitudes, d^n <= 2^20) up to one global phase (a Clifford given by its
+ * images has no defined phase): C|y> = prod_j D_j^{y_j} C|0>, with C|0> the common +1
+ * eigenvector of the stabilizer rows.  re/im: d^n doubles each. */
+int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im);
+/* One amplitude <s|C|MPS> with the same global-phase convention (d^n <= 2^20). */
+int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im);
+
+/* Tableau of C: exps[2n][2n] (row-major; rows 0..n-1 = C Z_j C^dag, rows n..2n-1 = C X_j C^dag;
+ * columns x_0..x_{n-1} | z_0..z_{n-1}) and phase[2n] (mod 2d, units of tau). */
+int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
+/* Inverse tableau: rows C^dag Z_j C (0..n-1) and C^dag X_j C (n..2n-1), same layout. */
+int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
+/* Bond dimensions chi[0..n-2] (bond j joins qudits j and j+1). */
+int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi);
+/* Schmidt values of bond `bond` (count <= chi of that bond), sorted descending. */
+int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count);
+/* Weyl string P = C^dag Z_k C of the last non-Clifford gate: x[n], z[n], r. */
+int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
+int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
+/* Disentangler decisions of the circuit since the last reset: (bond, class index) per bond
+ * visit, in visit order; class 0 = nothing applied.  *count receives the total number
+ * recorded; at most cap pairs are copied. */
+int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, int32_t* count);
+
+/* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded. */
+int gcamps_sync(gcamps_t* h);
+/* Back to |0...0>, C = I, counters and decisions cleared, for every circuit (enqueued on the
+ * handle's stream; asynchronous). */
+int gcamps_reset(gcamps_t* h);
+const char* gcamps_last_error(gcamps_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCAMPS_H */

@@ -1,0 +1,230 @@
+"""GB300-native GCAMPS hot path (arxiv 2511.06672): Python binding of libgcamps.
+
+The binding only marshals arguments; every step of the simulation runs in the CUDA kernels of
+libgcamps (``csrc/``), behind the C ABI of ``include/gcamps.h``.  Importing the package does not
+touch the GPU; creating a ``Simulator`` loads the library and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import _native as N
+from ._native import OP_DTYPE, OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE
+
+__all__ = ["Simulator", "GcampsError", "sp4_images", "num_candidates", "candidate", "ops_from_gates",
+           "OP_DTYPE", "OP_CLIFFORD", "OP_NONCLIFFORD", "OP_DISENTANGLE"]
+
+
+class GcampsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gcamps error {code}: {msg}")
+        self.code = code
+
+
+def _check(lib, h, rc):
+    if rc != N.OK:
+        msg = lib.gcamps_last_error(h).decode() if h else ""
+        raise GcampsError(rc, msg)
+
+
+def num_candidates(d: int) -> int:
+    return N.load().gcamps_num_candidates(d)
+
+
+def sp4_images(d: int, sp_index: int, shift=(0, 0, 0, 0)) -> np.ndarray:
+    """Generator images (20 int32) of the seeded-circuit gate (sp_index, shift)."""
+    lib = N.load()
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    img = np.zeros(20, dtype=np.int32)
+    rc = lib.gcamps_sp4_images(d, int(sp_index), N.ptr(sh, C.c_int32), N.ptr(img, C.c_int32))
+    if rc:
+        raise GcampsError(rc, "bad sp4 index or shift")
+    return img
+
+
+def candidate(d: int, k: int):
+    """(images[20], unitary d^2 x d^2) of disentangler class k, from the library's host tables."""
+    lib = N.load()
+    img = np.zeros(20, dtype=np.int32)
+    u = np.zeros(2 * d ** 4)
+    rc = lib.gcamps_candidate(d, k, N.ptr(img, C.c_int32), N.ptr(u, C.c_double))
+    if rc:
+        raise GcampsError(rc, "bad class index")
+    return img, (u[0::2] + 1j * u[1::2]).reshape(d * d, d * d)
+
+
+def ops_from_gates(gates: Iterable, d: int, disentangle_after_t: bool = True) -> np.ndarray:
+    """Gate list (synth.circuits gates) -> array of gcamps_op records."""
+    rows = []
+    cache = {}
+    for g in gates:
+        if hasattr(g, "sp_index"):
+            key = (g.sp_index, tuple(g.shift))
+            if key not in cache:
+                cache[key] = sp4_images(d, g.sp_index, g.shift)
+            r = np.zeros((), dtype=OP_DTYPE)
+            r["kind"], r["q0"], r["q1"] = OP_CLIFFORD, g.q0, g.q1
+            r["img"] = cache[key]
+            rows.append(r)
+        else:
+            r = np.zeros((), dtype=OP_DTYPE)
+            r["kind"], r["q0"], r["q1"] = OP_NONCLIFFORD, g.site, -1
+            ph = np.zeros(4)
+            ph[: len(g.phases)] = g.phases
+            r["phases"] = ph
+            rows.append(r)
+            if disentangle_after_t:
+                r2 = np.zeros((), dtype=OP_DTYPE)
+                r2["kind"] = OP_DISENTANGLE
+                rows.append(r2)
+    out = np.zeros(len(rows), dtype=OP_DTYPE)
+    for i, r in enumerate(rows):
+        out[i] = r
+    return out
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Simulator:
+    """psi = C|MPS> for ``batch`` independent circuits of n qudits (Sec. 3 of the paper)."""
+
+    def __init__(self, n: int, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
+                 tie_tol: float = 1e-10, batch: int = 1, stream=None, strict_weight: float = 0.0):
+        self._lib = N.load()
+        o = N.Opts()
+        self._lib.gcamps_default_opts(C.byref(o))
+        o.cutoff, o.max_sweeps, o.tie_tol, o.strict_weight = cutoff, max_sweeps, tie_tol, strict_weight
+        s = _stream_handle(stream)
+        o.cuda_stream = C.c_void_p(s) if s else None
+        h = C.c_void_p()
+        rc = self._lib.gcamps_create_batch(batch, n, d, chi_max, C.byref(o), C.byref(h))
+        if rc:
+            raise GcampsError(rc, "gcamps_create failed")
+        self._h = h
+        self.n, self.d, self.chi_max, self.batch = n, d, chi_max, batch
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gcamps_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, rc):
+        _check(self._lib, self._h, rc)
+
+    # -- gates
+    def apply_clifford(self, q0: int, q1: int, img: Sequence[int]):
+        a = np.ascontiguousarray(img, dtype=np.int32)
+        self._c(self._lib.gcamps_apply_clifford(self._h, q0, q1, N.ptr(a, C.c_int32)))
+
+    def apply_nonclifford(self, site: int, phases: Sequence[float]):
+        p = np.zeros(4)
+        p[: len(phases)] = phases
+        self._c(self._lib.gcamps_apply_nonclifford(self._h, site, N.ptr(p, C.c_double)))
+
+    def disentangle(self) -> dict:
+        st = N.Stats()
+        self._c(self._lib.gcamps_disentangle(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def run(self, ops: np.ndarray, begin: Optional[Sequence[int]] = None):
+        ops = np.ascontiguousarray(ops, dtype=OP_DTYPE)
+        b = None if begin is None else np.ascontiguousarray(begin, dtype=np.int32)
+        self._c(self._lib.gcamps_run(self._h, ops.ctypes.data_as(C.c_void_p), len(ops),
+                                     None if b is None else N.ptr(b, C.c_int32)))
+
+    def run_device(self, ops_dev_ptr: int, begin_dev_ptr: int):
+        self._c(self._lib.gcamps_run_device(self._h, C.c_void_p(ops_dev_ptr), C.c_void_p(begin_dev_ptr)))
+
+    def sync(self):
+        self._c(self._lib.gcamps_sync(self._h))
+
+    def reset(self):
+        self._c(self._lib.gcamps_reset(self._h))
+
+    # -- readouts
+    def expect_weyl(self, x, z, circuit: int = 0) -> complex:
+        xa = np.ascontiguousarray(x, dtype=np.int32)
+        za = np.ascontiguousarray(z, dtype=np.int32)
+        re, im = C.c_double(), C.c_double()
+        self._c(self._lib.gcamps_expect_weyl(self._h, circuit, N.ptr(xa, C.c_int32), N.ptr(za, C.c_int32),
+                                             C.byref(re), C.byref(im)))
+        return complex(re.value, im.value)
+
+    def statevector(self, circuit: int = 0) -> np.ndarray:
+        dim = self.d ** self.n
+        re, im = np.zeros(dim), np.zeros(dim)
+        self._c(self._lib.gcamps_statevector(self._h, circuit, N.ptr(re, C.c_double), N.ptr(im, C.c_double)))
+        return re + 1j * im
+
+    def amplitude(self, digits, circuit: int = 0) -> complex:
+        a = np.ascontiguousarray(digits, dtype=np.int32)
+        re, im = C.c_double(), C.c_double()
+        self._c(self._lib.gcamps_amplitude(self._h, circuit, N.ptr(a, C.c_int32), C.byref(re), C.byref(im)))
+        return complex(re.value, im.value)
+
+    def tableau(self, circuit: int = 0):
+        n = self.n
+        e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
+        p = np.zeros(2 * n, dtype=np.uint8)
+        self._c(self._lib.gcamps_get_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
+        return e, p
+
+    def inverse_tableau(self, circuit: int = 0):
+        n = self.n
+        e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
+        p = np.zeros(2 * n, dtype=np.uint8)
+        self._c(self._lib.gcamps_get_inverse_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
+        return e, p
+
+    def bond_dims(self, circuit: int = 0) -> list:
+        a = np.zeros(self.n - 1, dtype=np.int32)
+        self._c(self._lib.gcamps_get_bond_dims(self._h, circuit, N.ptr(a, C.c_int32)))
+        return a.tolist()
+
+    def schmidt_values(self, bond: int, circuit: int = 0) -> np.ndarray:
+        s = np.zeros(self.d * self.chi_max * self.d + 64)
+        cnt = C.c_int32()
+        self._c(self._lib.gcamps_get_schmidt(self._h, circuit, bond, N.ptr(s, C.c_double), C.byref(cnt)))
+        return s[: cnt.value].copy()
+
+    def last_weyl(self, circuit: int = 0):
+        x = np.zeros(self.n, dtype=np.int32)
+        z = np.zeros(self.n, dtype=np.int32)
+        r = C.c_int32()
+        self._c(self._lib.gcamps_get_last_weyl(self._h, circuit, N.ptr(x, C.c_int32), N.ptr(z, C.c_int32),
+                                               C.byref(r)))
+        return r.value, x, z
+
+    def stats(self, circuit: int = 0) -> dict:
+        st = N.Stats()
+        self._c(self._lib.gcamps_get_stats(self._h, circuit, C.byref(st)))
+        return st.as_dict()
+
+    def decisions(self, circuit: int = 0) -> list:
+        cnt = C.c_int32()
+        self._c(self._lib.gcamps_get_decisions(self._h, circuit, None, 0, C.byref(cnt)))
+        a = np.zeros(2 * max(cnt.value, 1), dtype=np.int32)
+        self._c(self._lib.gcamps_get_decisions(self._h, circuit, N.ptr(a, C.c_int32), cnt.value, C.byref(cnt)))
+        return [(int(a[2 * i]), int(a[2 * i + 1])) for i in range(min(cnt.value, len(a) // 2))]

@@ -1,0 +1,1356 @@
+// Device engine of libgcamps: the GCAMPS non-Clifford step (arxiv 2511.06672, Sec. 3) on sm_103a.
+//
+// One CTA runs one circuit.  A launch processes a whole gate list for every circuit of the
+// batch, so the control flow of the method (support span of the commuted Weyl string, bond
+// dimensions after truncation, the disentangler decision at every bond) stays on the device and
+// no host round trip separates two steps.
+//
+// Layout of a circuit in device memory (see gcamps_internal.h):
+//   tableau   fwd exps [2n][2n] | fwd phase [2n] | inv exps [2n][2n] | inv phase [2n]  (uint8)
+//             rows 0..n-1: C Z_j C^dag (fwd) / C^dag Z_j C (inv); rows n..2n-1: the X_j images;
+//             columns x_0..x_{n-1} | z_0..z_{n-1}; phase in units of tau = exp(i pi/d), mod 2d.
+//   MPS       site j in its own slot, compact row-major (a, s, b) with the current bond dims
+//             dims[j] x d x dims[j+1]; complex128.
+//   scratch   two-site tensor, Jacobi buffers, matmul staging, per-warp scoring buffers.
+//
+// All arithmetic on the MPS is complex128 (FP64), the precision the paper's simulator uses
+// (Sec. 4.1.2); the tableau is exact integer arithmetic mod d / mod 2d.
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cstdint>
+
+#include "gcamps_internal.h"
+
+namespace gcx {
+namespace {
+
+// ------------------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc + conj(a) * b
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// -------------------------------------------------------------------------- per-CTA workspace
+struct Smem {
+  uint8_t lut[81 * 5];        // conjugation table of the current two-qudit Clifford
+  int img[20];                // its generator images, 4 x (x0, z0, x1, z1, r)
+  int inv[20];                // images of its inverse
+  uint8_t src[4][2 * kMaxN];  // rows read by a row product
+  int srcr[4];
+  double scores[kMaxK];
+  double red[kWarps * 4];
+  double2 coef[4];            // MPO term coefficients c_m tau^{...}
+  double2 tau[6];             // tau^k, k < 2d
+  int flag;
+  int ival[8];
+  double dval[4];
+};
+
+struct Ctx {
+  const Engine* e;
+  int c, n, d, K;
+  uint8_t *fx, *fr, *ix, *ir;
+  double2* mps;
+  int* dims;
+  int* meta;
+  long long* stats;
+  double* dstats;
+  int* dec;
+  int8_t* weyl;
+  double2* scr;
+  double* sing;
+  int* perm;
+};
+
+__device__ __forceinline__ double2* site_ptr(const Ctx& C, int j) { return C.mps + C.e->site_off[j]; }
+
+__device__ Ctx make_ctx(const Engine& e, int c) {
+  Ctx C;
+  C.e = &e;
+  C.c = c;
+  C.n = e.n;
+  C.d = e.d;
+  C.K = e.K;
+  uint8_t* t = e.tab + (long long)c * e.tab_stride;
+  const int n = e.n;
+  C.fx = t;
+  C.fr = t + 4 * n * n;
+  C.ix = C.fr + 2 * n;
+  C.ir = C.ix + 4 * n * n;
+  C.mps = e.mps + (long long)c * e.mps_stride;
+  C.dims = e.dims + (long long)c * (n + 1);
+  C.meta = e.meta + (long long)c * M_COUNT;
+  C.stats = e.stats + (long long)c * S_COUNT;
+  C.dstats = e.dstats + (long long)c * 2;
+  C.dec = e.dec + (long long)c * kDecCap * 2;
+  C.weyl = e.weyl + (long long)c * 2 * n;
+  C.scr = e.scr + (long long)c * e.sl.total;
+  C.sing = e.sing + (long long)c * e.sing_stride;
+  C.perm = e.iscr + (long long)c * e.iscr_stride;
+  return C;
+}
+
+__device__ void set_status(const Ctx& C, int code) {
+  if (C.meta[M_STATUS] == 0) C.meta[M_STATUS] = code;
+}
+
+__device__ double block_sum(double v, Smem& s) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s.red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) t += s.red[i];
+  return t;
+}
+
+__device__ void block_copy(double2* dst, const double2* src, long long count) {
+  for (long long i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
+// C[M x N] = A[M x K] * B[K x N], row-major, no aliasing.
+__device__ void block_matmul(double2* Cm, const double2* A, const double2* B, int M, int K, int N) {
+  const long long total = (long long)M * N;
+  for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int r = (int)(idx / N), col = (int)(idx % N);
+    const double2* a = A + (long long)r * K;
+    double2 acc = cz();
+    for (int k = 0; k < K; ++k) acc = cfma(a[k], B[(long long)k * N + col], acc);
+    Cm[idx] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------- tableau (Sec. 2.3)
+// Images are normalised to 4 x (x0, z0, x1, z1, r); for one qudit only generators 0, 1 are used
+// and x1 = z1 = 0.
+
+// lut[v] = exponents and phase of G W(v) G^dag for every local exponent vector v, where
+// W(v) = X_q0^v0 Z_q0^v1 X_q1^v2 Z_q1^v3 and the images of the generators are s.img.  The product of
+// images is accumulated with the Weyl rule  (tau^r W(a))(tau^r' W(b)) = tau^{r+r'+2 sum z(a) x(b)} W(a+b).
+__device__ void lut_build(Smem& s, int nq, int d) {
+  const int ng = 2 * nq;
+  int nent = d * d;
+  if (nq == 2) nent *= d * d;
+  for (int v = threadIdx.x; v < nent; v += blockDim.x) {
+    int dig[4] = {0, 0, 0, 0};
+    int t = v;
+    for (int k = ng - 1; k >= 0; --k) {
+      dig[k] = t % d;
+      t /= d;
+    }
+    int ax0 = 0, az0 = 0, ax1 = 0, az1 = 0, r = 0;
+    for (int k = 0; k < ng; ++k) {
+      const int* g = s.img + 5 * k;
+      for (int p = 0; p < dig[k]; ++p) {
+        r += g[4] + 2 * (az0 * g[0] + az1 * g[2]);
+        ax0 = (ax0 + g[0]) % d;
+        az0 = (az0 + g[1]) % d;
+        ax1 = (ax1 + g[2]) % d;
+        az1 = (az1 + g[3]) % d;
+      }
+    }
+    uint8_t* o = s.lut + 5 * v;
+    o[0] = (uint8_t)ax0;
+    o[1] = (uint8_t)az0;
+    o[2] = (uint8_t)ax1;
+    o[3] = (uint8_t)az1;
+    o[4] = (uint8_t)(r % (2 * d));
+  }
+  __syncthreads();
+  // Inverse images: the unique v with G W(v) G^dag = tau^delta g_k gives G^dag g_k G = tau^{-delta} W(v).
+  for (int v = threadIdx.x; v < nent; v += blockDim.x) {
+    const uint8_t* o = s.lut + 5 * v;
+    int hit = -1, cnt = 0;
+    for (int k = 0; k < 4; ++k) {
+      if (o[k]) {
+        ++cnt;
+        hit = (o[k] == 1) ? k : -2;
+      }
+    }
+    if (cnt == 1 && hit >= 0 && hit < ng) {
+      int dig[4] = {0, 0, 0, 0};
+      int t = v;
+      for (int k = ng - 1; k >= 0; --k) {
+        dig[k] = t % d;
+        t /= d;
+      }
+      int* w = s.inv + 5 * hit;
+      for (int k = 0; k < 4; ++k) w[k] = dig[k];
+      w[4] = (2 * d - o[4]) % (2 * d);
+    }
+  }
+  __syncthreads();
+}
+
+// Conjugate every row of a tableau by the Clifford of s.lut on sites q0 (, q1).
+__device__ void tab_apply_lut(Smem& s, uint8_t* X, uint8_t* R, int n, int d, int q0, int q1, int nq) {
+  for (int row = threadIdx.x; row < 2 * n; row += blockDim.x) {
+    uint8_t* e = X + (long long)row * 2 * n;
+    int v = e[q0] * d + e[n + q0];
+    if (nq == 2) v = (v * d + e[q1]) * d + e[n + q1];
+    const uint8_t* o = s.lut + 5 * v;
+    e[q0] = o[0];
+    e[n + q0] = o[1];
+    if (nq == 2) {
+      e[q1] = o[2];
+      e[n + q1] = o[3];
+    }
+    R[row] = (uint8_t)((R[row] + o[4]) % (2 * d));
+  }
+  __syncthreads();
+}
+
+// Replace the rows of the generators on (q0, q1) by products of the old rows: row(g_k) becomes
+// tau^{r_k} prod_g row(g)^{v_k[g]} for the images (v_k, r_k) in s.inv (generator order
+// X_q0, Z_q0, X_q1, Z_q1; row of X_q is n + q, of Z_q is q).
+__device__ void tab_rowprod(Smem& s, uint8_t* X, uint8_t* R, int n, int d, int q0, int q1, int nq) {
+  const int ng = 2 * nq;
+  const int rowlen = 2 * n;
+  for (int i = threadIdx.x; i < ng * rowlen; i += blockDim.x) {
+    const int g = i / rowlen, j = i % rowlen;
+    const int q = (g >> 1) ? q1 : q0;
+    const int row = (g & 1) ? q : n + q;
+    s.src[g][j] = X[(long long)row * rowlen + j];
+  }
+  if (threadIdx.x < ng) {
+    const int g = threadIdx.x;
+    const int q = (g >> 1) ? q1 : q0;
+    s.srcr[g] = R[(g & 1) ? q : n + q];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < ng) {
+    constexpr int kPer = (kMaxN + 31) / 32;
+    int ax[kPer], az[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) ax[t] = az[t] = 0;
+    int r = s.inv[5 * w + 4];
+    for (int g = 0; g < ng; ++g) {
+      const int pw = s.inv[5 * w + g];
+      for (int p = 0; p < pw; ++p) {
+        int loc = 0;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+          const int j = lane + 32 * t;
+          if (j < n) loc += az[t] * s.src[g][j];
+        }
+        r += s.srcr[g] + 2 * warp_sum_int(loc);
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+          const int j = lane + 32 * t;
+          if (j < n) {
+            ax[t] = (ax[t] + s.src[g][j]) % d;
+            az[t] = (az[t] + s.src[g][n + j]) % d;
+          }
+        }
+      }
+    }
+    const int q = (w >> 1) ? q1 : q0;
+    const int row = (w & 1) ? q : n + q;
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int j = lane + 32 * t;
+      if (j < n) {
+        X[(long long)row * rowlen + j] = (uint8_t)ax[t];
+        X[(long long)row * rowlen + n + j] = (uint8_t)az[t];
+      }
+    }
+    if (lane == 0) R[row] = (uint8_t)(((r % (2 * d)) + 2 * d) % (2 * d));
+  }
+  __syncthreads();
+}
+
+__device__ void load_images(Smem& s, const int32_t* img, int nq) {
+  if (threadIdx.x < 20) {
+    int v = 0;
+    const int k = threadIdx.x / 5, f = threadIdx.x % 5;
+    if (nq == 2) {
+      v = img[threadIdx.x];
+    } else if (k < 2) {
+      if (f == 0) v = img[3 * k + 0];
+      else if (f == 1) v = img[3 * k + 1];
+      else if (f == 4) v = img[3 * k + 2];
+    }
+    s.img[threadIdx.x] = v;
+    s.inv[threadIdx.x] = 0;
+  }
+  __syncthreads();
+}
+
+// C <- G C (Sec. 3, top loop of Fig. 3).  Forward rows are conjugated by G; the rows of the
+// inverse tableau for G's sites become products of old rows via the images of G^{-1}.
+__device__ void apply_clifford(Smem& s, const Ctx& C, int q0, int q1, const int32_t* img) {
+  const int nq = (q1 < 0) ? 1 : 2;
+  load_images(s, img, nq);
+  lut_build(s, nq, C.d);
+  tab_apply_lut(s, C.fx, C.fr, C.n, C.d, q0, q1, nq);
+  tab_rowprod(s, C.ix, C.ir, C.n, C.d, q0, q1, nq);
+  if (threadIdx.x == 0) C.stats[S_CLIFF] += 1;
+}
+
+// C <- C Q^dag (Sec. 3): the inverse rows are conjugated by Q, the forward rows of Q's sites
+// become products of old rows via the images of Q^{-1}.
+__device__ void fold_candidate(Smem& s, const Ctx& C, int k, int q0) {
+  load_images(s, C.e->candImg + 20 * k, 2);
+  lut_build(s, 2, C.d);
+  tab_apply_lut(s, C.ix, C.ir, C.n, C.d, q0, q0 + 1, 2);
+  tab_rowprod(s, C.fx, C.fr, C.n, C.d, q0, q0 + 1, 2);
+}
+
+// --------------------------------------------------------- one-sided Jacobi SVD (block level)
+// Orthogonalises the n columns of B (m x n, column-major) by complex Jacobi rotations applied
+// from the right, accumulating them in W (n x n, column-major, starts as I):  B_in W = B_out.
+// Round-robin ordering: in each round the n/2 column pairs are disjoint and handled by the
+// warps in parallel.  A pair is rotated while |b_i^H b_j| > tol * |b_i| |b_j|.  Returns the number
+// of sweeps, or -1 if `max_sweeps` were not enough.
+__device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* W, int max_sweeps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long i = threadIdx.x; i < (long long)n * n; i += blockDim.x)
+    W[i] = ((i % n) == (i / n)) ? make_double2(1.0, 0.0) : cz();
+  if (threadIdx.x == 0) s.flag = 0;
+  __syncthreads();
+  if (n <= 1) return 0;
+  const int N = n + (n & 1);
+  const int npairs = N / 2;
+  const double tol = 1e-14;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < N - 1; ++round) {
+      for (int p = warp; p < npairs; p += kWarps) {
+        const int pa = (p == 0) ? 0 : 1 + ((p - 1 + round) % (N - 1));
+        const int qa = 1 + ((N - 2 - p + round) % (N - 1));
+        int i = pa < qa ? pa : qa, j = pa < qa ? qa : pa;
+        if (j >= n) continue;
+        double2* bi = B + (long long)i * m;
+        double2* bj = B + (long long)j * m;
+        double al = 0, be = 0, gr = 0, gi = 0;
+        for (int r = lane; r < m; r += 32) {
+          const double2 x = bi[r], y = bj[r];
+          al = fma(x.x, x.x, fma(x.y, x.y, al));
+          be = fma(y.x, y.x, fma(y.y, y.y, be));
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));   // Re conj(x) y
+          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));  // Im conj(x) y
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        const double g = hypot(gr, gi);
+        if (!(g > tol * sqrt(al) * sqrt(be)) || g < 1e-300) continue;
+        const double zeta = (be - al) / (2.0 * g);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t);
+        const double sn = cs * t;
+        const double2 e = make_double2(gr / g, gi / g);     // gamma / |gamma|
+        const double2 se = cscale(e, sn), sec = cscale(cconj(e), sn);
+        // b_i' = cs b_i - sn conj(e) b_j ; b_j' = sn e b_i + cs b_j
+        for (int r = lane; r < m; r += 32) {
+          const double2 x = bi[r], y = bj[r];
+          bi[r] = csub(cscale(x, cs), cmul(sec, y));
+          bj[r] = cadd(cmul(se, x), cscale(y, cs));
+        }
+        double2* wi = W + (long long)i * n;
+        double2* wj = W + (long long)j * n;
+        for (int r = lane; r < n; r += 32) {
+          const double2 x = wi[r], y = wj[r];
+          wi[r] = csub(cscale(x, cs), cmul(sec, y));
+          wj[r] = cadd(cmul(se, x), cscale(y, cs));
+        }
+        if (lane == 0) s.flag = 1;
+      }
+      __syncthreads();
+    }
+    const int rotated = s.flag;
+    __syncthreads();
+    if (threadIdx.x == 0) s.flag = 0;
+    __syncthreads();
+    if (!rotated) return sweep + 1;
+  }
+  return -1;
+}
+
+// Singular values of the orthogonalised columns, sorted descending: sing[i] = |b_perm[i]|.
+__device__ void sorted_column_norms(const double2* B, int m, int n, double* sv_tmp, double* sing, int* perm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < n; j += kWarps) {
+    double a = 0;
+    for (int r = lane; r < m; r += 32) a += cabs2(B[(long long)j * m + r]);
+    a = warp_sum(a);
+    if (lane == 0) sv_tmp[j] = sqrt(a);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = sv_tmp[j];
+    int rank = 0;
+    for (int i = 0; i < n; ++i) {
+      const double u = sv_tmp[i];
+      rank += (u > v) || (u == v && i < j);
+    }
+    perm[rank] = j;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sing[j] = sv_tmp[perm[j]];
+  __syncthreads();
+}
+
+// Factor M (rows x cols, row-major) = U S Vh keeping the k largest singular values with
+// s_i > cutoff * s_0 (at most cap, at least one).  U: rows x k, Vh: k x cols, both row-major in
+// scratch; S in C.sing[0..k).  If renorm, S is rescaled to unit norm.  Returns k; *disc gets the
+// discarded weight sum_{i>=k} s_i^2.
+struct Factor {
+  double2* U;
+  double2* Vh;
+  int k;
+  double disc;
+};
+
+__device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, int cols, int cap,
+                             bool renorm) {
+  const Engine& e = *C.e;
+  double2* B = C.scr + e.sl.b;
+  double2* W = C.scr + e.sl.w;
+  double2* U = C.scr + e.sl.u;
+  double2* Vh = C.scr + e.sl.vh;
+  double* sing = C.sing;
+  double* svt = C.sing + e.sing_stride / 2;
+  int* perm = C.perm;
+  const bool tall = rows >= cols;
+  const int m = tall ? rows : cols;
+  const int n = tall ? cols : rows;
+  // B = M (tall) or M^H (wide), column-major m x n
+  for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx % cols);
+    if (tall) B[(long long)c * m + r] = M[idx];
+    else B[(long long)r * m + c] = cconj(M[idx]);
+  }
+  __syncthreads();
+  const int sweeps = jacobi_orthogonalize(s, B, m, n, W, 60);
+  if (sweeps < 0 && threadIdx.x == 0) set_status(C, GCAMPS_ENOCONV);
+  sorted_column_norms(B, m, n, svt, sing, perm);
+  // rank rule
+  if (threadIdx.x == 0) {
+    int k = 0;
+    const double s0 = sing[0];
+    if (s0 > 0) {
+      while (k < n && sing[k] > e.cutoff * s0) ++k;
+    }
+    if (k > cap) k = cap;
+    if (k < 1) k = 1;
+    double kept = 0, drop = 0;
+    for (int i = 0; i < n; ++i) (i < k ? kept : drop) += sing[i] * sing[i];
+    s.ival[0] = k;
+    s.dval[0] = drop;
+    s.dval[1] = (renorm && kept > 0) ? 1.0 / sqrt(kept) : 1.0;
+  }
+  __syncthreads();
+  const int k = s.ival[0];
+  const double scale = s.dval[1];
+  Factor F;
+  F.U = U;
+  F.Vh = Vh;
+  F.k = k;
+  F.disc = s.dval[0];
+  // U and Vh
+  for (long long idx = threadIdx.x; idx < (long long)rows * k; idx += blockDim.x) {
+    const int r = (int)(idx / k), i = (int)(idx % k);
+    const int pj = perm[i];
+    if (tall) {
+      const double sv = sing[i];
+      U[idx] = sv > 0 ? cscale(B[(long long)pj * m + r], 1.0 / sv) : cz();
+    } else {
+      U[idx] = W[(long long)pj * n + r];
+    }
+  }
+  for (long long idx = threadIdx.x; idx < (long long)k * cols; idx += blockDim.x) {
+    const int i = (int)(idx / cols), c = (int)(idx % cols);
+    const int pj = perm[i];
+    if (tall) {
+      Vh[idx] = cconj(W[(long long)pj * n + c]);
+    } else {
+      const double sv = sing[i];
+      Vh[idx] = sv > 0 ? cscale(cconj(B[(long long)pj * m + c]), 1.0 / sv) : cz();
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sing[i] *= scale;
+  __syncthreads();
+  return F;
+}
+
+// ---------------------------------------------------------------- canonical-form moves (Sec. 2.4)
+__device__ void note_chi(const Ctx& C, int k) {
+  if (threadIdx.x == 0 && k > C.stats[S_MAXCHI]) C.stats[S_MAXCHI] = k;
+}
+
+// Centre j -> j+1: A_j = U S Vh, A_j <- U, A_{j+1} <- S Vh A_{j+1}.  Singular values at or below
+// cutoff * s_0 (numerical zeros) are dropped, no renormalisation.  `canonical`: the sites right of
+// j+1 are right-orthonormal, so the singular values are Schmidt values and the bond is also capped
+// at its Schmidt-rank bound d^min(b, n-b) (drops only rounding noise).  Right after an MPO the
+// right part is not orthonormal and no such cap applies; the kept count is then at most the
+// current bond dimension.
+__device__ void move_right(Smem& s, const Ctx& C, int j, bool canonical) {
+  const int d = C.d;
+  const int cl = C.dims[j], cr = C.dims[j + 1], cr2 = C.dims[j + 2];
+  double2* A = site_ptr(C, j);
+  double2* A2 = site_ptr(C, j + 1);
+  Factor F = svd_factor(s, C, A, cl * d, cr, canonical ? C.e->bond_bound[j + 1] : (1 << 30), false);
+  const int k = F.k;
+  block_copy(A, F.U, (long long)cl * d * k);
+  for (long long idx = threadIdx.x; idx < (long long)k * cr; idx += blockDim.x)
+    F.Vh[idx] = cscale(F.Vh[idx], C.sing[idx / cr]);
+  __syncthreads();
+  double2* tmp = C.scr + C.e->sl.tmp;
+  block_matmul(tmp, F.Vh, A2, k, cr, d * cr2);
+  __syncthreads();
+  block_copy(A2, tmp, (long long)k * d * cr2);
+  if (threadIdx.x == 0) {
+    C.dims[j + 1] = k;
+    C.meta[M_OC] = j + 1;
+  }
+  __syncthreads();
+}
+
+// Centre j -> j-1: A_j = U S Vh, A_j <- Vh, A_{j-1} <- A_{j-1} U S.  With truncation (cap, renorm)
+// this is one step of the right-to-left compression sweep.
+__device__ double move_left(Smem& s, const Ctx& C, int j, int cap, bool renorm) {
+  const int d = C.d;
+  const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
+  double2* A = site_ptr(C, j);
+  double2* A0 = site_ptr(C, j - 1);
+  const int bb = C.e->bond_bound[j];
+  Factor F = svd_factor(s, C, A, cl, d * cr, cap < bb ? cap : bb, renorm);
+  const int k = F.k;
+  block_copy(A, F.Vh, (long long)k * d * cr);
+  for (long long idx = threadIdx.x; idx < (long long)cl * k; idx += blockDim.x)
+    F.U[idx] = cscale(F.U[idx], C.sing[idx % k]);
+  __syncthreads();
+  double2* tmp = C.scr + C.e->sl.tmp;
+  block_matmul(tmp, A0, F.U, cl2 * d, cl, k);
+  __syncthreads();
+  block_copy(A0, tmp, (long long)cl2 * d * k);
+  if (threadIdx.x == 0) {
+    C.dims[j] = k;
+    C.meta[M_OC] = j - 1;
+  }
+  __syncthreads();
+  return F.disc;
+}
+
+__device__ void move_center(Smem& s, const Ctx& C, int target) {
+  while (true) {
+    const int oc = C.meta[M_OC];
+    __syncthreads();
+    if (oc < target) move_right(s, C, oc, true);
+    else if (oc > target) move_left(s, C, oc, 1 << 30, false);
+    else break;
+  }
+}
+
+// ------------------------------------------------- non-Clifford step (Sec. 2.3.1, Sec. 2.4, Sec. 3)
+// P = C^dag Z_site C is row `site` of the inverse tableau; diag(t) = sum_m c_m Z^m with
+// c_m = (1/d) sum_j t_j omega^{-mj}; C^dag diag(t) C = sum_m c_m P^m is applied as an MPO of bond
+// dimension d that is diagonal in m.  (X^a Z^b)_{s s'} = omega^{b s'} delta_{s, s'+a}, so each
+// MPO tensor is a gather with phases.
+__device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double* phases) {
+  const int n = C.n, d = C.d;
+  const uint8_t* row = C.ix + (long long)site * 2 * n;
+  // support span and sum_j x_j z_j
+  if (threadIdx.x == 0) {
+    s.ival[0] = n;
+    s.ival[1] = -1;
+    s.ival[2] = 0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int x = row[j], z = row[n + j];
+    C.weyl[j] = (int8_t)x;
+    C.weyl[n + j] = (int8_t)z;
+    if (x | z) {
+      atomicMin(&s.ival[0], j);
+      atomicMax(&s.ival[1], j);
+    }
+    if (x * z) atomicAdd(&s.ival[2], x * z);
+  }
+  __syncthreads();
+  const int f = s.ival[0], l = s.ival[1];
+  const int sxz = s.ival[2] % d;
+  const int r = C.ir[site];
+  __syncthreads();
+  if (f > l) {  // a row of a valid tableau is never the identity
+    if (threadIdx.x == 0) set_status(C, GCAMPS_EINVAL);
+    __syncthreads();
+    return;
+  }
+  if (threadIdx.x == 0) {
+    C.meta[M_WEYL_R] = r;
+    C.meta[M_F] = f;
+    C.meta[M_L] = l;
+    C.meta[M_HAVE_SPAN] = 1;
+    C.stats[S_T] += 1;
+    // coefficients of the d MPO terms, including the phase of P^m:
+    // (tau^r W)^m = tau^{r m} omega^{sxz m(m-1)/2} W(m x, m z)
+    for (int m = 0; m < d; ++m) {
+      double re = 0, im = 0;
+      for (int j = 0; j < d; ++j) {
+        double sn, cs;
+        sincos(phases[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
+        re += cs;
+        im += sn;
+      }
+      const int ph = (r * m + 2 * sxz * (m * (m - 1) / 2)) % (2 * d);
+      s.coef[m] = cmul(make_double2(re / d, im / d), s.tau[ph]);
+    }
+  }
+  __syncthreads();
+  // centre into [f, l]
+  {
+    int oc = C.meta[M_OC];
+    __syncthreads();
+    const int target = oc < f ? f : (oc > l ? l : oc);
+    move_center(s, C, target);
+  }
+  double2* stage = C.scr + C.e->sl.theta;
+  for (int j = f; j <= l; ++j) {
+    const int cl = C.dims[j], cr = C.dims[j + 1];
+    const int x = row[j], z = row[n + j];
+    const double2* A = site_ptr(C, j);
+    const bool first = (j == f), last = (j == l);
+    const int ml = (first ? 1 : d), mr = (last ? 1 : d);
+    const int ncl = cl * ml, ncr = cr * mr;
+    const long long total = (long long)ncl * d * ncr;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int B = (int)(idx % ncr);
+      const int sidx = (int)((idx / ncr) % d);
+      const int Aa = (int)(idx / ((long long)ncr * d));
+      double2 v = cz();
+      if (f == l) {
+        for (int m = 0; m < d; ++m) {
+          const int am = (m * x) % d, bm = (m * z) % d;
+          const int sp = (sidx - am + d) % d;
+          const double2 ph = s.tau[(2 * bm * sp) % (2 * d)];
+          v = cadd(v, cmul(s.coef[m], cmul(ph, A[((long long)Aa * d + sp) * cr + B])));
+        }
+      } else {
+        const int ml_idx = first ? -1 : Aa / cl;
+        const int mr_idx = last ? -1 : B / cr;
+        const int a = first ? Aa : Aa % cl;
+        const int b = last ? B : B % cr;
+        int m = first ? mr_idx : ml_idx;
+        if (!first && !last && ml_idx != mr_idx) m = -1;
+        if (m >= 0) {
+          const int am = (m * x) % d, bm = (m * z) % d;
+          const int sp = (sidx - am + d) % d;
+          v = cmul(s.tau[(2 * bm * sp) % (2 * d)], A[((long long)a * d + sp) * cr + b]);
+          if (first) v = cmul(s.coef[m], v);
+        }
+      }
+      stage[idx] = v;
+    }
+    __syncthreads();
+    block_copy(site_ptr(C, j), stage, total);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = f + 1; j <= l; ++j) C.dims[j] *= d;
+  __syncthreads();
+  if (l > f) {
+    // canonicalise [f, l] left to right from f, then truncate right to left
+    if (threadIdx.x == 0) C.meta[M_OC] = f;
+    __syncthreads();
+    for (int j = f; j < l; ++j) move_right(s, C, j, false);
+    double disc = 0;
+    for (int j = l; j > f; --j) {
+      disc += move_left(s, C, j, C.e->chi_max, true);
+      note_chi(C, C.dims[j]);
+    }
+    if (threadIdx.x == 0) {
+      C.dstats[0] += disc;
+      if (C.e->strict_weight > 0 && disc > C.e->strict_weight) set_status(C, GCAMPS_ECHI);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------- candidate scoring (warp level)
+// Householder reduction of a Hermitian m x m matrix (row-major, full storage, overwritten) to a
+// real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).
+__device__ void warp_tridiag(double2* A, int m, double* dg, double* od, int lane) {
+  for (int k = 0; k + 2 < m; ++k) {
+    const int r = m - k - 1;
+    double nrm2 = 0;
+    for (int i = lane; i < r; i += 32) nrm2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
+    nrm2 = warp_sum(nrm2);
+    const double2 x0 = A[(long long)(k + 1) * m + k];
+    const double ax0 = hypot(x0.x, x0.y);
+    if (lane == 0) dg[k] = A[(long long)k * m + k].x;
+    __syncwarp();
+    const double alpha = sqrt(nrm2);
+    if (nrm2 == 0.0 || nrm2 - ax0 * ax0 <= 1e-30 * nrm2) {
+      if (lane == 0) od[k] = ax0;
+      __syncwarp();
+      continue;
+    }
+    const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    const double h = alpha * (alpha + ax0);  // v^H v / 2
+    if (lane == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+    __syncwarp();
+    // p = A_sub v / h, kept in row k
+    for (int i = lane; i < r; i += 32) {
+      double2 acc = cz();
+      const double2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
+      for (int j = 0; j < r; ++j) acc = cfma(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
+      A[(long long)k * m + k + 1 + i] = cscale(acc, 1.0 / h);
+    }
+    __syncwarp();
+    double kr = 0;
+    for (int i = lane; i < r; i += 32) {
+      const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
+      kr += v.x * p.x + v.y * p.y;
+    }
+    kr = warp_sum(kr) / (2.0 * h);
+    __syncwarp();
+    for (int i = lane; i < r; i += 32) {
+      const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
+      A[(long long)k * m + k + 1 + i] = make_double2(p.x - kr * v.x, p.y - kr * v.y);
+    }
+    __syncwarp();
+    for (int idx = lane; idx < r * r; idx += 32) {
+      const int i = idx / r, j = idx % r;
+      const double2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
+      const double2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
+      const double2 t = cadd(cmul(vi, cconj(wj)), cmul(wi, cconj(vj)));
+      double2* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
+      *a = csub(*a, t);
+    }
+    if (lane == 0) od[k] = alpha;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (m >= 2) {
+      dg[m - 2] = A[(long long)(m - 2) * m + (m - 2)].x;
+      const double2 e = A[(long long)(m - 1) * m + (m - 2)];
+      od[m - 2] = hypot(e.x, e.y);
+    }
+    dg[m - 1] = A[(long long)(m - 1) * m + (m - 1)].x;
+  }
+  __syncwarp();
+}
+
+// Eigenvalues of the symmetric tridiagonal (dg, od) by implicit QR steps with the Wilkinson
+// shift (bulge chased from the top of the unreduced block), deflating from the bottom when an
+// off-diagonal falls below eps * |T|.  Eigenvalues overwrite dg.  Returns false at the cap.
+__device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
+  if (m <= 1) return true;
+  double tn = 0;
+  for (int i = 0; i < m; ++i) tn += fabs(dg[i]);
+  for (int i = 0; i + 1 < m; ++i) tn += fabs(od[i]);
+  const double thr = 2.220446049250313e-16 * tn;
+  int hi = m - 1, iters = 0;
+  while (hi > 0) {
+    if (fabs(od[hi - 1]) <= thr) {
+      od[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && fabs(od[lo - 1]) > thr) --lo;
+    if (++iters > 60 * m) return false;
+    const double a = dg[hi - 1], b = od[hi - 1], c = dg[hi];
+    const double delta = 0.5 * (a - c);
+    const double den = delta + copysign(hypot(delta, b), delta);
+    const double mu = (den != 0.0) ? c - b * b / den : c - fabs(b);
+    double x = dg[lo] - mu, z = od[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double rr = hypot(x, z);
+      double cs = 1.0, sn = 0.0;
+      if (rr > 0.0) {
+        cs = x / rr;
+        sn = z / rr;
+      }
+      if (k > lo) od[k - 1] = rr;
+      const double ak = dg[k], bk = od[k], ck = dg[k + 1];
+      const double cc = cs * cs, ss = sn * sn, c2 = 2.0 * cs * sn;
+      dg[k] = cc * ak + c2 * bk + ss * ck;
+      dg[k + 1] = ss * ak - c2 * bk + cc * ck;
+      od[k] = cs * sn * (ck - ak) + (cc - ss) * bk;
+      if (k + 1 < hi) {
+        const double fo = od[k + 1];
+        z = sn * fo;
+        od[k + 1] = cs * fo;
+        x = od[k];
+      }
+    }
+  }
+  return true;
+}
+
+// von Neumann entropy (natural log) of Q theta across (a, s) | (t, b), from the eigenvalues of the
+// Gram matrix on the smaller side.  Runs on one warp; every lane returns the value.
+__device__ double score_candidate(const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
+                                  double2* ws, bool* ok) {
+  const int lane = threadIdx.x & 31;
+  const int d = C.d, dd = d * d;
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols;
+  double2* tp = ws;
+  double2* G = ws + C.e->tcap;
+  double* dg = reinterpret_cast<double*>(G + C.e->wcap);
+  double* od = dg + m;
+  for (long long idx = lane; idx < (long long)rows * cols; idx += 32) {
+    const int rr = (int)(idx / cols), col = (int)(idx % cols);
+    const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
+    const double2* q = Q + (sd * d + t) * dd;
+    const double2* th = theta + (long long)a * dd * cr + b;
+    double2 acc = cz();
+    for (int u = 0; u < dd; ++u) acc = cfma(q[u], th[(long long)u * cr], acc);
+    tp[idx] = acc;
+  }
+  __syncwarp();
+  if (rows <= cols) {
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int i = idx / m, j = idx % m;
+      const double2* ri = tp + (long long)i * cols;
+      const double2* rj = tp + (long long)j * cols;
+      double2 acc = cz();
+      for (int c = 0; c < cols; ++c) acc = cfmac(rj[c], ri[c], acc);   // sum ri conj(rj)
+      G[idx] = acc;
+    }
+  } else {
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int i = idx / m, j = idx % m;
+      double2 acc = cz();
+      for (int r = 0; r < rows; ++r) acc = cfmac(tp[(long long)r * cols + i], tp[(long long)r * cols + j], acc);
+      G[idx] = acc;
+    }
+  }
+  __syncwarp();
+  warp_tridiag(G, m, dg, od, lane);
+  double ent = 0.0;
+  if (lane == 0) {
+    *ok = tridiag_eigenvalues(dg, od, m);
+    double tot = 0;
+    for (int i = 0; i < m; ++i) tot += fmax(dg[i], 0.0);
+    if (tot > 0) {
+      for (int i = 0; i < m; ++i) {
+        const double p = fmax(dg[i], 0.0) / tot;
+        if (p > 0) ent -= p * log(p);
+      }
+    }
+  }
+  ent = __shfl_sync(0xffffffffu, ent, 0);
+  __syncwarp();
+  return ent;
+}
+
+// ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
+__device__ void visit_bond(Smem& s, const Ctx& C, int i, bool ltr, int* accepted) {
+  const Engine& e = *C.e;
+  const int d = C.d, dd = d * d;
+  const int cl = C.dims[i], ch = C.dims[i + 1], cr = C.dims[i + 2];
+  double2* theta = C.scr + e.sl.theta;
+  double2* tmp = C.scr + e.sl.tmp;
+  block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl * d, ch, d * cr);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  double2* ws = C.scr + e.sl.warp + (long long)warp * e.sl.warp_stride;
+  for (int k = warp; k < C.K; k += kWarps) {
+    bool ok = true;
+    const double sc = score_candidate(C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, &ok);
+    if ((threadIdx.x & 31) == 0) {
+      s.scores[k] = sc;
+      if (!ok) set_status(C, GCAMPS_ENOCONV);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double best = s.scores[0];
+    for (int k = 1; k < C.K; ++k) best = fmin(best, s.scores[k]);
+    int kb = 0;
+    while (s.scores[kb] > best + e.tie_tol) ++kb;
+    if (!(s.scores[kb] < s.scores[0] - e.tie_tol)) kb = 0;
+    s.ival[4] = kb;
+    C.stats[S_BONDS] += 1;
+    C.stats[S_CANDS] += C.K;
+    {
+      const double R = cl * d, Cc = d * cr;
+      const double m = R < Cc ? R : Cc, M = R < Cc ? Cc : R;
+      C.dstats[1] += C.K * (8.0 * dd * R * Cc + 4.0 * m * (m + 1.0) * M + (16.0 / 3.0) * m * m * m);
+    }
+    const int nd = C.meta[M_NDEC];
+    if (nd < kDecCap) {
+      C.dec[2 * nd] = i;
+      C.dec[2 * nd + 1] = kb;
+    }
+    C.meta[M_NDEC] = nd + 1;
+  }
+  __syncthreads();
+  const int kb = s.ival[4];
+  if (kb != 0) {
+    const double2* Q = e.candU + (long long)kb * dd * dd;
+    const long long total = (long long)cl * dd * cr;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int b = (int)(idx % cr), u = (int)((idx / cr) % dd);
+      const long long a = idx / ((long long)cr * dd);
+      double2 acc = cz();
+      for (int v = 0; v < dd; ++v) acc = cfma(Q[u * dd + v], theta[(a * dd + v) * cr + b], acc);
+      tmp[idx] = acc;
+    }
+    __syncthreads();
+    block_copy(theta, tmp, total);
+    __syncthreads();
+    fold_candidate(s, C, kb, i);
+    if (threadIdx.x == 0) C.stats[S_ACC] += 1;
+    ++*accepted;
+  }
+  const int bb = e.bond_bound[i + 1];
+  Factor F = svd_factor(s, C, theta, cl * d, d * cr, e.chi_max < bb ? e.chi_max : bb, true);
+  const int k = F.k;
+  if (ltr) {
+    for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
+      F.Vh[idx] = cscale(F.Vh[idx], C.sing[idx / (d * cr)]);
+  } else {
+    for (long long idx = threadIdx.x; idx < (long long)cl * d * k; idx += blockDim.x)
+      F.U[idx] = cscale(F.U[idx], C.sing[idx % k]);
+  }
+  __syncthreads();
+  block_copy(site_ptr(C, i), F.U, (long long)cl * d * k);
+  block_copy(site_ptr(C, i + 1), F.Vh, (long long)k * d * cr);
+  if (threadIdx.x == 0) {
+    C.dims[i + 1] = k;
+    C.meta[M_OC] = ltr ? i + 1 : i;
+    C.dstats[0] += F.disc;
+  }
+  note_chi(C, k);
+  __syncthreads();
+}
+
+__device__ void disentangle(Smem& s, const Ctx& C) {
+  if (!C.meta[M_HAVE_SPAN]) return;
+  const int f = C.meta[M_F], l = C.meta[M_L];
+  __syncthreads();
+  if (l <= f) return;
+  for (int sweep = 0; sweep < C.e->max_sweeps; ++sweep) {
+    const bool ltr = (sweep & 1) == 0;
+    move_center(s, C, ltr ? f : l);
+    int acc = 0;
+    for (int t = 0; t < l - f; ++t) {
+      const int i = ltr ? f + t : l - 1 - t;
+      visit_bond(s, C, i, ltr, &acc);
+    }
+    if (threadIdx.x == 0) C.stats[S_SWEEPS] += 1;
+    __syncthreads();
+    if (acc == 0) break;
+  }
+}
+
+__device__ void init_tau(Smem& s, int d) {
+  if (threadIdx.x < 2 * d) {
+    double sn, cs;
+    sincospi((double)threadIdx.x / d, &sn, &cs);
+    s.tau[threadIdx.x] = make_double2(cs, sn);
+  }
+  __syncthreads();
+}
+
+__device__ void run_op(Smem& s, const Ctx& C, const gcamps_op& op) {
+  switch (op.kind) {
+    case GCAMPS_OP_CLIFFORD:
+      apply_clifford(s, C, op.q0, op.q1, op.img);
+      break;
+    case GCAMPS_OP_NONCLIFFORD:
+      apply_nonclifford(s, C, op.q0, op.phases);
+      break;
+    case GCAMPS_OP_DISENTANGLE:
+      disentangle(s, C);
+      break;
+    default:
+      break;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_run(Engine e, const gcamps_op* ops, const int32_t* begin) {
+  __shared__ Smem s;
+  const int c = blockIdx.x;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  const int stop = begin[c + 1];
+  for (int i = begin[c]; i < stop; ++i) run_op(s, C, ops[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_run_all(Engine e, const gcamps_op* ops, int nops) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, blockIdx.x);
+  init_tau(s, e.d);
+  for (int i = 0; i < nops; ++i) run_op(s, C, ops[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_single(Engine e, gcamps_op op) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, blockIdx.x);
+  init_tau(s, e.d);
+  run_op(s, C, op);
+}
+
+// |0...0> with C = I, counters cleared.
+__global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
+  Ctx C = make_ctx(e, blockIdx.x);
+  const int n = e.n, d = e.d;
+  for (int i = threadIdx.x; i < 4 * n * n; i += blockDim.x) {
+    const int row = i / (2 * n), col = i % (2 * n);
+    // row j < n: Z_j -> z column n + j; row n + j: X_j -> x column j
+    const uint8_t v = (row < n) ? (col == n + row) : (col == row - n);
+    C.fx[i] = v;
+    C.ix[i] = v;
+  }
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    C.fr[i] = 0;
+    C.ir[i] = 0;
+    C.weyl[i] = 0;
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double2* A = site_ptr(C, j);
+    for (int sidx = 0; sidx < d; ++sidx) A[sidx] = make_double2(sidx == 0 ? 1.0 : 0.0, 0.0);
+  }
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) C.dims[j] = 1;
+  if (threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;
+  if (threadIdx.x < S_COUNT) C.stats[threadIdx.x] = (threadIdx.x == S_MAXCHI) ? 1 : 0;
+  if (threadIdx.x < 2) C.dstats[threadIdx.x] = 0.0;
+}
+
+// ------------------------------------------------------------------------------ readouts
+// <MPS| P' |MPS> with P' = C^dag W C = tau^r (x)_j X^{a_j} Z^{b_j}: the inverse-tableau rows are
+// multiplied in the order of W = prod_j X_j^{x_j} Z_j^{z_j}, then transfer matrices left to right.
+__global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8_t* xz, double2* out) {
+  __shared__ Smem s;
+  __shared__ int acc_x[kMaxN], acc_z[kMaxN];
+  __shared__ int acc_r;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  const int n = e.n, d = e.d;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) acc_x[j] = acc_z[j] = 0;
+  if (threadIdx.x == 0) acc_r = 0;
+  __syncthreads();
+  for (int q = 0; q < n; ++q) {
+    for (int kind = 0; kind < 2; ++kind) {
+      const int pw = kind == 0 ? xz[q] : xz[n + q];
+      const int rowi = kind == 0 ? n + q : q;
+      const uint8_t* R = C.ix + (long long)rowi * 2 * n;
+      for (int p = 0; p < pw; ++p) {
+        double loc = 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) loc += acc_z[j] * R[j];
+        const int tot = (int)llround(block_sum(loc, s));
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          acc_x[j] = (acc_x[j] + R[j]) % d;
+          acc_z[j] = (acc_z[j] + R[n + j]) % d;
+        }
+        if (threadIdx.x == 0) acc_r = (acc_r + C.ir[rowi] + 2 * tot) % (2 * d);
+        __syncthreads();
+      }
+    }
+  }
+  // transfer matrices: E (chi x chi) starts as [[1]]
+  double2* E = C.scr + e.sl.b;
+  double2* T = C.scr + e.sl.tmp;
+  double2* E2 = C.scr + e.sl.u;
+  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int cl = C.dims[j], cr = C.dims[j + 1];
+    const double2* A = site_ptr(C, j);
+    const int a_j = acc_x[j], b_j = acc_z[j];
+    // T[a, s, b'] = sum_{a'} E[a, a'] (X^a Z^b A)[a', s, b'],  (X^a Z^b A)[a', s, b'] = omega^{b (s-a)} A[a', s-a, b']
+    for (long long idx = threadIdx.x; idx < (long long)cl * d * cr; idx += blockDim.x) {
+      const int bp = (int)(idx % cr), sd = (int)((idx / cr) % d), a = (int)(idx / ((long long)cr * d));
+      const int sp = (sd - a_j + d) % d;
+      const double2 ph = s.tau[(2 * b_j * sp) % (2 * d)];
+      double2 acc = cz();
+      for (int ap = 0; ap < cl; ++ap) acc = cfma(E[(long long)a * cl + ap], A[((long long)ap * d + sp) * cr + bp], acc);
+      T[idx] = cmul(ph, acc);
+    }
+    __syncthreads();
+    // E'[b, b'] = sum_{a, s} conj(A[a, s, b]) T[a, s, b']
+    for (long long idx = threadIdx.x; idx < (long long)cr * cr; idx += blockDim.x) {
+      const int b = (int)(idx / cr), bp = (int)(idx % cr);
+      double2 acc = cz();
+      for (int a = 0; a < cl; ++a)
+        for (int sd = 0; sd < d; ++sd)
+          acc = cfmac(A[((long long)a * d + sd) * cr + b], T[((long long)a * d + sd) * cr + bp], acc);
+      E2[idx] = acc;
+    }
+    __syncthreads();
+    block_copy(E, E2, (long long)cr * cr);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = cmul(s.tau[acc_r], E[0]);
+}
+
+// Schmidt values of one bond: move the centre next to it and take the singular values.
+__global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond, double* sv, int* cnt) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  move_center(s, C, bond);
+  const int cl = C.dims[bond], cr = C.dims[bond + 1];
+  Factor F = svd_factor(s, C, site_ptr(C, bond), cl * e.d, cr, 1 << 30, false);
+  (void)F;
+  const int m = cl * e.d < cr ? cl * e.d : cr;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = C.sing[i];
+  if (threadIdx.x == 0) *cnt = m;
+}
+
+// Dense MPS vector mv[x] (d^n entries): contraction left to right through two ping-pong buffers
+// of dim * maxdim entries each (the partial contraction over sites 0..j has d^{j+1} chi_{j+1}).
+__global__ void __launch_bounds__(kThreads) k_mps_dense(Engine e, int c, double2* mv, double2* bufa, double2* bufb, long long dim) {
+  Ctx C = make_ctx(e, c);
+  const int n = e.n, d = e.d;
+  double2* cur = bufa;
+  double2* nxt = bufb;
+  long long rowsn = d;
+  int chi = C.dims[1];
+  block_copy(cur, site_ptr(C, 0), (long long)d * chi);
+  __syncthreads();
+  for (int j = 1; j < n; ++j) {
+    const int cr = C.dims[j + 1];
+    block_matmul(nxt, cur, site_ptr(C, j), (int)rowsn, chi, d * cr);
+    __syncthreads();
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+    rowsn *= d;
+    chi = cr;
+  }
+  block_copy(mv, cur, dim);
+}
+
+// For every basis label x: W_x = prod_j D_j^{x_j} = tau^rho W(a, b) from the destabilizer rows.
+__global__ void k_weyl_of_labels(Engine e, int c, long long dim, int* aidx, uint8_t* bdig, int* rho) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= dim) return;
+  Ctx C = make_ctx(e, c);
+  const int n = e.n, d = e.d;
+  int ax[kMaxN], az[kMaxN];
+  for (int j = 0; j < n; ++j) ax[j] = az[j] = 0;
+  int r = 0;
+  long long t = x;
+  int digs[kMaxN];
+  for (int j = n - 1; j >= 0; --j) {
+    digs[j] = (int)(t % d);
+    t /= d;
+  }
+  for (int q = 0; q < n; ++q) {
+    const uint8_t* R = C.fx + (long long)(n + q) * 2 * n;
+    for (int p = 0; p < digs[q]; ++p) {
+      int dot = 0;
+      for (int j = 0; j < n; ++j) dot += az[j] * R[j];
+      r += C.fr[n + q] + 2 * dot;
+      for (int j = 0; j < n; ++j) {
+        ax[j] = (ax[j] + R[j]) % d;
+        az[j] = (az[j] + R[n + j]) % d;
+      }
+    }
+  }
+  int ai = 0;
+  for (int j = 0; j < n; ++j) {
+    ai = ai * d + ax[j];
+    bdig[x * n + j] = (uint8_t)az[j];
+  }
+  aidx[x] = ai;
+  rho[x] = r % (2 * d);
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// C|0>: common +1 eigenvector of the stabilizer rows, by projecting a fixed pseudo-random vector
+// with prod_j (1/d) sum_m S_j^m, then normalising.  One CTA.
+__global__ void __launch_bounds__(kThreads) k_stab_state(Engine e, int c, long long dim, double2* v, double2* w) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  const int n = e.n, d = e.d;
+  for (long long y = threadIdx.x; y < dim; y += blockDim.x) {
+    const unsigned long long h = mix64((unsigned long long)y * 2 + 1);
+    const unsigned long long g = mix64((unsigned long long)y * 2 + 2);
+    v[y] = make_double2((double)(h >> 11) / 9007199254740992.0 - 0.5, (double)(g >> 11) / 9007199254740992.0 - 0.5);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const uint8_t* R = C.fx + (long long)j * 2 * n;
+    const int r = C.fr[j];
+    // S^m = tau^{r m + 2 sxz m(m-1)/2} W(m x, m z); (W(a,b) v)(y) = omega^{b.(y-a)} v(y-a)
+    int sxz = 0;
+    for (int q = 0; q < n; ++q) sxz += R[q] * R[n + q];
+    for (long long y = threadIdx.x; y < dim; y += blockDim.x) {
+      double2 acc = cz();
+      for (int m = 0; m < d; ++m) {
+        long long src = 0;
+        int dot = 0;
+        long long t = y;
+        long long pw = 1;
+        for (int q = n - 1; q >= 0; --q) {
+          const int yq = (int)(t % d);
+          t /= d;
+          const int aq = (m * R[q]) % d, bq = (m * R[n + q]) % d;
+          const int sq = (yq - aq + d) % d;
+          dot += bq * sq;
+          src += sq * pw;
+          pw *= d;
+        }
+        const int ph = (r * m + 2 * (sxz % d) * (m * (m - 1) / 2) + 2 * dot) % (2 * d);
+        acc = cfma(s.tau[ph], v[src], acc);
+      }
+      w[y] = cscale(acc, 1.0 / d);
+    }
+    __syncthreads();
+    block_copy(v, w, dim);
+    __syncthreads();
+  }
+  double nrm = 0;
+  for (long long y = threadIdx.x; y < dim; y += blockDim.x) nrm += cabs2(v[y]);
+  nrm = block_sum(nrm, s);
+  const double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
+  for (long long y = threadIdx.x; y < dim; y += blockDim.x) v[y] = cscale(v[y], inv);
+}
+
+// psi(y) = sum_x M_x tau^{rho(x)} omega^{b(x).(y - a(x))} s0(y - a(x)) for the requested labels y.
+__global__ void k_apply_clifford_dense(Engine e, long long dim, const double2* mv, const double2* s0,
+                                       const int* aidx, const uint8_t* bdig, const int* rho,
+                                       const int32_t* ys, long long nys, double2* out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nys) return;
+  const int n = e.n, d = e.d;
+  const long long y = ys ? ys[t] : t;
+  int yd[kMaxN];
+  {
+    long long u = y;
+    for (int j = n - 1; j >= 0; --j) {
+      yd[j] = (int)(u % d);
+      u /= d;
+    }
+  }
+  double2 tau_t[6];
+  for (int k = 0; k < 2 * d; ++k) {
+    double sn, cs;
+    sincospi((double)k / d, &sn, &cs);
+    tau_t[k] = make_double2(cs, sn);
+  }
+  double2 acc = cz();
+  for (long long x = 0; x < dim; ++x) {
+    const double2 mx = mv[x];
+    if (mx.x == 0.0 && mx.y == 0.0) continue;
+    int ai = aidx[x];
+    long long src = 0, pw = 1;
+    int dot = 0;
+    for (int j = n - 1; j >= 0; --j) {
+      const int aj = ai % d;
+      ai /= d;
+      const int sj = (yd[j] - aj + d) % d;
+      dot += bdig[x * n + j] * sj;
+      src += sj * pw;
+      pw *= d;
+    }
+    const double2 sv = s0[src];
+    if (sv.x == 0.0 && sv.y == 0.0) continue;
+    const int ph = (rho[x] + 2 * dot) % (2 * d);
+    acc = cfma(cmul(mx, tau_t[ph]), sv, acc);
+  }
+  out[t] = acc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- host launchers
+cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st) {
+  k_run<<<e.batch, kThreads, 0, st>>>(e, ops_dev, begin_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
+  k_run_all<<<e.batch, kThreads, 0, st>>>(e, ops_dev, nops);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
+  k_single<<<e.batch, kThreads, 0, st>>>(e, op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const Engine& e, cudaStream_t st) {
+  k_reset<<<e.batch, kThreads, 0, st>>>(e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expect(const Engine& e, int circuit, const int8_t* xz_dev, double2* out_dev, cudaStream_t st) {
+  k_expect<<<1, kThreads, 0, st>>>(e, circuit, xz_dev, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev, cudaStream_t st) {
+  k_schmidt<<<1, kThreads, 0, st>>>(e, circuit, bond, s_dev, cnt_dev);
+  return cudaGetLastError();
+}
+
+// work layout: bufa[dim * maxdim] | bufb[dim * maxdim] | mv[dim] | s0[dim] | w[dim] | aidx[dim] |
+// rho[dim] | bdig[dim * n]
+cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, long long dim,
+                               const int32_t* ys_dev, long long nys, void* work, cudaStream_t st) {
+  const long long nbuf = dim * (long long)e.maxdim;
+  double2* bufa = reinterpret_cast<double2*>(work);
+  double2* bufb = bufa + nbuf;
+  double2* mv = bufb + nbuf;
+  double2* s0 = mv + dim;
+  double2* w = s0 + dim;
+  int* aidx = reinterpret_cast<int*>(w + dim);
+  int* rho = aidx + dim;
+  uint8_t* bdig = reinterpret_cast<uint8_t*>(rho + dim);
+  k_mps_dense<<<1, kThreads, 0, st>>>(e, circuit, mv, bufa, bufb, dim);
+  const int blk = 128;
+  k_weyl_of_labels<<<(unsigned)((dim + blk - 1) / blk), blk, 0, st>>>(e, circuit, dim, aidx, bdig, rho);
+  k_stab_state<<<1, kThreads, 0, st>>>(e, circuit, dim, s0, w);
+  k_apply_clifford_dense<<<(unsigned)((nys + blk - 1) / blk), blk, 0, st>>>(e, dim, mv, s0, aidx, bdig, rho,
+                                                                          ys_dev, nys, out_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace gcx

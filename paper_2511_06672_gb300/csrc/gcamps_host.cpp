@@ -1,0 +1,943 @@
+// Host side of libgcamps: the C ABI of include/gcamps.h, argument validation, device memory,
+// and the one-time construction of the two-qudit disentangler classes (Sec. 3, Sec. 3.1).
+//
+// Nothing here computes a step of the simulation: every call enqueues kernels of
+// gcamps_engine.cu on the handle's stream.  The host code only (a) checks arguments, (b) builds
+// per-d constant tables once (the symplectic group Sp(4, F_d), its classes modulo single-qudit
+// Cliffords, the class unitaries), and (c) moves inputs and outputs.
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gcamps_internal.h"
+
+namespace gcx {
+cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st);
+}
+
+using gcx::Engine;
+using cplx = std::complex<double>;
+
+namespace {
+
+// ------------------------------------------------------------------ symplectic group Sp(4, F_d)
+// A 4x4 matrix over F_d is stored as 16 base-d digits, row-major, most significant first, so the
+// numeric order of codes is the lexicographic order of the row-major entries.  Column k holds the
+// exponents (x_q0, z_q0, x_q1, z_q1) of the image of generator k (X_q0, Z_q0, X_q1, Z_q1).
+using Mat4 = std::array<int, 16>;
+
+uint64_t encode(const Mat4& m, int d) {
+  uint64_t c = 0;
+  for (int i = 0; i < 16; ++i) c = c * d + (uint64_t)m[i];
+  return c;
+}
+Mat4 decode(uint64_t c, int d) {
+  Mat4 m{};
+  for (int i = 15; i >= 0; --i) {
+    m[i] = (int)(c % d);
+    c /= d;
+  }
+  return m;
+}
+Mat4 matmul4(const Mat4& a, const Mat4& b, int d) {
+  Mat4 r{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int s = 0;
+      for (int k = 0; k < 4; ++k) s += a[4 * i + k] * b[4 * k + j];
+      r[4 * i + j] = s % d;
+    }
+  return r;
+}
+Mat4 from_columns(const int cols[4][4]) {
+  Mat4 m{};
+  for (int c = 0; c < 4; ++c)
+    for (int r = 0; r < 4; ++r) m[4 * r + c] = cols[c][r];
+  return m;
+}
+
+// Lambda(u, v) = sum_q z_q(u) x_q(v) - x_q(u) z_q(v)  (W(u) W(v) = omega^Lambda W(v) W(u)).
+int lam(const int* u, const int* v, int nq, int d) {
+  int s = 0;
+  for (int q = 0; q < nq; ++q) s += u[2 * q + 1] * v[2 * q] - u[2 * q] * v[2 * q + 1];
+  return ((s % d) + d) % d;
+}
+
+struct Tables {
+  int d = 0;
+  std::vector<uint64_t> sp4;                 // sorted codes
+  std::vector<Mat4> reps;                    // class representatives, class 0 = identity
+  std::vector<int32_t> img;                  // [K][20]
+  std::vector<double> u;                     // [K][d^4][2] unitaries
+};
+
+// BFS closure of the generators H_0, S_0, H_1, S_1, SUM_01 (Table 1) acting by left
+// multiplication; the Clifford group modulo Weyl shifts and phases is Sp(4, F_d).
+std::vector<uint64_t> enumerate_sp4(int d) {
+  const int m1 = d - 1;
+  const int H0[4][4] = {{0, 1, 0, 0}, {m1, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  const int S0[4][4] = {{1, 1, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  const int H1[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 0, 1}, {0, 0, m1, 0}};
+  const int S1[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 1}, {0, 0, 0, 1}};
+  const int SUM[4][4] = {{1, 0, 1, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, m1, 0, 1}};
+  const Mat4 gens[5] = {from_columns(H0), from_columns(S0), from_columns(H1), from_columns(S1),
+                        from_columns(SUM)};
+  uint64_t space = 1;
+  for (int i = 0; i < 16; ++i) space *= d;
+  std::vector<uint8_t> seen(space / 8 + 1, 0);
+  Mat4 id{};
+  for (int i = 0; i < 4; ++i) id[5 * i] = 1;
+  std::vector<uint64_t> out;
+  std::vector<Mat4> frontier{id};
+  const uint64_t c0 = encode(id, d);
+  seen[c0 >> 3] |= (uint8_t)(1u << (c0 & 7));
+  out.push_back(c0);
+  while (!frontier.empty()) {
+    std::vector<Mat4> next;
+    for (const Mat4& m : frontier)
+      for (const Mat4& g : gens) {
+        const Mat4 p = matmul4(g, m, d);
+        const uint64_t c = encode(p, d);
+        if (seen[c >> 3] & (1u << (c & 7))) continue;
+        seen[c >> 3] |= (uint8_t)(1u << (c & 7));
+        out.push_back(c);
+        next.push_back(p);
+      }
+    frontier.swap(next);
+  }
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+int std_phase(const int* v, int d) {
+  if (d % 2) return 0;
+  return (v[0] * v[1] + v[2] * v[3]) % (2 * d);
+}
+
+// Images (x0, z0, x1, z1, r) of the generators for  W(shift) U_S.
+void images_of(const Mat4& s, const int* shift, int d, int32_t* img) {
+  for (int k = 0; k < 4; ++k) {
+    int v[4];
+    for (int r = 0; r < 4; ++r) v[r] = s[4 * r + k];
+    const int ph = std_phase(v, d) + 2 * lam(shift, v, 2, d);
+    for (int r = 0; r < 4; ++r) img[5 * k + r] = v[r];
+    img[5 * k + 4] = ph % (2 * d);
+  }
+}
+
+// Dense matrix of tau^r X^x0 Z^z0 (x) X^x1 Z^z1 (qudit 0 most significant).
+std::vector<cplx> weyl_dense(const int32_t* w, int d) {
+  const int D = d * d;
+  std::vector<cplx> m(D * D, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int yp = 0; yp < D; ++yp) {
+    const int y0 = yp / d, y1 = yp % d;
+    const int o0 = (y0 + w[0]) % d, o1 = (y1 + w[2]) % d;
+    const int ph = w[4] + 2 * (w[1] * y0 + w[3] * y1);   // tau units
+    m[(o0 * d + o1) * D + yp] = std::polar(1.0, pi * (double)(ph % (2 * d)) / d);
+  }
+  return m;
+}
+
+std::vector<cplx> mm(const std::vector<cplx>& a, const std::vector<cplx>& b, int D) {
+  std::vector<cplx> r(D * D, 0.0);
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) {
+      const cplx aik = a[i * D + k];
+      if (aik == 0.0) continue;
+      for (int j = 0; j < D; ++j) r[i * D + j] += aik * b[k * D + j];
+    }
+  return r;
+}
+
+// The Clifford with the given generator images: U|00> = v, the common +1 eigenvector of the
+// images of Z_0, Z_1 (first entry above 1e-8 in modulus made real positive);
+// U|y0 y1> = Ximg_0^{y0} Ximg_1^{y1} v.
+std::vector<cplx> unitary_from_images(const int32_t* img, int d) {
+  const int D = d * d;
+  std::vector<cplx> proj(D * D, 0.0);
+  for (int i = 0; i < D; ++i) proj[i * D + i] = 1.0;
+  for (int q = 0; q < 2; ++q) {
+    const std::vector<cplx> z = weyl_dense(img + 5 * (2 * q + 1), d);
+    std::vector<cplx> acc(D * D, 0.0), p(D * D, 0.0);
+    for (int i = 0; i < D; ++i) p[i * D + i] = 1.0;
+    for (int m = 0; m < d; ++m) {
+      for (int i = 0; i < D * D; ++i) acc[i] += p[i];
+      p = mm(p, z, D);
+    }
+    for (auto& a : acc) a /= (double)d;
+    proj = mm(proj, acc, D);
+  }
+  int best = 0;
+  double bn = -1;
+  for (int c = 0; c < D; ++c) {
+    double s = 0;
+    for (int r = 0; r < D; ++r) s += std::norm(proj[r * D + c]);
+    if (s > bn + 1e-12) {
+      bn = s;
+      best = c;
+    }
+  }
+  std::vector<cplx> v(D);
+  double nrm = 0;
+  for (int r = 0; r < D; ++r) {
+    v[r] = proj[r * D + best];
+    nrm += std::norm(v[r]);
+  }
+  nrm = std::sqrt(nrm);
+  for (auto& a : v) a /= nrm;
+  for (int r = 0; r < D; ++r)
+    if (std::abs(v[r]) > 1e-8) {
+      const cplx ph = std::abs(v[r]) / v[r];
+      for (auto& a : v) a *= ph;
+      break;
+    }
+  const std::vector<cplx> x0 = weyl_dense(img + 0, d), x1 = weyl_dense(img + 10, d);
+  std::vector<cplx> u(D * D, 0.0);
+  for (int y = 0; y < D; ++y) {
+    std::vector<cplx> col = v;
+    const int reps[2] = {y / d, y % d};
+    for (int q = 0; q < 2; ++q)
+      for (int t = 0; t < reps[q]; ++t) {
+        const std::vector<cplx>& x = q ? x1 : x0;
+        std::vector<cplx> nc(D, 0.0);
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j) nc[i] += x[i * D + j] * col[j];
+        col.swap(nc);
+      }
+    for (int i = 0; i < D; ++i) u[i * D + y] = col[i];
+  }
+  return u;
+}
+
+// Classes {(L_0 (+) L_1) S} of Sp(4, F_d) under single-qudit symplectic maps applied after S.
+// Representative: lexicographically smallest member; the identity class is represented by the
+// identity and listed first, the others in representative order.
+void build_tables(Tables& t, int d) {
+  t.d = d;
+  t.sp4 = enumerate_sp4(d);
+  std::vector<Mat4> sl2;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b)
+      for (int c = 0; c < d; ++c)
+        for (int e = 0; e < d; ++e)
+          if (((a * e - b * c) % d + d) % d == 1) {
+            Mat4 m{};
+            m[0] = a;
+            m[1] = b;
+            m[4] = c;
+            m[5] = e;
+            sl2.push_back(m);
+          }
+  std::vector<Mat4> blocks;
+  for (const Mat4& a : sl2)
+    for (const Mat4& b : sl2) {
+      Mat4 m{};
+      m[0] = a[0];
+      m[1] = a[1];
+      m[4] = a[4];
+      m[5] = a[5];
+      m[10] = b[0];
+      m[11] = b[1];
+      m[14] = b[4];
+      m[15] = b[5];
+      blocks.push_back(m);
+    }
+  std::vector<int> cls(t.sp4.size(), -1);
+  std::vector<Mat4> reps;
+  for (size_t i = 0; i < t.sp4.size(); ++i) {
+    if (cls[i] >= 0) continue;
+    const Mat4 s = decode(t.sp4[i], d);
+    const int id = (int)reps.size();
+    reps.push_back(s);
+    for (const Mat4& b : blocks) {
+      const uint64_t c = encode(matmul4(b, s, d), d);
+      const size_t pos = (size_t)(std::lower_bound(t.sp4.begin(), t.sp4.end(), c) - t.sp4.begin());
+      cls[pos] = id;
+    }
+  }
+  Mat4 id{};
+  for (int i = 0; i < 4; ++i) id[5 * i] = 1;
+  const size_t ipos = (size_t)(std::lower_bound(t.sp4.begin(), t.sp4.end(), encode(id, d)) - t.sp4.begin());
+  const int idc = cls[ipos];
+  t.reps.clear();
+  t.reps.push_back(id);
+  for (int c = 0; c < (int)reps.size(); ++c)
+    if (c != idc) t.reps.push_back(reps[c]);
+  const int K = (int)t.reps.size();
+  const int D = d * d;
+  t.img.assign((size_t)K * 20, 0);
+  t.u.assign((size_t)K * D * D * 2, 0.0);
+  const int zero[4] = {0, 0, 0, 0};
+  for (int k = 0; k < K; ++k) {
+    images_of(t.reps[k], zero, d, &t.img[(size_t)k * 20]);
+    const std::vector<cplx> u = unitary_from_images(&t.img[(size_t)k * 20], d);
+    for (int i = 0; i < D * D; ++i) {
+      t.u[((size_t)k * D * D + i) * 2] = u[i].real();
+      t.u[((size_t)k * D * D + i) * 2 + 1] = u[i].imag();
+    }
+  }
+}
+
+Tables g_tables[4];
+std::once_flag g_once[4];
+
+const Tables& tables(int d) {
+  std::call_once(g_once[d], [d] { build_tables(g_tables[d], d); });
+  return g_tables[d];
+}
+
+// Symplectic images with phases of order d.  nq = 1: img[3k..3k+2] = (x, z, r).
+bool valid_images(const int32_t* img, int nq, int d, std::string* why) {
+  int v[4][5];
+  for (int k = 0; k < 2 * nq; ++k) {
+    for (int f = 0; f < 5; ++f) v[k][f] = 0;
+    if (nq == 2) {
+      for (int f = 0; f < 5; ++f) v[k][f] = img[5 * k + f];
+    } else {
+      v[k][0] = img[3 * k];
+      v[k][1] = img[3 * k + 1];
+      v[k][4] = img[3 * k + 2];
+    }
+    for (int f = 0; f < 4; ++f)
+      if (v[k][f] < 0 || v[k][f] >= d) {
+        *why = "image exponent out of range [0, d)";
+        return false;
+      }
+    if (v[k][4] < 0 || v[k][4] >= 2 * d) {
+      *why = "image phase out of range [0, 2d)";
+      return false;
+    }
+    if (d % 2) {
+      if (v[k][4] % 2) {
+        *why = "odd d: image phase must be a power of omega (even in units of tau)";
+        return false;
+      }
+    } else {
+      const int xz = v[k][0] * v[k][1] + v[k][2] * v[k][3];
+      if ((v[k][4] + xz) % 2) {
+        *why = "d = 2: image must be Hermitian (phase + x.z even)";
+        return false;
+      }
+    }
+  }
+  for (int i = 0; i < 2 * nq; ++i)
+    for (int j = 0; j < 2 * nq; ++j) {
+      int ei[4] = {0, 0, 0, 0}, ej[4] = {0, 0, 0, 0};
+      ei[i] = 1;
+      ej[j] = 1;
+      if (lam(v[i], v[j], nq, d) != lam(ei, ej, nq, d)) {
+        *why = "images are not symplectic";
+        return false;
+      }
+    }
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------ handle
+struct gcamps {
+  Engine e{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  void* dev_block = nullptr;      // one allocation for everything but the op buffer
+  gcamps_op* ops_dev = nullptr;
+  size_t ops_cap = 0;
+  int32_t* begin_dev = nullptr;
+  int8_t* xz_dev = nullptr;
+  double2* out_dev = nullptr;
+  double* schmidt_dev = nullptr;
+  int* cnt_dev = nullptr;
+};
+
+namespace {
+
+int fail(gcamps_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(gcamps_t* h, cudaError_t e, const char* where) {
+  return fail(h, GCAMPS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GC_CUDA(h, call)                                     \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, #call); \
+  } while (0)
+
+long long sat_pow(int d, int k, long long cap) {
+  long long v = 1;
+  for (int i = 0; i < k; ++i) {
+    v *= d;
+    if (v >= cap) return cap;
+  }
+  return v;
+}
+
+int device_status(gcamps_t* h) {
+  std::vector<int> meta((size_t)h->e.batch * gcx::M_COUNT);
+  cudaError_t e = cudaMemcpyAsync(meta.data(), h->e.meta, meta.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device status");
+  for (int c = 0; c < h->e.batch; ++c) {
+    const int s = meta[(size_t)c * gcx::M_COUNT + gcx::M_STATUS];
+    if (s) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "device status %d on circuit %d (%s)", s, c,
+               s == GCAMPS_ENOCONV ? "iteration cap reached" : "chi_max bound");
+      return fail(h, s, buf);
+    }
+  }
+  return GCAMPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gcamps_default_opts(gcamps_opts* o) {
+  if (!o) return;
+  o->cutoff = 1e-12;
+  o->max_sweeps = 8;
+  o->score_kind = 0;
+  o->precision = 0;
+  o->tie_tol = 1e-10;
+  o->strict_weight = 0.0;
+  o->cuda_stream = nullptr;
+}
+
+int gcamps_num_candidates(int d) {
+  if (d != 2 && d != 3) return -1;
+  return (int)tables(d).reps.size();
+}
+
+int gcamps_sp4_images(int d, int64_t sp_index, const int32_t* shift, int32_t* img) {
+  if ((d != 2 && d != 3) || !img) return GCAMPS_EINVAL;
+  const Tables& t = tables(d);
+  if (sp_index < 0 || (uint64_t)sp_index >= t.sp4.size()) return GCAMPS_EINVAL;
+  int sh[4] = {0, 0, 0, 0};
+  if (shift)
+    for (int i = 0; i < 4; ++i) {
+      if (shift[i] < 0 || shift[i] >= d) return GCAMPS_EINVAL;
+      sh[i] = shift[i];
+    }
+  images_of(decode(t.sp4[(size_t)sp_index], d), sh, d, img);
+  return GCAMPS_OK;
+}
+
+int gcamps_candidate(int d, int k, int32_t* img, double* u) {
+  if ((d != 2 && d != 3) || !img) return GCAMPS_EINVAL;
+  const Tables& t = tables(d);
+  if (k < 0 || k >= (int)t.reps.size()) return GCAMPS_EINVAL;
+  std::memcpy(img, &t.img[(size_t)k * 20], 20 * sizeof(int32_t));
+  if (u) {
+    const size_t dd = (size_t)d * d * d * d * 2;
+    std::memcpy(u, &t.u[(size_t)k * dd], dd * sizeof(double));
+  }
+  return GCAMPS_OK;
+}
+
+int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out) {
+  return gcamps_create_batch(1, n, d, chi_max, o, out);
+}
+
+int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out) {
+  if (!out) return GCAMPS_EINVAL;
+  *out = nullptr;
+  if (batch < 1 || n < 2 || n > gcx::kMaxN || (d != 2 && d != 3) || chi_max < 1) return GCAMPS_EINVAL;
+  gcamps_opts opts;
+  gcamps_default_opts(&opts);
+  if (o) opts = *o;
+  if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind != 0 || opts.precision != 0 ||
+      !(opts.tie_tol >= 0.0))
+    return GCAMPS_EINVAL;
+  gcamps_t* h = new (std::nothrow) gcamps;
+  if (!h) return GCAMPS_ENOMEM;
+  const Tables& tb = tables(d);
+  Engine& e = h->e;
+  e.n = n;
+  e.d = d;
+  e.K = (int)tb.reps.size();
+  e.chi_max = chi_max;
+  e.batch = batch;
+  e.max_sweeps = opts.max_sweeps;
+  e.cutoff = opts.cutoff;
+  e.tie_tol = opts.tie_tol;
+  e.strict_weight = opts.strict_weight;
+  // bond capacities: after the MPO a bond holds at most d * min(chi_max, Schmidt bound)
+  std::vector<long long> cap(n + 1, 1);
+  std::vector<int> bound(n + 1, 1);
+  long long maxdim = 1;
+  for (int b = 1; b < n; ++b) {
+    const long long sb = sat_pow(d, std::min(b, n - b), 1LL << 30);
+    bound[b] = (int)sb;
+    cap[b] = d * std::min<long long>(chi_max, sb);
+    maxdim = std::max(maxdim, cap[b]);
+  }
+  e.maxdim = (int)maxdim;
+  std::vector<long long> off(n + 1, 0);
+  long long tcap = 1;
+  for (int j = 0; j < n; ++j) {
+    const long long sz = cap[j] * d * cap[j + 1];
+    off[j + 1] = off[j] + sz;
+    tcap = std::max(tcap, sz);
+    if (j + 2 <= n) tcap = std::max(tcap, cap[j] * d * d * cap[j + 2]);
+  }
+  const long long maxm = (long long)d * maxdim;
+  e.tcap = tcap;
+  e.wcap = maxm * maxm;
+  gcx::ScratchLayout& sl = e.sl;
+  sl.theta = 0;
+  sl.b = sl.theta + tcap;
+  sl.w = sl.b + tcap;
+  sl.u = sl.w + e.wcap;
+  sl.vh = sl.u + tcap;
+  sl.tmp = sl.vh + tcap;
+  sl.warp = sl.tmp + tcap;
+  sl.warp_stride = tcap + e.wcap + maxm + 64;
+  sl.total = sl.warp + gcx::kWarps * sl.warp_stride;
+  e.tab_stride = 2LL * (4LL * n * n + 2LL * n);
+  e.mps_stride = off[n];
+  e.sing_stride = 2 * maxm + 64;
+  e.iscr_stride = maxm + 64;
+  // one device block, carved up
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t bytes = 0;
+  const size_t o_tab = bytes;
+  bytes = align(bytes + (size_t)batch * e.tab_stride);
+  const size_t o_mps = bytes;
+  bytes = align(bytes + (size_t)batch * e.mps_stride * sizeof(double2));
+  const size_t o_off = bytes;
+  bytes = align(bytes + (size_t)(n + 1) * sizeof(long long));
+  const size_t o_bound = bytes;
+  bytes = align(bytes + (size_t)(n + 1) * sizeof(int));
+  const size_t o_dims = bytes;
+  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(int));
+  const size_t o_meta = bytes;
+  bytes = align(bytes + (size_t)batch * gcx::M_COUNT * sizeof(int));
+  const size_t o_stats = bytes;
+  bytes = align(bytes + (size_t)batch * gcx::S_COUNT * sizeof(long long));
+  const size_t o_dstats = bytes;
+  bytes = align(bytes + (size_t)batch * 2 * sizeof(double));
+  const size_t o_dec = bytes;
+  bytes = align(bytes + (size_t)batch * gcx::kDecCap * 2 * sizeof(int));
+  const size_t o_weyl = bytes;
+  bytes = align(bytes + (size_t)batch * 2 * n);
+  const size_t o_scr = bytes;
+  bytes = align(bytes + (size_t)batch * sl.total * sizeof(double2));
+  const size_t o_sing = bytes;
+  bytes = align(bytes + (size_t)batch * e.sing_stride * sizeof(double));
+  const size_t o_iscr = bytes;
+  bytes = align(bytes + (size_t)batch * e.iscr_stride * sizeof(int));
+  const size_t o_candU = bytes;
+  const int D = d * d;
+  bytes = align(bytes + (size_t)e.K * D * D * sizeof(double2));
+  const size_t o_candI = bytes;
+  bytes = align(bytes + (size_t)e.K * 20 * sizeof(int32_t));
+  const size_t o_aux = bytes;
+  bytes = align(bytes + (size_t)(gcx::kMaxN * 2 + 64) + 4096);
+  if (opts.cuda_stream) {
+    h->stream = (cudaStream_t)opts.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return GCAMPS_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  if (cudaMalloc(&h->dev_block, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return GCAMPS_ENOMEM;
+  }
+  char* base = (char*)h->dev_block;
+  e.tab = (uint8_t*)(base + o_tab);
+  e.mps = (double2*)(base + o_mps);
+  e.site_off = (const long long*)(base + o_off);
+  e.bond_bound = (const int*)(base + o_bound);
+  e.dims = (int*)(base + o_dims);
+  e.meta = (int*)(base + o_meta);
+  e.stats = (long long*)(base + o_stats);
+  e.dstats = (double*)(base + o_dstats);
+  e.dec = (int*)(base + o_dec);
+  e.weyl = (int8_t*)(base + o_weyl);
+  e.scr = (double2*)(base + o_scr);
+  e.sing = (double*)(base + o_sing);
+  e.iscr = (int*)(base + o_iscr);
+  e.candU = (const double2*)(base + o_candU);
+  e.candImg = (const int32_t*)(base + o_candI);
+  h->xz_dev = (int8_t*)(base + o_aux);
+  h->out_dev = (double2*)(base + o_aux + align(gcx::kMaxN * 2));
+  h->cnt_dev = (int*)(h->out_dev + 2);
+  cudaError_t ce = cudaMemcpyAsync((void*)e.site_off, off.data(), (size_t)(n + 1) * sizeof(long long),
+                                   cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.bond_bound, bound.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                         h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.candU, tb.u.data(), tb.u.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.candImg, tb.img.data(), tb.img.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess) ce = gcx::launch_reset(e, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) {
+    gcamps_destroy(h);
+    return GCAMPS_ECUDA;
+  }
+  *out = h;
+  return GCAMPS_OK;
+}
+
+void gcamps_destroy(gcamps_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->dev_block) cudaFree(h->dev_block);
+  if (h->ops_dev) cudaFree(h->ops_dev);
+  if (h->begin_dev) cudaFree(h->begin_dev);
+  if (h->schmidt_dev) cudaFree(h->schmidt_dev);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* gcamps_last_error(gcamps_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img) {
+  if (!h) return GCAMPS_EINVAL;
+  const int n = h->e.n;
+  if (!img || q0 < 0 || q0 >= n || q1 >= n || q1 == q0 || q1 < -1)
+    return fail(h, GCAMPS_EINVAL, "bad qudit indices or null images");
+  const int nq = q1 < 0 ? 1 : 2;
+  std::string why;
+  if (!valid_images(img, nq, h->e.d, &why)) return fail(h, GCAMPS_EINVAL, why);
+  gcamps_op op;
+  std::memset(&op, 0, sizeof op);
+  op.kind = GCAMPS_OP_CLIFFORD;
+  op.q0 = q0;
+  op.q1 = q1;
+  std::memcpy(op.img, img, sizeof(int32_t) * (nq == 2 ? 20 : 6));
+  GC_CUDA(h, gcx::launch_single(h->e, op, h->stream));
+  return GCAMPS_OK;
+}
+
+int gcamps_apply_nonclifford(gcamps_t* h, int site, const double* phases) {
+  if (!h) return GCAMPS_EINVAL;
+  if (!phases || site < 0 || site >= h->e.n) return fail(h, GCAMPS_EINVAL, "bad site or null phases");
+  gcamps_op op;
+  std::memset(&op, 0, sizeof op);
+  op.kind = GCAMPS_OP_NONCLIFFORD;
+  op.q0 = site;
+  op.q1 = -1;
+  for (int j = 0; j < h->e.d; ++j) {
+    if (!std::isfinite(phases[j])) return fail(h, GCAMPS_EINVAL, "non-finite phase");
+    op.phases[j] = phases[j];
+  }
+  GC_CUDA(h, gcx::launch_single(h->e, op, h->stream));
+  return GCAMPS_OK;
+}
+
+int gcamps_disentangle(gcamps_t* h, gcamps_stats* st) {
+  if (!h) return GCAMPS_EINVAL;
+  gcamps_op op;
+  std::memset(&op, 0, sizeof op);
+  op.kind = GCAMPS_OP_DISENTANGLE;
+  GC_CUDA(h, gcx::launch_single(h->e, op, h->stream));
+  if (st) return gcamps_get_stats(h, 0, st);
+  return GCAMPS_OK;
+}
+
+static int validate_ops(gcamps_t* h, const gcamps_op* ops, int nops) {
+  std::string why;
+  for (int i = 0; i < nops; ++i) {
+    const gcamps_op& op = ops[i];
+    const int n = h->e.n;
+    switch (op.kind) {
+      case GCAMPS_OP_CLIFFORD: {
+        if (op.q0 < 0 || op.q0 >= n || op.q1 >= n || op.q1 == op.q0 || op.q1 < -1)
+          return fail(h, GCAMPS_EINVAL, "op " + std::to_string(i) + ": bad qudits");
+        if (!valid_images(op.img, op.q1 < 0 ? 1 : 2, h->e.d, &why))
+          return fail(h, GCAMPS_EINVAL, "op " + std::to_string(i) + ": " + why);
+        break;
+      }
+      case GCAMPS_OP_NONCLIFFORD:
+        if (op.q0 < 0 || op.q0 >= n) return fail(h, GCAMPS_EINVAL, "op " + std::to_string(i) + ": bad site");
+        for (int j = 0; j < h->e.d; ++j)
+          if (!std::isfinite(op.phases[j])) return fail(h, GCAMPS_EINVAL, "non-finite phase");
+        break;
+      case GCAMPS_OP_DISENTANGLE:
+        break;
+      default:
+        return fail(h, GCAMPS_EINVAL, "op " + std::to_string(i) + ": unknown kind");
+    }
+  }
+  return GCAMPS_OK;
+}
+
+int gcamps_run(gcamps_t* h, const gcamps_op* ops, int nops, const int32_t* begin) {
+  if (!h || nops < 0 || (nops > 0 && !ops)) return GCAMPS_EINVAL;
+  if (begin) {
+    if (begin[0] != 0) return fail(h, GCAMPS_EINVAL, "begin[0] must be 0");
+    for (int c = 0; c < h->e.batch; ++c)
+      if (begin[c + 1] < begin[c] || begin[c + 1] > nops) return fail(h, GCAMPS_EINVAL, "bad begin offsets");
+  }
+  int rc = validate_ops(h, ops, nops);
+  if (rc) return rc;
+  if (nops == 0) return GCAMPS_OK;
+  if ((size_t)nops > h->ops_cap) {
+    if (h->ops_dev) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->ops_dev);
+      h->ops_dev = nullptr;
+    }
+    size_t cap = 1024;
+    while (cap < (size_t)nops) cap *= 2;
+    if (cudaMalloc(&h->ops_dev, cap * sizeof(gcamps_op)) != cudaSuccess) {
+      cudaGetLastError();
+      h->ops_cap = 0;
+      return fail(h, GCAMPS_ENOMEM, "op buffer");
+    }
+    h->ops_cap = cap;
+  }
+  GC_CUDA(h, cudaMemcpyAsync(h->ops_dev, ops, (size_t)nops * sizeof(gcamps_op), cudaMemcpyHostToDevice, h->stream));
+  if (begin) {
+    if (!h->begin_dev) GC_CUDA(h, cudaMalloc(&h->begin_dev, (size_t)(h->e.batch + 1) * sizeof(int32_t)));
+    GC_CUDA(h, cudaMemcpyAsync(h->begin_dev, begin, (size_t)(h->e.batch + 1) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, h->stream));
+    GC_CUDA(h, gcx::launch_run(h->e, h->ops_dev, h->begin_dev, h->stream));
+  } else {
+    GC_CUDA(h, gcx::launch_run_all(h->e, h->ops_dev, nops, h->stream));
+  }
+  return GCAMPS_OK;
+}
+
+int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begin_dev) {
+  if (!h || !ops_dev || !begin_dev) return GCAMPS_EINVAL;
+  GC_CUDA(h, gcx::launch_run(h->e, ops_dev, begin_dev, h->stream));
+  return GCAMPS_OK;
+}
+
+int gcamps_sync(gcamps_t* h) {
+  if (!h) return GCAMPS_EINVAL;
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return device_status(h);
+}
+
+int gcamps_reset(gcamps_t* h) {
+  if (!h) return GCAMPS_EINVAL;
+  GC_CUDA(h, gcx::launch_reset(h->e, h->stream));
+  return GCAMPS_OK;
+}
+
+static int check_circuit(gcamps_t* h, int circuit) {
+  if (!h) return GCAMPS_EINVAL;
+  if (circuit < 0 || circuit >= h->e.batch) return fail(h, GCAMPS_EINVAL, "circuit index out of range");
+  return GCAMPS_OK;
+}
+
+int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* re, double* im) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  const int n = h->e.n, d = h->e.d;
+  if (!x || !z || !re || !im) return fail(h, GCAMPS_EINVAL, "null argument");
+  std::vector<int8_t> xz(2 * n);
+  for (int j = 0; j < n; ++j) {
+    if (x[j] < 0 || x[j] >= d || z[j] < 0 || z[j] >= d) return fail(h, GCAMPS_EINVAL, "exponent out of range");
+    xz[j] = (int8_t)x[j];
+    xz[n + j] = (int8_t)z[j];
+  }
+  GC_CUDA(h, cudaMemcpyAsync(h->xz_dev, xz.data(), 2 * n, cudaMemcpyHostToDevice, h->stream));
+  GC_CUDA(h, gcx::launch_expect(h->e, circuit, h->xz_dev, h->out_dev, h->stream));
+  double2 r;
+  GC_CUDA(h, cudaMemcpyAsync(&r, h->out_dev, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  *re = r.x;
+  *im = r.y;
+  return device_status(h);
+}
+
+static int statevector_impl(gcamps_t* h, int circuit, const int32_t* ys, long long nys, double* re, double* im) {
+  const int n = h->e.n, d = h->e.d;
+  long long dim = 1;
+  for (int j = 0; j < n; ++j) {
+    dim *= d;
+    if (dim > (1LL << 20)) return fail(h, GCAMPS_EINVAL, "d^n above 2^20: dense readout not supported");
+  }
+  const long long nbuf = dim * (long long)h->e.maxdim;
+  const size_t bytes = (size_t)(2 * nbuf + 3 * dim) * sizeof(double2) + (size_t)dim * (2 * sizeof(int) + n) + 256;
+  void* work = nullptr;
+  if (cudaMalloc(&work, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GCAMPS_ENOMEM, "statevector workspace");
+  }
+  int32_t* ys_dev = nullptr;
+  double2* out = nullptr;
+  cudaError_t ce = cudaMalloc(&out, (size_t)nys * sizeof(double2));
+  if (ce == cudaSuccess && ys) ce = cudaMalloc(&ys_dev, (size_t)nys * sizeof(int32_t));
+  if (ce == cudaSuccess && ys)
+    ce = cudaMemcpyAsync(ys_dev, ys, (size_t)nys * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess) ce = gcx::launch_statevector(h->e, circuit, out, dim, ys_dev, nys, work, h->stream);
+  std::vector<double2> host((size_t)nys);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(host.data(), out, (size_t)nys * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  cudaFree(work);
+  if (out) cudaFree(out);
+  if (ys_dev) cudaFree(ys_dev);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "statevector");
+  for (long long i = 0; i < nys; ++i) {
+    re[i] = host[(size_t)i].x;
+    im[i] = host[(size_t)i].y;
+  }
+  return device_status(h);
+}
+
+int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!re || !im) return fail(h, GCAMPS_EINVAL, "null output");
+  long long dim = 1;
+  for (int j = 0; j < h->e.n; ++j) {
+    dim *= h->e.d;
+    if (dim > (1LL << 20)) return fail(h, GCAMPS_EINVAL, "d^n above 2^20: dense readout not supported");
+  }
+  return statevector_impl(h, circuit, nullptr, dim, re, im);
+}
+
+int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!digits || !re || !im) return fail(h, GCAMPS_EINVAL, "null argument");
+  long long y = 0;
+  for (int j = 0; j < h->e.n; ++j) {
+    if (digits[j] < 0 || digits[j] >= h->e.d) return fail(h, GCAMPS_EINVAL, "digit out of range");
+    y = y * h->e.d + digits[j];
+    if (y > (1LL << 30)) return fail(h, GCAMPS_EINVAL, "d^n above 2^20: dense readout not supported");
+  }
+  const int32_t yy = (int32_t)y;
+  return statevector_impl(h, circuit, &yy, 1, re, im);
+}
+
+int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  const int n = h->e.n;
+  const uint8_t* t = h->e.tab + (long long)circuit * h->e.tab_stride;
+  if (exps) GC_CUDA(h, cudaMemcpyAsync(exps, t, 4 * n * n, cudaMemcpyDeviceToHost, h->stream));
+  if (phase) GC_CUDA(h, cudaMemcpyAsync(phase, t + 4 * n * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return device_status(h);
+}
+
+int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  const int n = h->e.n;
+  const uint8_t* t = h->e.tab + (long long)circuit * h->e.tab_stride + 4 * n * n + 2 * n;
+  if (exps) GC_CUDA(h, cudaMemcpyAsync(exps, t, 4 * n * n, cudaMemcpyDeviceToHost, h->stream));
+  if (phase) GC_CUDA(h, cudaMemcpyAsync(phase, t + 4 * n * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return device_status(h);
+}
+
+int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!chi) return fail(h, GCAMPS_EINVAL, "null output");
+  const int n = h->e.n;
+  std::vector<int> dims(n + 1);
+  GC_CUDA(h, cudaMemcpyAsync(dims.data(), h->e.dims + (long long)circuit * (n + 1), (n + 1) * sizeof(int),
+                             cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < n - 1; ++j) chi[j] = dims[j + 1];
+  return device_status(h);
+}
+
+int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!s || !count || bond < 0 || bond >= h->e.n - 1) return fail(h, GCAMPS_EINVAL, "bad bond or null output");
+  if (!h->schmidt_dev) GC_CUDA(h, cudaMalloc(&h->schmidt_dev, (size_t)(h->e.d * h->e.maxdim + 64) * sizeof(double)));
+  GC_CUDA(h, gcx::launch_schmidt(h->e, circuit, bond, h->schmidt_dev, h->cnt_dev, h->stream));
+  int cnt = 0;
+  GC_CUDA(h, cudaMemcpyAsync(&cnt, h->cnt_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  GC_CUDA(h, cudaMemcpy(s, h->schmidt_dev, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost));
+  *count = cnt;
+  return device_status(h);
+}
+
+int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  const int n = h->e.n;
+  std::vector<int8_t> w(2 * n);
+  std::vector<int> meta(gcx::M_COUNT);
+  GC_CUDA(h, cudaMemcpyAsync(w.data(), h->e.weyl + (long long)circuit * 2 * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(meta.data(), h->e.meta + (long long)circuit * gcx::M_COUNT, gcx::M_COUNT * sizeof(int),
+                             cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < n; ++j) {
+    if (x) x[j] = w[j];
+    if (z) z[j] = w[n + j];
+  }
+  if (r) *r = meta[gcx::M_WEYL_R];
+  return device_status(h);
+}
+
+int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!st) return fail(h, GCAMPS_EINVAL, "null output");
+  long long s[gcx::S_COUNT];
+  double ds[2];
+  int meta[gcx::M_COUNT];
+  GC_CUDA(h, cudaMemcpyAsync(s, h->e.stats + (long long)circuit * gcx::S_COUNT, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(ds, h->e.dstats + (long long)circuit * 2, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(meta, h->e.meta + (long long)circuit * gcx::M_COUNT, sizeof meta, cudaMemcpyDeviceToHost,
+                             h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  st->t_gates = s[gcx::S_T];
+  st->clifford_gates = s[gcx::S_CLIFF];
+  st->bonds_visited = s[gcx::S_BONDS];
+  st->candidates_scored = s[gcx::S_CANDS];
+  st->accepted = s[gcx::S_ACC];
+  st->sweeps = s[gcx::S_SWEEPS];
+  st->max_chi = (int32_t)s[gcx::S_MAXCHI];
+  st->status = meta[gcx::M_STATUS];
+  st->discarded_weight = ds[0];
+  st->scoring_flops = ds[1];
+  return device_status(h);
+}
+
+int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, int32_t* count) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!count || cap < 0 || (cap > 0 && !pairs)) return fail(h, GCAMPS_EINVAL, "bad output");
+  int meta[gcx::M_COUNT];
+  GC_CUDA(h, cudaMemcpyAsync(meta, h->e.meta + (long long)circuit * gcx::M_COUNT, sizeof meta, cudaMemcpyDeviceToHost,
+                             h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int nd = meta[gcx::M_NDEC];
+  *count = nd;
+  const int ncopy = std::min(std::min(nd, (int)cap), gcx::kDecCap);
+  if (ncopy > 0)
+    GC_CUDA(h, cudaMemcpy(pairs, h->e.dec + (long long)circuit * gcx::kDecCap * 2, (size_t)ncopy * 2 * sizeof(int),
+                          cudaMemcpyDeviceToHost));
+  return device_status(h);
+}
+
+}  // extern "C"

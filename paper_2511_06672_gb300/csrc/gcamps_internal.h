@@ -1,0 +1,71 @@
+// Internal layout shared by the host side (gcamps_host.cpp) and the device engine
+// (gcamps_engine.cu) of libgcamps.  Not part of the public C ABI (include/gcamps.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gcamps.h"
+
+namespace gcx {
+
+constexpr int kThreads = 256;             // threads per CTA; one CTA runs one circuit
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxN = 128;                // qudits per circuit
+constexpr int kMaxK = 90;                 // disentangler classes (d = 3)
+constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
+
+// meta[] words per circuit
+enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_COUNT };
+// stats[] counters per circuit (int64)
+enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_COUNT };
+
+// Scratch areas of one circuit, as element offsets (double2) from its scratch base.
+struct ScratchLayout {
+  long long theta;   // two-site tensor / MPO output staging         [tcap]
+  long long b;       // Jacobi working matrix                          [tcap]
+  long long w;       // accumulated Jacobi rotations                   [wcap]
+  long long u;       // left factor                                    [tcap]
+  long long vh;      // right factor                                   [tcap]
+  long long tmp;     // matmul staging                                 [tcap]
+  long long warp;    // per-warp scoring scratch, kWarps x warp_stride
+  long long warp_stride;
+  long long total;   // elements per circuit
+};
+
+struct Engine {
+  int n, d, K, chi_max, batch, max_sweeps, maxdim;
+  double cutoff, tie_tol, strict_weight;
+  long long tcap;                 // elements of the largest two-site matrix
+  long long wcap;                 // elements of the largest Jacobi rotation matrix
+  // per-circuit state, circuit c at base + c * stride
+  uint8_t* tab;     long long tab_stride;   // fwd exps | fwd phase | inv exps | inv phase
+  double2* mps;     long long mps_stride;   // site slots
+  const long long* site_off;                // [n] slot offsets (shared by all circuits)
+  const int* bond_bound;                    // [n+1] Schmidt-rank bound d^min(b, n-b) of bond b
+  int* dims;                                // [batch][n+1]
+  int* meta;                                // [batch][M_COUNT]
+  long long* stats;                         // [batch][S_COUNT]
+  double* dstats;                           // [batch][2]: discarded weight, spare
+  int* dec;                                 // [batch][kDecCap][2]
+  int8_t* weyl;                             // [batch][2n]
+  double2* scr;     ScratchLayout sl;       // per-circuit scratch, stride sl.total
+  double* sing;     long long sing_stride;  // singular values / eigenvalues
+  int* iscr;        long long iscr_stride;  // permutation scratch
+  const double2* candU;                     // [K][d^4] class unitaries, row-major
+  const int32_t* candImg;                   // [K][20] class images
+};
+
+// Host -> device entry points implemented in gcamps_engine.cu.
+cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev,
+                       cudaStream_t st);
+cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st);
+cudaError_t launch_reset(const Engine& e, cudaStream_t st);
+cudaError_t launch_expect(const Engine& e, int circuit, const int8_t* xz_dev, double2* out_dev,
+                          cudaStream_t st);
+cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, long long dim,
+                               const int32_t* ys_dev, long long nys, void* work, cudaStream_t st);
+cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
+                           cudaStream_t st);
+
+}  // namespace gcx

@@ -1,0 +1,90 @@
+"""CPU checks of libgcamps: it builds for sm_103a, exports every symbol include/gcamps.h
+declares, and its host-only tables (no GPU call) agree bit-exactly with the oracle:
+
+* gcamps_sp4_images: the seeded-circuit gate (index into lexicographic Sp(4, F_d), Weyl shift)
+  -> generator images, vs oracle.clifford.random_gate_images;
+* gcamps_candidate: the 20 / 90 disentangler classes (order, images, unitaries) vs
+  oracle.clifford.candidates.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_06672_gb300.build import build_library
+    from paper_2511_06672_gb300 import _native
+    build_library()
+    return _native.load()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "gcamps.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gcamps_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_match_header(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2511_06672_gb300._native import EXPORTS
+    assert sorted(EXPORTS) == names
+
+
+def test_num_candidates(lib):
+    assert lib.gcamps_num_candidates(2) == 20
+    assert lib.gcamps_num_candidates(3) == 90
+    assert lib.gcamps_num_candidates(5) == -1
+
+
+def _imgs_to_array(imgs):
+    out = []
+    for w in imgs:
+        out.extend([int(w.x[0]), int(w.z[0]), int(w.x[1]), int(w.z[1]), int(w.r)])
+    return np.array(out, dtype=np.int32)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_sp4_images_match_oracle(lib, d):
+    from oracle import clifford
+    import paper_2511_06672_gb300 as G
+    rng = np.random.default_rng(100 + d)
+    order = len(clifford.sp_group(2, d))
+    for idx in list(rng.integers(0, order, 60)) + [0, order - 1]:
+        shift = tuple(int(a) for a in rng.integers(0, d, 4))
+        got = G.sp4_images(d, int(idx), shift)
+        want = _imgs_to_array(clifford.random_gate_images(int(idx), shift, d))
+        assert np.array_equal(got, want), (idx, shift)
+    with pytest.raises(G.GcampsError):
+        G.sp4_images(d, order, (0, 0, 0, 0))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_candidates_match_oracle(lib, d):
+    from oracle import clifford
+    import paper_2511_06672_gb300 as G
+    cands = clifford.candidates(d)
+    assert G.num_candidates(d) == len(cands)
+    for k, (_s, imgs, u) in enumerate(cands):
+        img, ug = G.candidate(d, k)
+        assert np.array_equal(img, _imgs_to_array(imgs)), k
+        assert np.allclose(ug, u, atol=1e-12), k
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    """With no CUDA device the create call returns an error code instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    rc = lib.gcamps_create(4, 3, 8, None, C.byref(h))
+    assert rc != 0 and not h.value

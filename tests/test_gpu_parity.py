@@ -1,0 +1,266 @@
+"""GPU parity of libgcamps against the FP64 oracle, through the C ABI.
+
+Bars (fixed before measuring):
+* tableau (forward and inverse), Weyl strings, bond dimensions, disentangler decisions:
+  bit-exact / identical;
+* state vector (d^n <= 6561): relative 2-norm error <= 1e-10 after the best global phase
+  (a Clifford given by its generator images has no defined global phase);
+* <W> for Weyl strings, Schmidt values: absolute error <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import clifford, statevector as sv
+from oracle.gcamps import GCAMPS
+from oracle.weyl import Weyl
+from synth import brickwork_circuit, t_gate_phases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    return G
+
+
+def oracle_run(gates, n, d, chi_max, cutoff, max_sweeps=8):
+    g = GCAMPS(n, d, chi_max=chi_max, cutoff=cutoff, max_sweeps=max_sweeps)
+    for gt in gates:
+        g.apply_gate(gt)
+        if not hasattr(gt, "sp_index"):
+            g.disentangle()
+    return g
+
+
+def gpu_run(G, gates, n, d, chi_max, cutoff, max_sweeps=8):
+    sim = G.Simulator(n, d, chi_max=chi_max, cutoff=cutoff, max_sweeps=max_sweeps)
+    sim.run(G.ops_from_gates(gates, d))
+    sim.sync()
+    return sim
+
+
+def inverse_exps(tab):
+    rows = tab.inverse_rows()
+    n = tab.n
+    e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
+    p = np.zeros(2 * n, dtype=np.uint8)
+    for k, w in enumerate(rows):
+        e[k, :n] = w.x
+        e[k, n:] = w.z
+        p[k] = w.r
+    return e, p
+
+
+def assert_same_tableaux(sim, ref):
+    e, p = sim.tableau()
+    re_, rp = ref.tab.exps_phase()
+    assert np.array_equal(e, re_)
+    assert np.array_equal(p, rp)
+    ie, ip = sim.inverse_tableau()
+    rie, rip = inverse_exps(ref.tab)
+    assert np.array_equal(ie, rie)
+    assert np.array_equal(ip, rip)
+
+
+@pytest.mark.parametrize("d,n,seed", [(2, 6, 1), (3, 5, 2), (3, 9, 3), (2, 13, 4)])
+def test_clifford_only_tableau_bit_exact(G, d, n, seed):
+    gates = brickwork_circuit(n, d, 2 * n, 0, seed)
+    sim = gpu_run(G, gates, n, d, 8, 1e-12)
+    ref = oracle_run(gates, n, d, 8, 1e-12)
+    assert_same_tableaux(sim, ref)
+    assert sim.stats()["clifford_gates"] == len(gates)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_single_qudit_cliffords(G, d):
+    n = 4
+    sim = G.Simulator(n, d, chi_max=8)
+    ref = GCAMPS(n, d, chi_max=8)
+    rng = np.random.default_rng(d)
+    one = [clifford.H_gate(d), clifford.S_gate(d)]
+    for step in range(30):
+        if step % 3 == 2:
+            gates = brickwork_circuit(n, d, 1, 0, 50 + step)
+            for g in gates:
+                sim.apply_clifford(g.q0, g.q1, G.sp4_images(d, g.sp_index, g.shift))
+                ref.apply_gate(g)
+            continue
+        u = one[rng.integers(2)]
+        q = int(rng.integers(n))
+        imgs = clifford.images_by_conjugation(u, 1, d)
+        flat = [int(imgs[0].x[0]), int(imgs[0].z[0]), imgs[0].r, int(imgs[1].x[0]), int(imgs[1].z[0]), imgs[1].r]
+        sim.apply_clifford(q, -1, flat)
+        ref.apply_clifford([q], imgs)
+    sim.sync()
+    assert_same_tableaux(sim, ref)
+
+
+@pytest.mark.parametrize("d,n,seed", [(2, 8, 7), (3, 8, 8)])
+def test_weyl_string_of_t_gate(G, d, n, seed):
+    """P = C^dag Z_k C from the inverse-tableau row vs Gaussian elimination (Sec. 2.3.1)."""
+    gates = brickwork_circuit(n, d, n, 0, seed)
+    sim = G.Simulator(n, d, chi_max=32, max_sweeps=0)
+    sim.run(G.ops_from_gates(gates, d))
+    ref = GCAMPS(n, d, chi_max=32)
+    for g in gates:
+        ref.apply_gate(g)
+    for k in range(n):
+        want = ref.weyl_of_z(k)
+        sim.apply_nonclifford(k, [0.0] * d)   # identity gate: only the Weyl string is recorded
+        r, x, z = sim.last_weyl()
+        assert r == want.r and np.array_equal(x, want.x) and np.array_equal(z, want.z), k
+
+
+@pytest.mark.parametrize("d,n,layers,t,seed", [(3, 8, 8, 8, 1), (3, 8, 8, 8, 2), (2, 8, 8, 8, 1),
+                                               (3, 6, 10, 12, 3), (2, 10, 10, 10, 5)])
+def test_small_circuits_vs_dense_and_oracle(G, d, n, layers, t, seed):
+    gates = brickwork_circuit(n, d, layers, t, seed)
+    sim = gpu_run(G, gates, n, d, 64, 1e-14)
+    ref = oracle_run(gates, n, d, 64, 1e-14)
+    assert sim.decisions() == ref.decisions
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    assert_same_tableaux(sim, ref)
+    psi = sv.run(gates, n, d)
+    err, _ = sv.same_up_to_phase(sim.statevector(), psi)
+    assert err < TOL
+    rng = np.random.default_rng(seed)
+    for _ in range(5):
+        x, z = rng.integers(0, d, n), rng.integers(0, d, n)
+        want = sv.expect_weyl(psi, Weyl(0, x, z, d), n, d)
+        assert abs(sim.expect_weyl(x, z) - want) < TOL
+    z0 = np.zeros(n, dtype=np.int64)
+    z0[0] = 1
+    assert abs(sim.expect_weyl(np.zeros(n, dtype=np.int64), z0) - sv.expect_weyl(psi, Weyl(0, np.zeros(n), z0, d), n, d)) < TOL
+    st = sim.stats()
+    assert st["t_gates"] == t and st["status"] == 0
+    assert st["candidates_scored"] == ref.candidates_scored
+
+
+def test_config1_full_amplitudes(G):
+    """Plain FP64, qutrits, n = 8, 8 layers, 8 T gates, chi_max = 64, no truncation: the full
+    6561-amplitude vector and <Z_0> against dense simulation."""
+    d, n = 3, 8
+    gates = brickwork_circuit(n, d, 8, 8, 1)
+    sim = gpu_run(G, gates, n, d, 64, 1e-14)
+    psi = sv.run(gates, n, d)
+    v = sim.statevector()
+    err, ph = sv.same_up_to_phase(v, psi)
+    assert err < TOL
+    for y in (0, 1, 100, 3280, 6560):
+        digits = [(y // d ** (n - 1 - j)) % d for j in range(n)]
+        assert abs(sim.amplitude(digits) * ph - psi[y]) < TOL
+
+
+def test_no_disentangling_exact_and_chi_growth(G):
+    d, n = 3, 6
+    gates = brickwork_circuit(n, d, 6, 6, 4)
+    sim = gpu_run(G, gates, n, d, 243, 1e-14, max_sweeps=0)
+    ref = oracle_run(gates, n, d, 243, 1e-14, max_sweeps=0)
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    assert max(sim.bond_dims()) > 3
+    err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
+    assert err < TOL
+
+
+def test_truncation_matches_oracle(G):
+    """chi_max binds (d = 3, chi_max = 3): both sides truncate the same way."""
+    d, n = 3, 7
+    gates = brickwork_circuit(n, d, 7, 10, 6)
+    sim = gpu_run(G, gates, n, d, 3, 1e-12, max_sweeps=0)
+    ref = oracle_run(gates, n, d, 3, 1e-12, max_sweeps=0)
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    assert max(sim.bond_dims()) == 3
+    err, _ = sv.same_up_to_phase(sim.statevector(), ref.statevector())
+    assert err < 1e-9
+    assert abs(sim.stats()["discarded_weight"] - ref.discarded) < 1e-10
+
+
+@pytest.mark.parametrize("d", [3, 2])
+def test_full_size_benchmark_circuit(G, d):
+    """The benchmark workload itself (n = 32, 24 layers, 32 T gates, chi_max = 256, cutoff 1e-12,
+    seed 1): every decision, the tableaux, bond dimensions, Schmidt values and <W> against the
+    oracle run of the same circuit."""
+    n, layers, t, chi, cut = 32, 24, 32, 256, 1e-12
+    gates = brickwork_circuit(n, d, layers, t, 1)
+    sim = gpu_run(G, gates, n, d, chi, cut)
+    ref = oracle_run(gates, n, d, chi, cut)
+    assert sim.decisions() == ref.decisions
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    assert_same_tableaux(sim, ref)
+    for b in range(0, n - 1, 5):
+        s = sim.schmidt_values(b)
+        s = s[s > 1e-13]
+        want = ref.mps.schmidt_values(b)
+        want = want[want > 1e-13]
+        assert len(s) == len(want) and np.max(np.abs(s - want)) < TOL
+    rng = np.random.default_rng(d)
+    for _ in range(4):
+        x, z = np.zeros(n, dtype=np.int64), np.zeros(n, dtype=np.int64)
+        sites = rng.choice(n, 3, replace=False)
+        x[sites] = rng.integers(0, d, 3)
+        z[sites] = rng.integers(0, d, 3)
+        assert abs(sim.expect_weyl(x, z) - ref.expect_weyl(x, z)) < TOL
+    st = sim.stats()
+    assert st["t_gates"] == t and st["candidates_scored"] == ref.candidates_scored
+
+
+def test_batch_matches_single_runs(G):
+    d, n = 3, 10
+    circuits = [brickwork_circuit(n, d, 8, 10, s) for s in (11, 12, 13)]
+    ops = [G.ops_from_gates(c, d) for c in circuits]
+    begin = np.cumsum([0] + [len(o) for o in ops]).astype(np.int32)
+    sim = G.Simulator(n, d, chi_max=32, cutoff=1e-12, batch=3)
+    sim.run(np.concatenate(ops), begin)
+    sim.sync()
+    for c, gates in enumerate(circuits):
+        ref = oracle_run(gates, n, d, 32, 1e-12)
+        assert sim.decisions(c) == ref.decisions
+        e, p = sim.tableau(c)
+        re_, rp = ref.tab.exps_phase()
+        assert np.array_equal(e, re_) and np.array_equal(p, rp)
+        assert sim.bond_dims(c) == ref.mps.bond_dims()
+
+
+def test_invalid_input_leaves_handle_usable(G):
+    d, n = 3, 4
+    sim = G.Simulator(n, d, chi_max=8)
+    bad = np.array(G.sp4_images(d, 5, (0, 0, 0, 0)))
+    bad[0] = (bad[0] + 1) % d                         # breaks the symplectic form
+    with pytest.raises(G.GcampsError) as ei:
+        sim.apply_clifford(0, 1, bad)
+    assert ei.value.code == 1
+    with pytest.raises(G.GcampsError):
+        sim.apply_clifford(0, 0, G.sp4_images(d, 5, (0, 0, 0, 0)))
+    with pytest.raises(G.GcampsError):
+        sim.apply_nonclifford(n, t_gate_phases(d))
+    odd_phase = np.array(G.sp4_images(d, 5, (0, 0, 0, 0)))
+    odd_phase[4] = 1                                   # tau^1 is not a power of omega for d = 3
+    with pytest.raises(G.GcampsError):
+        sim.apply_clifford(0, 1, odd_phase)
+    sim.apply_clifford(0, 1, G.sp4_images(d, 5, (1, 0, 0, 2)))
+    sim.apply_nonclifford(1, t_gate_phases(d))
+    sim.disentangle()
+    sim.sync()
+    assert sim.stats()["status"] == 0
+
+
+def test_reset(G):
+    d, n = 3, 6
+    gates = brickwork_circuit(n, d, 6, 6, 21)
+    sim = gpu_run(G, gates, n, d, 32, 1e-12)
+    sim.reset()
+    e, p = sim.tableau()
+    assert np.array_equal(e, GCAMPS(n, d, 8).tab.exps_phase()[0]) and not p.any()
+    assert sim.bond_dims() == [1] * (n - 1)
+    assert sim.stats()["t_gates"] == 0
+    sim.run(G.ops_from_gates(gates, d))
+    ref = oracle_run(gates, n, d, 32, 1e-12)
+    assert sim.decisions() == ref.decisions
