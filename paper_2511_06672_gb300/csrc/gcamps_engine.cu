@@ -128,6 +128,17 @@ __device__ void set_status(const Ctx& C, int code) {
   if (C.meta[M_STATUS] == 0) C.meta[M_STATUS] = code;
 }
 
+// First failure of a circuit: which routine (1 = Jacobi SVD, 2 = tridiagonal eigenvalues) and the
+// matrix shape it had, for gcamps_last_error.
+__device__ void set_failure(const Ctx& C, int code, int where, int a, int b) {
+  if (C.meta[M_STATUS] == 0) {
+    C.meta[M_STATUS] = code;
+    C.meta[M_DIAG_WHERE] = where;
+    C.meta[M_DIAG_A] = a;
+    C.meta[M_DIAG_B] = b;
+  }
+}
+
 __device__ double block_sum(double v, Smem& s) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -337,12 +348,18 @@ __device__ void fold_candidate(Smem& s, const Ctx& C, int k, int q0) {
 // Orthogonalises the n columns of B (m x n, column-major) by complex Jacobi rotations applied
 // from the right, accumulating them in W (n x n, column-major, starts as I):  B_in W = B_out.
 // Round-robin ordering: in each round the n/2 column pairs are disjoint and handled by the
-// warps in parallel.  A pair is rotated while |b_i^H b_j| > tol * |b_i| |b_j|.  Returns the number
-// of sweeps, or -1 if `max_sweeps` were not enough.
+// warps in parallel.  A pair is rotated while |b_i^H b_j| > tol * |b_i| |b_j|, unless one of the
+// two columns is numerically zero (|b|^2 <= 1e-30 |B|_F^2): the direction of such a column is
+// rounding noise, rotating it never settles, and its singular value lies below any truncation
+// cutoff.  Returns the number of sweeps, or -1 if `max_sweeps` were not enough.
 __device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* W, int max_sweeps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (long long i = threadIdx.x; i < (long long)n * n; i += blockDim.x)
     W[i] = ((i % n) == (i / n)) ? make_double2(1.0, 0.0) : cz();
+  double fro = 0;
+  for (long long i = threadIdx.x; i < (long long)m * n; i += blockDim.x) fro += cabs2(B[i]);
+  fro = block_sum(fro, s);
+  const double zero_col = 1e-30 * fro;
   if (threadIdx.x == 0) s.flag = 0;
   __syncthreads();
   if (n <= 1) return 0;
@@ -371,6 +388,7 @@ __device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* 
         gr = warp_sum(gr);
         gi = warp_sum(gi);
         const double g = hypot(gr, gi);
+        if (al <= zero_col || be <= zero_col) continue;
         if (!(g > tol * sqrt(al) * sqrt(be)) || g < 1e-300) continue;
         const double zeta = (be - al) / (2.0 * g);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
@@ -460,7 +478,7 @@ __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, 
   }
   __syncthreads();
   const int sweeps = jacobi_orthogonalize(s, B, m, n, W, 60);
-  if (sweeps < 0 && threadIdx.x == 0) set_status(C, GCAMPS_ENOCONV);
+  if (sweeps < 0 && threadIdx.x == 0) set_failure(C, GCAMPS_ENOCONV, 1, rows, cols);
   sorted_column_norms(B, m, n, svt, sing, perm);
   // rank rule
   if (threadIdx.x == 0) {
@@ -708,8 +726,14 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
 
 // ---------------------------------------------------------- candidate scoring (warp level)
 // Householder reduction of a Hermitian m x m matrix (row-major, full storage, overwritten) to a
-// real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).
+// real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).  A column whose entries below
+// the subdiagonal are below 1e-16 |A|_F is taken as already reduced: reflecting such a column
+// underflows (h ~ |x|^2) and would poison the matrix, while dropping it moves eigenvalues by at
+// most that much.
 __device__ void warp_tridiag(double2* A, int m, double* dg, double* od, int lane) {
+  double fro2 = 0;
+  for (int idx = lane; idx < m * m; idx += 32) fro2 += cabs2(A[idx]);
+  fro2 = warp_sum(fro2);
   for (int k = 0; k + 2 < m; ++k) {
     const int r = m - k - 1;
     double nrm2 = 0;
@@ -720,7 +744,7 @@ __device__ void warp_tridiag(double2* A, int m, double* dg, double* od, int lane
     if (lane == 0) dg[k] = A[(long long)k * m + k].x;
     __syncwarp();
     const double alpha = sqrt(nrm2);
-    if (nrm2 == 0.0 || nrm2 - ax0 * ax0 <= 1e-30 * nrm2) {
+    if (nrm2 - ax0 * ax0 <= 1e-32 * fro2) {
       if (lane == 0) od[k] = ax0;
       __syncwarp();
       continue;
@@ -893,7 +917,7 @@ __device__ void visit_bond(Smem& s, const Ctx& C, int i, bool ltr, int* accepted
     const double sc = score_candidate(C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, &ok);
     if ((threadIdx.x & 31) == 0) {
       s.scores[k] = sc;
-      if (!ok) set_status(C, GCAMPS_ENOCONV);
+      if (!ok) set_failure(C, GCAMPS_ENOCONV, 2, cl * d, d * cr);
     }
   }
   __syncthreads();

@@ -392,11 +392,15 @@ int device_status(gcamps_t* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "device status");
   for (int c = 0; c < h->e.batch; ++c) {
-    const int s = meta[(size_t)c * gcx::M_COUNT + gcx::M_STATUS];
+    const int* mc = &meta[(size_t)c * gcx::M_COUNT];
+    const int s = mc[gcx::M_STATUS];
     if (s) {
-      char buf[128];
-      snprintf(buf, sizeof buf, "device status %d on circuit %d (%s)", s, c,
-               s == GCAMPS_ENOCONV ? "iteration cap reached" : "chi_max bound");
+      char buf[192];
+      const int where = mc[gcx::M_DIAG_WHERE];
+      snprintf(buf, sizeof buf, "device status %d on circuit %d (%s; %s, matrix %d x %d)", s, c,
+               s == GCAMPS_ENOCONV ? "iteration cap reached" : (s == GCAMPS_ECHI ? "chi_max bound" : "invalid state"),
+               where == 1 ? "Jacobi SVD" : (where == 2 ? "tridiagonal eigenvalues" : "-"), mc[gcx::M_DIAG_A],
+               mc[gcx::M_DIAG_B]);
       return fail(h, s, buf);
     }
   }

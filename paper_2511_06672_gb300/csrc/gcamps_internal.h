@@ -16,7 +16,8 @@ constexpr int kMaxK = 90;                 // disentangler classes (d = 3)
 constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
 
 // meta[] words per circuit
-enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_COUNT };
+enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_DIAG_WHERE, M_DIAG_A, M_DIAG_B,
+            M_COUNT };
 // stats[] counters per circuit (int64)
 enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_COUNT };
 
