@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -185,13 +186,19 @@ def main():
     import paper_2511_06672_gb300 as G
 
     stream = torch.cuda.Stream()
+    streams = {2: torch.cuda.Stream(), 3: torch.cuda.Stream()}   # the two handles run concurrently
     sims, ops_host, ops_dev, begin_dev = {}, {}, {}, {}
     for d in (2, 3):
-        sims[d] = G.Simulator(N, d, chi_max=CHI, cutoff=CUTOFF, batch=SEEDS_PER_D, stream=stream)
+        sims[d] = G.Simulator(N, d, chi_max=CHI, cutoff=CUTOFF, batch=SEEDS_PER_D, stream=streams[d],
+                              cluster_size=args.cluster)
         o, b = workload_ops(G, d, rank)
-        ops_host[d] = (o, b)
+        # e2e inputs live in pinned host memory
+        o_pin = torch.from_numpy(o.view(np.uint8).copy()).pin_memory().numpy().view(G.OP_DTYPE)
+        b_pin = torch.from_numpy(b.copy()).pin_memory().numpy()
+        ops_host[d] = (o_pin, b_pin)
         ops_dev[d] = torch.from_numpy(o.view(np.uint8)).to(f"cuda:{local}")
         begin_dev[d] = torch.from_numpy(b).to(f"cuda:{local}")
+    torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
     lib = G._native.load()
@@ -199,20 +206,27 @@ def main():
 
     def launch_all(events=None):
         """One step: back to |0...0> and C = I, then the full gate list of every circuit (one
-        engine launch per d), all enqueued on `stream`.  `events`: optional list of
-        (start, end) CUDA-event pairs recorded around each engine launch."""
+        engine launch per d).  The qubit and qutrit handles run on their own streams, forked from
+        and joined back into `stream`.  `events`: optional (start, end) CUDA-event pairs recorded
+        around each engine launch on its stream."""
+        fork = torch.cuda.Event()
+        fork.record(stream)
         for i, d in enumerate((2, 3)):
             s = sims[d]
+            streams[d].wait_event(fork)
             rc = lib.gcamps_reset(s._h)
             if events is not None:
-                events[i][0].record(stream)
+                events[i][0].record(streams[d])
             if rc == 0:
                 rc = lib.gcamps_run_device(s._h, C.c_void_p(ops_dev[d].data_ptr()),
                                            C.c_void_p(begin_dev[d].data_ptr()))
             if events is not None:
-                events[i][1].record(stream)
+                events[i][1].record(streams[d])
             if rc:
                 raise RuntimeError(lib.gcamps_last_error(s._h).decode())
+            join = torch.cuda.Event()
+            join.record(streams[d])
+            stream.wait_event(join)
 
     # warm-up (also checks status)
     for _ in range(args.warmup):
@@ -256,6 +270,7 @@ def main():
     cand_per_step = sum(st["candidates_scored"] for d in (2, 3) for st in stats[d])
     value = tg_per_step * args.steps * world / total_time
     cand_rate = cand_per_step * args.steps * world / total_time
+    vn_frac = sum(st["vn_evaluations"] for d in (2, 3) for st in stats[d]) / max(1, cand_per_step)
     flops_per_launch = sum(st["scoring_flops"] for d in (2, 3) for st in stats[d]) / 2.0
     launch_s = sum(engine_times) / len(engine_times)
     achieved = flops_per_launch / launch_s / 1e12
@@ -288,8 +303,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "layers": LAYERS, "t_gates": T, "chi_max": CHI,
                    "cutoff": CUTOFF, "d": [2, 3], "circuits_per_rank": 2 * SEEDS_PER_D,
-                   "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}"},
+                   "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}",
+                   "cluster_ctas_per_circuit": args.cluster},
         "candidates_per_s": cand_rate,
+        "vn_evaluated_fraction": vn_frac,
         "e2e": {"value": e2e_value, "unit": "T-gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * 2 * args.steps,
         "roofline": roofline,

@@ -56,6 +56,7 @@ typedef struct {
   double tie_tol;      /* accept Q only if S(Q) < S(I) - tie_tol; ties -> lowest index (1e-10) */
   double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
+  int cluster_size;    /* CTAs (one thread-block cluster) per circuit: 1, 2, 4, 8 or 16; 0 = 8   */
 } gcamps_opts;
 
 /* Per-circuit counters since creation (or gcamps_reset). */
@@ -66,14 +67,17 @@ typedef struct {
   int64_t candidates_scored;  /* (bond, class) entanglement scores evaluated                */
   int64_t accepted;           /* disentanglers applied                                      */
   int64_t sweeps;             /* disentangling sweeps                                       */
+  int64_t vn_evaluations;     /* exact von Neumann entropies computed (the others were      */
+                              /* excluded by the Renyi-2 lower bound S2 <= S_vN)            */
   int32_t max_chi;            /* largest bond dimension seen after any truncation           */
   int32_t status;             /* sticky device status: 0 or a GCAMPS_E* code                */
   double discarded_weight;    /* sum of discarded s_i^2 over all truncations                */
   double scoring_flops;       /* algorithmic FP64 flops of candidate scoring (see below)    */
 } gcamps_stats;
 /* scoring_flops counts, per scored class at a bond with R = chi_l d rows and C = d chi_r
- * columns (m = min(R, C), M = max(R, C)): 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram)
- * + (16/3) m^3 (Householder tridiagonalisation); the eigenvalue iteration is not counted. */
+ * columns (m = min(R, C), M = max(R, C)): 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram),
+ * plus (16/3) m^3 (Householder tridiagonalisation) per exact von Neumann evaluation; the
+ * eigenvalue iteration is not counted. */
 
 /* One operation of a gate list (gcamps_run).  kind: */
 #define GCAMPS_OP_CLIFFORD 1     /* q0, q1 (-1 for one qudit), img as for apply_clifford   */

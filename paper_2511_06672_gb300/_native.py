@@ -19,12 +19,13 @@ assert OP_DTYPE.itemsize == 128
 class Opts(C.Structure):
     _fields_ = [("cutoff", C.c_double), ("max_sweeps", C.c_int), ("score_kind", C.c_int),
                 ("precision", C.c_int), ("tie_tol", C.c_double), ("strict_weight", C.c_double),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("cluster_size", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("t_gates", C.c_int64), ("clifford_gates", C.c_int64), ("bonds_visited", C.c_int64),
                 ("candidates_scored", C.c_int64), ("accepted", C.c_int64), ("sweeps", C.c_int64),
+                ("vn_evaluations", C.c_int64),
                 ("max_chi", C.c_int32), ("status", C.c_int32), ("discarded_weight", C.c_double),
                 ("scoring_flops", C.c_double)]
 

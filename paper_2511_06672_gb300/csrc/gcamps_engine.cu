@@ -16,6 +16,7 @@
 // All arithmetic on the MPS is complex128 (FP64), the precision the paper's simulator uses
 // (Sec. 4.1.2); the tableau is exact integer arithmetic mod d / mod 2d.
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -25,6 +26,11 @@
 
 namespace gcx {
 namespace {
+
+namespace cg = cooperative_groups;
+
+// Classes are scored with the Renyi-2 bound first when the Gram has more rows than this.
+constexpr int kPruneMin = 9;
 
 // ------------------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
@@ -71,7 +77,12 @@ struct Smem {
   int inv[20];                // images of its inverse
   uint8_t src[4][2 * kMaxN];  // rows read by a row product
   int srcr[4];
-  double scores[kMaxK];
+  double s2[kMaxK];           // Renyi-2 entropy per class (cluster leader)
+  double vn[kMaxK];           // von Neumann entropy per class (cluster leader)
+  uint8_t evald[kMaxK];       // vn[k] valid
+  int list[kMaxK];            // classes to evaluate next (cluster leader)
+  int nlist;
+  int bcast;
   double red[kWarps * 4];
   double2 coef[4];            // MPO term coefficients c_m tau^{...}
   double2 tau[6];             // tau^k, k < 2d
@@ -83,6 +94,8 @@ struct Smem {
 struct Ctx {
   const Engine* e;
   int c, n, d, K;
+  int rank, csize;            // position in the circuit's cluster; rank 0 leads
+  double2* cta;               // this CTA's scoring scratch
   uint8_t *fx, *fr, *ix, *ir;
   double2* mps;
   int* dims;
@@ -98,10 +111,13 @@ struct Ctx {
 
 __device__ __forceinline__ double2* site_ptr(const Ctx& C, int j) { return C.mps + C.e->site_off[j]; }
 
-__device__ Ctx make_ctx(const Engine& e, int c) {
+__device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   Ctx C;
   C.e = &e;
   C.c = c;
+  C.rank = rank;
+  C.csize = e.csize;
+  C.cta = e.cscr + ((long long)c * e.csize + rank) * e.cl.total;
   C.n = e.n;
   C.d = e.d;
   C.K = e.K;
@@ -724,67 +740,95 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
   __syncthreads();
 }
 
-// ---------------------------------------------------------- candidate scoring (warp level)
+// --------------------------------------------------------------- candidate scoring (Sec. 3)
+// The same routines run on a warp (small problems, one class per warp) or on a whole CTA (large
+// problems, one class per CTA); the group type supplies the thread index, barrier and reduction.
+struct WarpGroup {
+  int tid;
+  static constexpr int n = 32;
+  __device__ void sync() const { __syncwarp(); }
+  __device__ double sum(double v) const { return warp_sum(v); }
+  __device__ double bcast(double v) const { return __shfl_sync(0xffffffffu, v, 0); }
+};
+struct BlockGroup {
+  Smem* s;
+  int tid, n;
+  __device__ void sync() const { __syncthreads(); }
+  __device__ double sum(double v) const { return block_sum(v, *s); }
+  __device__ double bcast(double v) const {
+    __syncthreads();
+    if (tid == 0) s->dval[2] = v;
+    __syncthreads();
+    const double r = s->dval[2];
+    __syncthreads();
+    return r;
+  }
+};
+
 // Householder reduction of a Hermitian m x m matrix (row-major, full storage, overwritten) to a
 // real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).  A column whose entries below
 // the subdiagonal are below 1e-16 |A|_F is taken as already reduced: reflecting such a column
 // underflows (h ~ |x|^2) and would poison the matrix, while dropping it moves eigenvalues by at
-// most that much.
-__device__ void warp_tridiag(double2* A, int m, double* dg, double* od, int lane) {
+// most that much.  Column k below the diagonal keeps the reflector v, row k right of it p and w.
+template <class Grp>
+__device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, double* od) {
   double fro2 = 0;
-  for (int idx = lane; idx < m * m; idx += 32) fro2 += cabs2(A[idx]);
-  fro2 = warp_sum(fro2);
+  for (int idx = g.tid; idx < m * m; idx += g.n) fro2 += cabs2(A[idx]);
+  fro2 = g.sum(fro2);
   for (int k = 0; k + 2 < m; ++k) {
     const int r = m - k - 1;
     double nrm2 = 0;
-    for (int i = lane; i < r; i += 32) nrm2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
-    nrm2 = warp_sum(nrm2);
+    for (int i = g.tid; i < r; i += g.n) nrm2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
+    nrm2 = g.sum(nrm2);
     const double2 x0 = A[(long long)(k + 1) * m + k];
     const double ax0 = hypot(x0.x, x0.y);
-    if (lane == 0) dg[k] = A[(long long)k * m + k].x;
-    __syncwarp();
+    if (g.tid == 0) dg[k] = A[(long long)k * m + k].x;
+    g.sync();
     const double alpha = sqrt(nrm2);
     if (nrm2 - ax0 * ax0 <= 1e-32 * fro2) {
-      if (lane == 0) od[k] = ax0;
-      __syncwarp();
+      if (g.tid == 0) od[k] = ax0;
+      g.sync();
       continue;
     }
     const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
     const double h = alpha * (alpha + ax0);  // v^H v / 2
-    if (lane == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
-    __syncwarp();
-    // p = A_sub v / h, kept in row k
-    for (int i = lane; i < r; i += 32) {
+    if (g.tid == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+    g.sync();
+    const double hinv = 1.0 / h;
+    for (int i = g.tid; i < r; i += g.n) {
       double2 acc = cz();
       const double2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
       for (int j = 0; j < r; ++j) acc = cfma(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
-      A[(long long)k * m + k + 1 + i] = cscale(acc, 1.0 / h);
+      A[(long long)k * m + k + 1 + i] = cscale(acc, hinv);
     }
-    __syncwarp();
+    g.sync();
     double kr = 0;
-    for (int i = lane; i < r; i += 32) {
+    for (int i = g.tid; i < r; i += g.n) {
       const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
       kr += v.x * p.x + v.y * p.y;
     }
-    kr = warp_sum(kr) / (2.0 * h);
-    __syncwarp();
-    for (int i = lane; i < r; i += 32) {
+    kr = g.sum(kr) * 0.5 * hinv;
+    g.sync();
+    for (int i = g.tid; i < r; i += g.n) {
       const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
       A[(long long)k * m + k + 1 + i] = make_double2(p.x - kr * v.x, p.y - kr * v.y);
     }
-    __syncwarp();
-    for (int idx = lane; idx < r * r; idx += 32) {
+    g.sync();
+    for (int idx = g.tid; idx < r * r; idx += g.n) {
       const int i = idx / r, j = idx % r;
+      if (j > i) continue;
       const double2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
       const double2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
       const double2 t = cadd(cmul(vi, cconj(wj)), cmul(wi, cconj(vj)));
       double2* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
-      *a = csub(*a, t);
+      const double2 nv = csub(*a, t);
+      *a = nv;
+      if (j != i) A[(long long)(k + 1 + j) * m + (k + 1 + i)] = cconj(nv);
     }
-    if (lane == 0) od[k] = alpha;
-    __syncwarp();
+    if (g.tid == 0) od[k] = alpha;
+    g.sync();
   }
-  if (lane == 0) {
+  if (g.tid == 0) {
     if (m >= 2) {
       dg[m - 2] = A[(long long)(m - 2) * m + (m - 2)].x;
       const double2 e = A[(long long)(m - 1) * m + (m - 2)];
@@ -792,7 +836,7 @@ __device__ void warp_tridiag(double2* A, int m, double* dg, double* od, int lane
     }
     dg[m - 1] = A[(long long)(m - 1) * m + (m - 1)].x;
   }
-  __syncwarp();
+  g.sync();
 }
 
 // Eigenvalues of the symmetric tridiagonal (dg, od) by implicit QR steps with the Wilkinson
@@ -843,19 +887,25 @@ __device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
   return true;
 }
 
-// von Neumann entropy (natural log) of Q theta across (a, s) | (t, b), from the eigenvalues of the
-// Gram matrix on the smaller side.  Runs on one warp; every lane returns the value.
-__device__ double score_candidate(const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
-                                  double2* ws, bool* ok) {
-  const int lane = threadIdx.x & 31;
+struct Score {
+  double s2, vn;
+  bool ok;
+};
+
+// One class Q on theta: theta' = Q theta over (a, s) x (t, b); its Gram G on the smaller side (lower
+// triangle computed, mirrored); the Renyi-2 entropy S2 = -ln(|G|_F^2 / tr(G)^2); and, if asked, the
+// von Neumann entropy -sum p ln p from the eigenvalues of G (p = lambda / tr G).  S2 <= S_vN always.
+template <class Grp>
+__device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
+                             double2* ws, long long gram_off, bool want_vn) {
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
   double2* tp = ws;
-  double2* G = ws + C.e->tcap;
-  double* dg = reinterpret_cast<double*>(G + C.e->wcap);
+  double2* G = ws + gram_off;
+  double* dg = reinterpret_cast<double*>(G + (long long)m * m);
   double* od = dg + m;
-  for (long long idx = lane; idx < (long long)rows * cols; idx += 32) {
+  for (long long idx = g.tid; idx < (long long)rows * cols; idx += g.n) {
     const int rr = (int)(idx / cols), col = (int)(idx % cols);
     const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
     const double2* q = Q + (sd * d + t) * dd;
@@ -864,76 +914,175 @@ __device__ double score_candidate(const Ctx& C, const double2* theta, int cl, in
     for (int u = 0; u < dd; ++u) acc = cfma(q[u], th[(long long)u * cr], acc);
     tp[idx] = acc;
   }
-  __syncwarp();
-  if (rows <= cols) {
-    for (int idx = lane; idx < m * m; idx += 32) {
-      const int i = idx / m, j = idx % m;
+  g.sync();
+  double tr = 0, fro = 0;
+  for (int idx = g.tid; idx < m * m; idx += g.n) {
+    const int i = idx / m, j = idx % m;
+    if (j > i) continue;
+    double2 acc = cz();
+    if (rows <= cols) {
       const double2* ri = tp + (long long)i * cols;
       const double2* rj = tp + (long long)j * cols;
-      double2 acc = cz();
-      for (int c = 0; c < cols; ++c) acc = cfmac(rj[c], ri[c], acc);   // sum ri conj(rj)
-      G[idx] = acc;
-    }
-  } else {
-    for (int idx = lane; idx < m * m; idx += 32) {
-      const int i = idx / m, j = idx % m;
-      double2 acc = cz();
+      for (int c = 0; c < cols; ++c) acc = cfmac(rj[c], ri[c], acc);   // sum_c ri conj(rj)
+    } else {
       for (int r = 0; r < rows; ++r) acc = cfmac(tp[(long long)r * cols + i], tp[(long long)r * cols + j], acc);
-      G[idx] = acc;
+    }
+    G[idx] = acc;
+    if (i == j) {
+      tr += acc.x;
+      fro += acc.x * acc.x;
+    } else {
+      G[(long long)j * m + i] = cconj(acc);
+      fro += 2.0 * cabs2(acc);
     }
   }
-  __syncwarp();
-  warp_tridiag(G, m, dg, od, lane);
-  double ent = 0.0;
-  if (lane == 0) {
-    *ok = tridiag_eigenvalues(dg, od, m);
+  tr = g.sum(tr);
+  fro = g.sum(fro);
+  Score sc;
+  sc.ok = true;
+  sc.s2 = (tr > 0.0 && fro > 0.0) ? -log(fro / (tr * tr)) : 0.0;
+  sc.vn = sc.s2;
+  if (!want_vn) return sc;
+  g.sync();
+  group_tridiag(g, G, m, dg, od);
+  double ent = 0.0, okv = 1.0;
+  if (g.tid == 0) {
+    okv = tridiag_eigenvalues(dg, od, m) ? 1.0 : 0.0;
     double tot = 0;
     for (int i = 0; i < m; ++i) tot += fmax(dg[i], 0.0);
     if (tot > 0) {
+      const double inv = 1.0 / tot;
       for (int i = 0; i < m; ++i) {
-        const double p = fmax(dg[i], 0.0) / tot;
+        const double p = fmax(dg[i], 0.0) * inv;
         if (p > 0) ent -= p * log(p);
       }
     }
   }
-  ent = __shfl_sync(0xffffffffu, ent, 0);
-  __syncwarp();
-  return ent;
+  sc.vn = g.bcast(ent);
+  sc.ok = g.bcast(okv) != 0.0;
+  return sc;
 }
 
-// ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
-__device__ void visit_bond(Smem& s, const Ctx& C, int i, bool ltr, int* accepted) {
+// Scores classes list[0..cnt) (all K classes if list is null) on the whole cluster: small problems
+// one class per warp, large ones one class per CTA.  Results go to the leader CTA's shared memory.
+__device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
+                              const int* list, int cnt, bool want_vn) {
   const Engine& e = *C.e;
   const int d = C.d, dd = d * d;
-  const int cl = C.dims[i], ch = C.dims[i + 1], cr = C.dims[i + 2];
-  double2* theta = C.scr + e.sl.theta;
-  double2* tmp = C.scr + e.sl.tmp;
-  block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl * d, ch, d * cr);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  double2* ws = C.scr + e.sl.warp + (long long)warp * e.sl.warp_stride;
-  for (int k = warp; k < C.K; k += kWarps) {
-    bool ok = true;
-    const double sc = score_candidate(C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, &ok);
-    if ((threadIdx.x & 31) == 0) {
-      s.scores[k] = sc;
-      if (!ok) set_failure(C, GCAMPS_ENOCONV, 2, cl * d, d * cr);
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols;
+  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (small) {
+    WarpGroup g{lane};
+    double2* ws = C.cta + e.cl.warp + (long long)warp * kSmallStride;
+    const int gw = C.rank * kWarps + warp, nw = C.csize * kWarps;
+    for (int t = gw; t < cnt; t += nw) {
+      const int k = list ? list[t] : t;
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn);
+      if (lane == 0) {
+        lead->s2[k] = sc.s2;
+        if (want_vn) {
+          lead->vn[k] = sc.vn;
+          lead->evald[k] = 1;
+        }
+        if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
+      }
+    }
+  } else {
+    BlockGroup g{&s, (int)threadIdx.x, (int)blockDim.x};
+    double2* ws = C.cta + e.cl.block;
+    for (int t = C.rank; t < cnt; t += C.csize) {
+      const int k = list ? list[t] : t;
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn);
+      if (threadIdx.x == 0) {
+        lead->s2[k] = sc.s2;
+        if (want_vn) {
+          lead->vn[k] = sc.vn;
+          lead->evald[k] = 1;
+        }
+        if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
+}
+
+__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+
+// ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
+// One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
+// decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class;
+// round 1 evaluates S_vN of the identity and of the class with the smallest S2, giving an upper bound
+// B on the best entropy; round 2 evaluates every other class with S2 <= B + tie_tol.  A class left out
+// has S_vN >= S2 > best + tie_tol, so the decision equals the one from evaluating every class.
+__device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, int* accepted) {
+  const Engine& e = *C.e;
+  const bool leader = C.rank == 0;
+  const int d = C.d, dd = d * d;
+  double2* theta = C.scr + e.sl.theta;
+  double2* tmp = C.scr + e.sl.tmp;
+  if (leader) {
+    const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
+    block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
+  }
+  cluster_sync();
+  const int cl = C.dims[i], cr = C.dims[i + 2];
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols;
+  const bool prune = m > kPruneMin;
+  score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, !prune);
+  cluster_sync();
+  if (prune) {
+    if (leader && threadIdx.x == 0) {
+      int kmin = 0;
+      for (int k = 0; k < C.K; ++k) {
+        s.evald[k] = 0;
+        if (s.s2[k] < s.s2[kmin]) kmin = k;
+      }
+      s.list[0] = 0;
+      s.nlist = 1;
+      if (kmin != 0) s.list[s.nlist++] = kmin;
+    }
+    cluster_sync();
+    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);
+    cluster_sync();
+    if (leader && threadIdx.x == 0) {
+      double bound = 1e300;
+      for (int k = 0; k < C.K; ++k)
+        if (s.evald[k]) bound = fmin(bound, s.vn[k]);
+      int cnt = 0;
+      for (int k = 0; k < C.K; ++k)
+        if (!s.evald[k] && s.s2[k] <= bound + e.tie_tol + 1e-12) s.list[cnt++] = k;
+      s.nlist = cnt;
+    }
+    cluster_sync();
+    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);
+    cluster_sync();
+  }
+  if (!leader) return;
   if (threadIdx.x == 0) {
-    double best = s.scores[0];
-    for (int k = 1; k < C.K; ++k) best = fmin(best, s.scores[k]);
+    double best = 1e300;
+    int nev = 0;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k]) {
+        best = fmin(best, s.vn[k]);
+        ++nev;
+      }
     int kb = 0;
-    while (s.scores[kb] > best + e.tie_tol) ++kb;
-    if (!(s.scores[kb] < s.scores[0] - e.tie_tol)) kb = 0;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k] && s.vn[k] <= best + e.tie_tol) {
+        kb = k;
+        break;
+      }
+    if (!(s.vn[kb] < s.vn[0] - e.tie_tol)) kb = 0;
     s.ival[4] = kb;
     C.stats[S_BONDS] += 1;
     C.stats[S_CANDS] += C.K;
+    C.stats[S_VN] += nev;
     {
-      const double R = cl * d, Cc = d * cr;
-      const double m = R < Cc ? R : Cc, M = R < Cc ? Cc : R;
-      C.dstats[1] += C.K * (8.0 * dd * R * Cc + 4.0 * m * (m + 1.0) * M + (16.0 / 3.0) * m * m * m);
+      const double R = rows, Cc = cols, mm = m, M = rows < cols ? cols : rows;
+      C.dstats[1] += C.K * (8.0 * dd * R * Cc + 4.0 * mm * (mm + 1.0) * M) + nev * (16.0 / 3.0) * mm * mm * mm;
     }
     const int nd = C.meta[M_NDEC];
     if (nd < kDecCap) {
@@ -962,7 +1111,7 @@ __device__ void visit_bond(Smem& s, const Ctx& C, int i, bool ltr, int* accepted
     ++*accepted;
   }
   const int bb = e.bond_bound[i + 1];
-  Factor F = svd_factor(s, C, theta, cl * d, d * cr, e.chi_max < bb ? e.chi_max : bb, true);
+  Factor F = svd_factor(s, C, theta, rows, cols, e.chi_max < bb ? e.chi_max : bb, true);
   const int k = F.k;
   if (ltr) {
     for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
@@ -983,22 +1132,28 @@ __device__ void visit_bond(Smem& s, const Ctx& C, int i, bool ltr, int* accepted
   __syncthreads();
 }
 
-__device__ void disentangle(Smem& s, const Ctx& C) {
+// Alternating sweeps over the bonds of the last span; every CTA of the cluster runs the loop, only
+// the leader touches the MPS and the tableau.
+__device__ void disentangle(Smem& s, Smem* lead, const Ctx& C) {
+  cluster_sync();
   if (!C.meta[M_HAVE_SPAN]) return;
   const int f = C.meta[M_F], l = C.meta[M_L];
-  __syncthreads();
   if (l <= f) return;
   for (int sweep = 0; sweep < C.e->max_sweeps; ++sweep) {
     const bool ltr = (sweep & 1) == 0;
-    move_center(s, C, ltr ? f : l);
+    if (C.rank == 0) move_center(s, C, ltr ? f : l);
     int acc = 0;
     for (int t = 0; t < l - f; ++t) {
       const int i = ltr ? f + t : l - 1 - t;
-      visit_bond(s, C, i, ltr, &acc);
+      visit_bond(s, lead, C, i, ltr, &acc);
     }
-    if (threadIdx.x == 0) C.stats[S_SWEEPS] += 1;
-    __syncthreads();
-    if (acc == 0) break;
+    if (C.rank == 0 && threadIdx.x == 0) {
+      C.stats[S_SWEEPS] += 1;
+      s.bcast = acc;
+    }
+    cluster_sync();
+    const int acc_all = lead->bcast;
+    if (acc_all == 0) break;
   }
 }
 
@@ -1011,16 +1166,17 @@ __device__ void init_tau(Smem& s, int d) {
   __syncthreads();
 }
 
-__device__ void run_op(Smem& s, const Ctx& C, const gcamps_op& op) {
+// Clifford and non-Clifford steps touch only the leader's state; disentangling uses the cluster.
+__device__ void run_op(Smem& s, Smem* lead, const Ctx& C, const gcamps_op& op) {
   switch (op.kind) {
     case GCAMPS_OP_CLIFFORD:
-      apply_clifford(s, C, op.q0, op.q1, op.img);
+      if (C.rank == 0) apply_clifford(s, C, op.q0, op.q1, op.img);
       break;
     case GCAMPS_OP_NONCLIFFORD:
-      apply_nonclifford(s, C, op.q0, op.phases);
+      if (C.rank == 0) apply_nonclifford(s, C, op.q0, op.phases);
       break;
     case GCAMPS_OP_DISENTANGLE:
-      disentangle(s, C);
+      disentangle(s, lead, C);
       break;
     default:
       break;
@@ -1030,25 +1186,33 @@ __device__ void run_op(Smem& s, const Ctx& C, const gcamps_op& op) {
 
 __global__ void __launch_bounds__(kThreads) k_run(Engine e, const gcamps_op* ops, const int32_t* begin) {
   __shared__ Smem s;
-  const int c = blockIdx.x;
-  Ctx C = make_ctx(e, c);
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
   const int stop = begin[c + 1];
-  for (int i = begin[c]; i < stop; ++i) run_op(s, C, ops[i]);
+  for (int i = begin[c]; i < stop; ++i) run_op(s, lead, C, ops[i]);
+  cluster_sync();
 }
 
 __global__ void __launch_bounds__(kThreads) k_run_all(Engine e, const gcamps_op* ops, int nops) {
   __shared__ Smem s;
-  Ctx C = make_ctx(e, blockIdx.x);
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
-  for (int i = 0; i < nops; ++i) run_op(s, C, ops[i]);
+  for (int i = 0; i < nops; ++i) run_op(s, lead, C, ops[i]);
+  cluster_sync();
 }
 
 __global__ void __launch_bounds__(kThreads) k_single(Engine e, gcamps_op op) {
   __shared__ Smem s;
-  Ctx C = make_ctx(e, blockIdx.x);
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
-  run_op(s, C, op);
+  run_op(s, lead, C, op);
+  cluster_sync();
 }
 
 // |0...0> with C = I, counters cleared.
@@ -1325,19 +1489,38 @@ __global__ void k_apply_clifford_dense(Engine e, long long dim, const double2* m
 }  // namespace
 
 // ---------------------------------------------------------------------------- host launchers
+// Engine kernels are launched with one thread-block cluster of e.csize CTAs per circuit.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(void (*kern)(KArgs...), const Engine& e, cudaStream_t st, Args... args) {
+  if (e.csize > 8) {
+    cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (a != cudaSuccess) return a;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(e.batch * e.csize), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)e.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st) {
-  k_run<<<e.batch, kThreads, 0, st>>>(e, ops_dev, begin_dev);
-  return cudaGetLastError();
+  return launch_cluster(k_run, e, st, e, ops_dev, begin_dev);
 }
 
 cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
-  k_run_all<<<e.batch, kThreads, 0, st>>>(e, ops_dev, nops);
-  return cudaGetLastError();
+  return launch_cluster(k_run_all, e, st, e, ops_dev, nops);
 }
 
 cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
-  k_single<<<e.batch, kThreads, 0, st>>>(e, op);
-  return cudaGetLastError();
+  return launch_cluster(k_single, e, st, e, op);
 }
 
 cudaError_t launch_reset(const Engine& e, cudaStream_t st) {

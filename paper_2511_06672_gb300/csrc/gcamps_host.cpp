@@ -420,6 +420,7 @@ void gcamps_default_opts(gcamps_opts* o) {
   o->tie_tol = 1e-10;
   o->strict_weight = 0.0;
   o->cuda_stream = nullptr;
+  o->cluster_size = 8;
 }
 
 int gcamps_num_candidates(int d) {
@@ -467,6 +468,10 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind != 0 || opts.precision != 0 ||
       !(opts.tie_tol >= 0.0))
     return GCAMPS_EINVAL;
+  if (opts.cluster_size == 0) opts.cluster_size = 8;
+  if (opts.cluster_size < 1 || opts.cluster_size > gcx::kMaxCluster ||
+      (opts.cluster_size & (opts.cluster_size - 1)))
+    return GCAMPS_EINVAL;
   gcamps_t* h = new (std::nothrow) gcamps;
   if (!h) return GCAMPS_ENOMEM;
   const Tables& tb = tables(d);
@@ -509,9 +514,12 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   sl.u = sl.w + e.wcap;
   sl.vh = sl.u + tcap;
   sl.tmp = sl.vh + tcap;
-  sl.warp = sl.tmp + tcap;
-  sl.warp_stride = tcap + e.wcap + maxm + 64;
-  sl.total = sl.warp + gcx::kWarps * sl.warp_stride;
+  sl.total = sl.tmp + tcap;
+  e.csize = opts.cluster_size;
+  gcx::CtaLayout& cly = e.cl;
+  cly.warp = 0;
+  cly.block = (long long)gcx::kWarps * gcx::kSmallStride;
+  cly.total = cly.block + tcap + e.wcap + maxm + 64;
   e.tab_stride = 2LL * (4LL * n * n + 2LL * n);
   e.mps_stride = off[n];
   e.sing_stride = 2 * maxm + 64;
@@ -541,6 +549,8 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   bytes = align(bytes + (size_t)batch * 2 * n);
   const size_t o_scr = bytes;
   bytes = align(bytes + (size_t)batch * sl.total * sizeof(double2));
+  const size_t o_cscr = bytes;
+  bytes = align(bytes + (size_t)batch * e.csize * cly.total * sizeof(double2));
   const size_t o_sing = bytes;
   bytes = align(bytes + (size_t)batch * e.sing_stride * sizeof(double));
   const size_t o_iscr = bytes;
@@ -579,6 +589,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.dec = (int*)(base + o_dec);
   e.weyl = (int8_t*)(base + o_weyl);
   e.scr = (double2*)(base + o_scr);
+  e.cscr = (double2*)(base + o_cscr);
   e.sing = (double*)(base + o_sing);
   e.iscr = (int*)(base + o_iscr);
   e.candU = (const double2*)(base + o_candU);
@@ -920,6 +931,7 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   st->candidates_scored = s[gcx::S_CANDS];
   st->accepted = s[gcx::S_ACC];
   st->sweeps = s[gcx::S_SWEEPS];
+  st->vn_evaluations = s[gcx::S_VN];
   st->max_chi = (int32_t)s[gcx::S_MAXCHI];
   st->status = meta[gcx::M_STATUS];
   st->discarded_weight = ds[0];

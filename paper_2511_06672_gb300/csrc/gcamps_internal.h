@@ -9,8 +9,11 @@
 
 namespace gcx {
 
-constexpr int kThreads = 256;             // threads per CTA; one CTA runs one circuit
+constexpr int kThreads = 256;             // threads per CTA; a cluster of CTAs runs one circuit
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCluster = 16;           // CTAs per circuit (thread-block cluster)
+constexpr int kSmall = 729;               // warp-level scoring when theta' and its Gram fit this many entries
+constexpr int kSmallStride = 2 * kSmall + 64;
 constexpr int kMaxN = 128;                // qudits per circuit
 constexpr int kMaxK = 90;                 // disentangler classes (d = 3)
 constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
@@ -18,8 +21,9 @@ constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
 // meta[] words per circuit
 enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_DIAG_WHERE, M_DIAG_A, M_DIAG_B,
             M_COUNT };
+// stats: S_VN counts exact von Neumann evaluations (the rest were excluded by the Renyi-2 bound)
 // stats[] counters per circuit (int64)
-enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_COUNT };
+enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN, S_COUNT };
 
 // Scratch areas of one circuit, as element offsets (double2) from its scratch base.
 struct ScratchLayout {
@@ -29,13 +33,20 @@ struct ScratchLayout {
   long long u;       // left factor                                    [tcap]
   long long vh;      // right factor                                   [tcap]
   long long tmp;     // matmul staging                                 [tcap]
-  long long warp;    // per-warp scoring scratch, kWarps x warp_stride
-  long long warp_stride;
   long long total;   // elements per circuit
 };
 
+// Scratch of one CTA (circuit c, cluster rank r at index c * csize + r): kWarps warp-level scoring
+// buffers of kSmallStride entries, then one block-level scoring buffer (theta' [tcap], Gram [wcap],
+// eigenvalue arrays).
+struct CtaLayout {
+  long long warp;    // 0
+  long long block;   // kWarps * kSmallStride
+  long long total;
+};
+
 struct Engine {
-  int n, d, K, chi_max, batch, max_sweeps, maxdim;
+  int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;
   double cutoff, tie_tol, strict_weight;
   long long tcap;                 // elements of the largest two-site matrix
   long long wcap;                 // elements of the largest Jacobi rotation matrix
@@ -51,6 +62,7 @@ struct Engine {
   int* dec;                                 // [batch][kDecCap][2]
   int8_t* weyl;                             // [batch][2n]
   double2* scr;     ScratchLayout sl;       // per-circuit scratch, stride sl.total
+  double2* cscr;    CtaLayout cl;           // per-CTA scratch, stride cl.total
   double* sing;     long long sing_stride;  // singular values / eigenvalues
   int* iscr;        long long iscr_stride;  // permutation scratch
   const double2* candU;                     // [K][d^4] class unitaries, row-major

@@ -40,8 +40,8 @@ def oracle_run(gates, n, d, chi_max, cutoff, max_sweeps=8):
     return g
 
 
-def gpu_run(G, gates, n, d, chi_max, cutoff, max_sweeps=8):
-    sim = G.Simulator(n, d, chi_max=chi_max, cutoff=cutoff, max_sweeps=max_sweeps)
+def gpu_run(G, gates, n, d, chi_max, cutoff, max_sweeps=8, cluster_size=8):
+    sim = G.Simulator(n, d, chi_max=chi_max, cutoff=cutoff, max_sweeps=max_sweeps, cluster_size=cluster_size)
     sim.run(G.ops_from_gates(gates, d))
     sim.sync()
     return sim
@@ -264,3 +264,32 @@ def test_reset(G):
     sim.run(G.ops_from_gates(gates, d))
     ref = oracle_run(gates, n, d, 32, 1e-12)
     assert sim.decisions() == ref.decisions
+
+
+@pytest.mark.parametrize("csize", [1, 2, 4, 16])
+def test_cluster_sizes_give_identical_decisions(G, csize):
+    """The disentangler decisions do not depend on how many CTAs score the classes (qutrits,
+    n = 12, chi up to 27, where the Renyi-2 pruning path is taken)."""
+    d, n = 3, 12
+    gates = brickwork_circuit(n, d, 12, 16, 31)
+    sim = gpu_run(G, gates, n, d, 64, 1e-12, cluster_size=csize)
+    ref = oracle_run(gates, n, d, 64, 1e-12)
+    assert sim.decisions() == ref.decisions
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    st = sim.stats()
+    assert st["vn_evaluations"] <= st["candidates_scored"]
+
+
+def test_renyi2_pruning_is_exact_on_large_bonds(G):
+    """Bonds with Gram size > 9 use the Renyi-2 bound: decisions still equal the oracle's, which
+    scores every class by SVD."""
+    d, n = 3, 8
+    gates = brickwork_circuit(n, d, 10, 14, 41)
+    sim = gpu_run(G, gates, n, d, 81, 1e-12)
+    ref = oracle_run(gates, n, d, 81, 1e-12)
+    assert max(ref.mps.bond_dims()) >= 9 or max(sim.stats()["max_chi"], 0) >= 9
+    assert sim.decisions() == ref.decisions
+    st = sim.stats()
+    assert st["vn_evaluations"] < st["candidates_scored"]
+    err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
+    assert err < TOL
