@@ -37,6 +37,10 @@ METRIC = "T-gates/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the engine is FP64-ALU bound
 
 
+def progress(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -229,9 +233,12 @@ def main():
             stream.wait_event(join)
 
     # warm-up (also checks status)
-    for _ in range(args.warmup):
+    progress("handles ready; warm-up")
+    for w in range(args.warmup):
+        t0 = time.perf_counter()
         launch_all()
         stream.synchronize()
+        progress(f"warm-up step {w}: {time.perf_counter() - t0:.2f} s")
     for d in (2, 3):
         sims[d].sync()
 
@@ -279,6 +286,7 @@ def main():
                 "kernel": "k_run (engine, one launch per d)", "flops_per_launch": flops_per_launch,
                 "launch_ms": 1e3 * launch_s, "peak_source": "FP64 nominal, profiling recipe table"}
 
+    progress(f"timed steps: {[round(t, 3) for t in times]}")
     # end to end: host gate lists, copies and readback inside the timed region
     torch.cuda.synchronize()
     e2e_times = []
@@ -312,6 +320,7 @@ def main():
         "roofline": roofline,
         "clocks": clk,
     }
+    progress(f"e2e steps: {[round(t, 3) for t in e2e_times]}")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, el, circ = cpu_oracle_sample(budget_s=15.0)
         line["cpu_baseline"] = {"value": rate, "unit": "T-gates/s", "cores": 1, "kind": "oracle",

@@ -69,6 +69,10 @@ typedef struct {
   int64_t sweeps;             /* disentangling sweeps                                       */
   int64_t vn_evaluations;     /* exact von Neumann entropies computed (the others were      */
                               /* excluded by the Renyi-2 lower bound S2 <= S_vN)            */
+  int64_t svd_calls;          /* truncating SVDs (one-sided Jacobi)                         */
+  int64_t jacobi_sweeps;      /* Jacobi sweeps over all SVDs                                */
+  int64_t jacobi_max_sweeps;  /* most sweeps one SVD needed                                 */
+  int64_t qr_calls;           /* Householder QRs (canonical-form moves)                     */
   int32_t max_chi;            /* largest bond dimension seen after any truncation           */
   int32_t status;             /* sticky device status: 0 or a GCAMPS_E* code                */
   double discarded_weight;    /* sum of discarded s_i^2 over all truncations                */
@@ -82,7 +86,9 @@ typedef struct {
 /* One operation of a gate list (gcamps_run).  kind: */
 #define GCAMPS_OP_CLIFFORD 1     /* q0, q1 (-1 for one qudit), img as for apply_clifford   */
 #define GCAMPS_OP_NONCLIFFORD 2  /* q0 = site, phases[0..d-1]                             */
-#define GCAMPS_OP_DISENTANGLE 3  /* disentangle the span of the last non-Clifford gate     */
+#define GCAMPS_OP_DISENTANGLE 3  /* disentangle the span of the last non-Clifford gate;    */
+                                 /* q0 > 0: at most q0 sweeps (else opts.max_sweeps);      */
+                                 /* q1 > 0: stop after q1 bond visits                      */
 typedef struct {
   int32_t kind;
   int32_t q0, q1;
@@ -167,13 +173,35 @@ int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t*
 int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi);
 /* Schmidt values of bond `bond` (count <= chi of that bond), sorted descending. */
 int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count);
+/* Tensor of MPS site j: dims[0..2] = (chi_l, d, chi_r); if t is not NULL it receives the
+ * chi_l d chi_r complex entries (interleaved re, im; row-major over (a, s, b)); cap = capacity of t
+ * in complex entries (EINVAL if too small). */
+int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, int32_t* dims);
 /* Weyl string P = C^dag Z_k C of the last non-Clifford gate: x[n], z[n], r. */
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
 int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
+/* Scores of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class),
+ * vn[k] (von Neumann entropy, valid where evaluated[k] = 1; the Renyi-2 bound excluded the others);
+ * K = gcamps_num_candidates(d) entries each; any pointer may be NULL. */
+int gcamps_get_last_scores(gcamps_t* h, int circuit, double* s2, double* vn, uint8_t* evaluated);
+/* Two-site tensor scored at the last bond visit: shape[0..1] = (chi_l, chi_r); theta receives the
+ * chi_l d d chi_r complex entries (interleaved re, im) when that count is at most 729 (larger
+ * tensors are not kept). */
+int gcamps_get_last_theta(gcamps_t* h, int circuit, double* theta, int32_t* shape);
 /* Disentangler decisions of the circuit since the last reset: (bond, class index) per bond
  * visit, in visit order; class 0 = nothing applied.  *count receives the total number
  * recorded; at most cap pairs are copied. */
 int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, int32_t* count);
+
+/* Disentangler scores of every class on a given two-site tensor (Sec. 3): theta is
+ * chi_l x d x d x chi_r complex (interleaved re, im, row-major over (a, s, t, b)), on host memory.
+ * s2[k] = Renyi-2 entropy and vn[k] = von Neumann entropy (natural log) of the Schmidt spectrum of
+ * Q_k theta across (a, s) | (t, b), K = gcamps_num_candidates(d) entries each.  Runs the same device
+ * code as gcamps_disentangle (every class evaluated here).  choice (may be NULL) receives the
+ * class the disentangler would apply to this theta (0 = none) and how many exact entropies its
+ * Renyi-2 pruning evaluated.  Synchronising. */
+int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* s2, double* vn,
+                       int32_t* choice);
 
 /* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded. */
 int gcamps_sync(gcamps_t* h);

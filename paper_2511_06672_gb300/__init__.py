@@ -211,6 +211,15 @@ class Simulator:
         self._c(self._lib.gcamps_get_schmidt(self._h, circuit, bond, N.ptr(s, C.c_double), C.byref(cnt)))
         return s[: cnt.value].copy()
 
+    def site(self, j: int, circuit: int = 0) -> np.ndarray:
+        """MPS tensor of site j, shape (chi_l, d, chi_r)."""
+        dims = np.zeros(3, dtype=np.int32)
+        self._c(self._lib.gcamps_get_site(self._h, circuit, j, None, 0, N.ptr(dims, C.c_int32)))
+        t = np.zeros(int(np.prod(dims)), dtype=np.complex128)
+        self._c(self._lib.gcamps_get_site(self._h, circuit, j, t.ctypes.data_as(C.POINTER(C.c_double)), t.size,
+                                          N.ptr(dims, C.c_int32)))
+        return t.reshape(tuple(int(x) for x in dims))
+
     def last_weyl(self, circuit: int = 0):
         x = np.zeros(self.n, dtype=np.int32)
         z = np.zeros(self.n, dtype=np.int32)
@@ -223,6 +232,36 @@ class Simulator:
         st = N.Stats()
         self._c(self._lib.gcamps_get_stats(self._h, circuit, C.byref(st)))
         return st.as_dict()
+
+    def score_theta(self, theta: np.ndarray):
+        """(S2, S_vN, chosen class, exact evaluations) for theta of shape (chi_l, d, d, chi_r)."""
+        t = np.ascontiguousarray(theta, dtype=np.complex128)
+        cl, cr = t.shape[0], t.shape[3]
+        s2 = np.zeros(self._lib.gcamps_num_candidates(self.d))
+        vn = np.zeros_like(s2)
+        ch = np.zeros(2, dtype=np.int32)
+        self._c(self._lib.gcamps_score_theta(self._h, cl, cr, t.ctypes.data_as(C.POINTER(C.c_double)),
+                                             N.ptr(s2, C.c_double), N.ptr(vn, C.c_double), N.ptr(ch, C.c_int32)))
+        return s2, vn, int(ch[0]), int(ch[1])
+
+    def last_scores(self, circuit: int = 0):
+        """(S2, S_vN, evaluated) of every class at the last disentangler bond visit."""
+        K = self._lib.gcamps_num_candidates(self.d)
+        s2, vn = np.zeros(K), np.zeros(K)
+        ev = np.zeros(K, dtype=np.uint8)
+        self._c(self._lib.gcamps_get_last_scores(self._h, circuit, N.ptr(s2, C.c_double), N.ptr(vn, C.c_double),
+                                                 N.ptr(ev, C.c_uint8)))
+        return s2, vn, ev.astype(bool)
+
+    def last_theta(self, circuit: int = 0):
+        """Two-site tensor of the last bond visit, shape (chi_l, d, d, chi_r), or None if too large."""
+        shape = np.zeros(2, dtype=np.int32)
+        buf = np.zeros(729, dtype=np.complex128)
+        self._c(self._lib.gcamps_get_last_theta(self._h, circuit, buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                                N.ptr(shape, C.c_int32)))
+        cl, cr = int(shape[0]), int(shape[1])
+        nel = cl * self.d * self.d * cr
+        return None if nel > 729 else buf[:nel].reshape(cl, self.d, self.d, cr).copy()
 
     def decisions(self, circuit: int = 0) -> list:
         cnt = C.c_int32()

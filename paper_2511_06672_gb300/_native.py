@@ -25,7 +25,8 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("t_gates", C.c_int64), ("clifford_gates", C.c_int64), ("bonds_visited", C.c_int64),
                 ("candidates_scored", C.c_int64), ("accepted", C.c_int64), ("sweeps", C.c_int64),
-                ("vn_evaluations", C.c_int64),
+                ("vn_evaluations", C.c_int64), ("svd_calls", C.c_int64), ("jacobi_sweeps", C.c_int64),
+                ("jacobi_max_sweeps", C.c_int64), ("qr_calls", C.c_int64),
                 ("max_chi", C.c_int32), ("status", C.c_int32), ("discarded_weight", C.c_double),
                 ("scoring_flops", C.c_double)]
 
@@ -39,8 +40,9 @@ EXPORTS = [
     "gcamps_create_batch", "gcamps_destroy", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
     "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
-    "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_last_weyl", "gcamps_get_stats",
-    "gcamps_get_decisions", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
+    "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
+    "gcamps_get_stats",
+    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
 ]
 
 _lib = None
@@ -76,9 +78,13 @@ def load(path: str = LIB_PATH):
         "gcamps_get_inverse_tableau": (C.c_int, [vp, C.c_int, u8p, u8p]),
         "gcamps_get_bond_dims": (C.c_int, [vp, C.c_int, i32p]),
         "gcamps_get_schmidt": (C.c_int, [vp, C.c_int, C.c_int, dp, i32p]),
+        "gcamps_get_site": (C.c_int, [vp, C.c_int, C.c_int, dp, C.c_int64, i32p]),
         "gcamps_get_last_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, i32p]),
         "gcamps_get_stats": (C.c_int, [vp, C.c_int, C.POINTER(Stats)]),
         "gcamps_get_decisions": (C.c_int, [vp, C.c_int, i32p, C.c_int32, i32p]),
+        "gcamps_score_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp, i32p]),
+        "gcamps_get_last_scores": (C.c_int, [vp, C.c_int, dp, dp, u8p]),
+        "gcamps_get_last_theta": (C.c_int, [vp, C.c_int, dp, i32p]),
         "gcamps_sync": (C.c_int, [vp]),
         "gcamps_reset": (C.c_int, [vp]),
         "gcamps_last_error": (C.c_char_p, [vp]),

@@ -58,6 +58,18 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
   return acc;
 }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+// x / |x|, and 1 for x = 0.  A subnormal x is first scaled by 2^600 (exact): its modulus carries only
+// a few significant bits, so the plain quotient has a modulus visibly different from 1 and a
+// Householder reflector built with it is no longer unitary.
+__device__ __forceinline__ double2 unit_phase(double2 x) {
+  if (x.x == 0.0 && x.y == 0.0) return make_double2(1.0, 0.0);
+  if (fabs(x.x) < 0x1p-900 && fabs(x.y) < 0x1p-900) {
+    x.x *= 0x1p600;
+    x.y *= 0x1p600;
+  }
+  const double ax = hypot(x.x, x.y);
+  return make_double2(x.x / ax, x.y / ax);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -473,6 +485,11 @@ struct Factor {
   double disc;
 };
 
+__device__ int block_qr(Smem& s, double2* B, int m, int n, double2* Q, double2* R, double* beta, double2* rdiag);
+
+// When the long side is at least twice the short one, the long side is first reduced by a QR
+// (B = Q R) and the Jacobi rotations act on the n x n factor R; the long factor is then Q times
+// the orthogonalised columns of R.
 __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, int cols, int cap,
                              bool renorm) {
   const Engine& e = *C.e;
@@ -480,6 +497,7 @@ __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, 
   double2* W = C.scr + e.sl.w;
   double2* U = C.scr + e.sl.u;
   double2* Vh = C.scr + e.sl.vh;
+  double2* Qb = C.scr + e.sl.tmp;
   double* sing = C.sing;
   double* svt = C.sing + e.sing_stride / 2;
   int* perm = C.perm;
@@ -493,9 +511,27 @@ __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, 
     else B[(long long)r * m + c] = cconj(M[idx]);
   }
   __syncthreads();
-  const int sweeps = jacobi_orthogonalize(s, B, m, n, W, 60);
-  if (sweeps < 0 && threadIdx.x == 0) set_failure(C, GCAMPS_ENOCONV, 1, rows, cols);
-  sorted_column_norms(B, m, n, svt, sing, perm);
+  const bool precond = n > 1 && m >= 2 * n;
+  int mm = m;
+  if (precond) {
+    block_qr(s, B, m, n, Qb, Vh, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
+    __syncthreads();
+    for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+      const int i = (int)(idx / n), c = (int)(idx % n);
+      B[(long long)c * n + i] = Vh[idx];
+    }
+    __syncthreads();
+    mm = n;
+  }
+  const int sweeps = jacobi_orthogonalize(s, B, mm, n, W, 60);
+  if (threadIdx.x == 0) {
+    if (sweeps < 0) set_failure(C, GCAMPS_ENOCONV, 1, rows, cols);
+    const int sw = sweeps < 0 ? 60 : sweeps;
+    C.stats[S_SVD] += 1;
+    C.stats[S_JSWEEPS] += sw;
+    if (sw > C.stats[S_JMAX]) C.stats[S_JMAX] = sw;
+  }
+  sorted_column_norms(B, mm, n, svt, sing, perm);
   // rank rule
   if (threadIdx.x == 0) {
     int k = 0;
@@ -519,25 +555,33 @@ __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, 
   F.Vh = Vh;
   F.k = k;
   F.disc = s.dval[0];
-  // U and Vh
-  for (long long idx = threadIdx.x; idx < (long long)rows * k; idx += blockDim.x) {
+  // X[:, i] = (long side) orthogonalised column perm[i] / sigma_i, an m-vector
+  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
     const int r = (int)(idx / k), i = (int)(idx % k);
     const int pj = perm[i];
-    if (tall) {
-      const double sv = sing[i];
-      U[idx] = sv > 0 ? cscale(B[(long long)pj * m + r], 1.0 / sv) : cz();
-    } else {
-      U[idx] = W[(long long)pj * n + r];
+    const double sv = sing[i];
+    double2 x = cz();
+    if (sv > 0) {
+      if (precond) {
+        const double2* col = B + (long long)pj * n;
+        for (int t = 0; t < n; ++t) x = cfma(Qb[(long long)t * m + r], col[t], x);
+      } else {
+        x = B[(long long)pj * m + r];
+      }
+      x = cscale(x, 1.0 / sv);
     }
+    if (tall) U[idx] = x;                              // U[r][i], r < rows
+    else Vh[(long long)i * cols + r] = cconj(x);       // Vh[i][r], r < cols
   }
-  for (long long idx = threadIdx.x; idx < (long long)k * cols; idx += blockDim.x) {
-    const int i = (int)(idx / cols), c = (int)(idx % cols);
-    const int pj = perm[i];
-    if (tall) {
-      Vh[idx] = cconj(W[(long long)pj * n + c]);
-    } else {
-      const double sv = sing[i];
-      Vh[idx] = sv > 0 ? cscale(cconj(B[(long long)pj * m + c]), 1.0 / sv) : cz();
+  if (tall) {
+    for (long long idx = threadIdx.x; idx < (long long)k * cols; idx += blockDim.x) {
+      const int i = (int)(idx / cols), c = (int)(idx % cols);
+      Vh[idx] = cconj(W[(long long)perm[i] * n + c]);
+    }
+  } else {
+    for (long long idx = threadIdx.x; idx < (long long)rows * k; idx += blockDim.x) {
+      const int r = (int)(idx / k), i = (int)(idx % k);
+      U[idx] = W[(long long)perm[i] * n + r];
     }
   }
   __syncthreads();
@@ -546,35 +590,170 @@ __device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, 
   return F;
 }
 
+// ------------------------------------------------------------ Householder QR (block level)
+// Reduced QR of B (m x n, column-major, overwritten): B = Q R with k = min(m, n); Q (m x k,
+// column-major) in Q, R (k x n, row-major) in R.  Reflector k is H = I - beta v v^H with
+// v = x + e^{i arg x_0} |x| e_1 on rows k..m-1 (x = column k), so H x = -e^{i arg x_0} |x| e_1.
+// Columns handled by warps in parallel; no rank decision (the reduced Q keeps k columns).
+__device__ int block_qr(Smem& s, double2* B, int m, int n, double2* Q, double2* R, double* beta, double2* rdiag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = m < n ? m : n;
+  // columns whose remaining part is below 1e-15 |B|_F are left unreflected (the reflector would
+  // underflow); R keeps their diagonal entry and drops the rest (<= 1e-15 |B|_F)
+  double fro = 0;
+  for (long long i = threadIdx.x; i < (long long)m * n; i += blockDim.x) fro += cabs2(B[i]);
+  fro = block_sum(fro, s);
+  const double tiny = 1e-30 * fro;
+  for (int j = 0; j < k; ++j) {
+    double2* x = B + (long long)j * m;
+    double nrm2 = 0;
+    for (int r = j + threadIdx.x; r < m; r += blockDim.x) nrm2 += cabs2(x[r]);
+    nrm2 = block_sum(nrm2, s);
+    const double2 x0 = x[j];
+    const double ax0 = hypot(x0.x, x0.y);
+    const double alpha = sqrt(nrm2);
+    __syncthreads();
+    if (nrm2 <= tiny) {
+      if (threadIdx.x == 0) {
+        beta[j] = 0.0;
+        rdiag[j] = x0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const double2 ph = unit_phase(x0);
+    const double bt = 1.0 / (alpha * (alpha + ax0));
+    if (threadIdx.x == 0) {
+      x[j] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+      beta[j] = bt;
+      rdiag[j] = make_double2(-ph.x * alpha, -ph.y * alpha);
+    }
+    __syncthreads();
+    for (int c = j + 1 + warp; c < n; c += kWarps) {
+      double2* y = B + (long long)c * m;
+      double wr = 0, wi = 0;   // w = v^H y
+      for (int r = j + lane; r < m; r += 32) {
+        const double2 v = x[r], t = y[r];
+        wr = fma(v.x, t.x, fma(v.y, t.y, wr));
+        wi = fma(v.x, t.y, fma(-v.y, t.x, wi));
+      }
+      wr = warp_sum(wr) * bt;
+      wi = warp_sum(wi) * bt;
+      const double2 w = make_double2(wr, wi);
+      for (int r = j + lane; r < m; r += 32) y[r] = csub(y[r], cmul(x[r], w));
+    }
+    __syncthreads();
+  }
+  // R (k x n, row-major)
+  for (long long idx = threadIdx.x; idx < (long long)k * n; idx += blockDim.x) {
+    const int i = (int)(idx / n), c = (int)(idx % n);
+    R[idx] = (c < i) ? cz() : (c == i ? rdiag[i] : B[(long long)c * m + i]);
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0]
+  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
+    const int r = (int)(idx % m), c = (int)(idx / m);
+    Q[idx] = (r == c) ? make_double2(1.0, 0.0) : cz();
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const double bt = beta[j];
+    if (bt == 0.0) continue;
+    const double2* x = B + (long long)j * m;
+    for (int c = j + warp; c < k; c += kWarps) {
+      double2* y = Q + (long long)c * m;
+      double wr = 0, wi = 0;
+      for (int r = j + lane; r < m; r += 32) {
+        const double2 v = x[r], t = y[r];
+        wr = fma(v.x, t.x, fma(v.y, t.y, wr));
+        wi = fma(v.x, t.y, fma(-v.y, t.x, wi));
+      }
+      wr = warp_sum(wr) * bt;
+      wi = warp_sum(wi) * bt;
+      const double2 w = make_double2(wr, wi);
+      for (int r = j + lane; r < m; r += 32) y[r] = csub(y[r], cmul(x[r], w));
+    }
+    __syncthreads();
+  }
+  return k;
+}
+
 // ---------------------------------------------------------------- canonical-form moves (Sec. 2.4)
 __device__ void note_chi(const Ctx& C, int k) {
   if (threadIdx.x == 0 && k > C.stats[S_MAXCHI]) C.stats[S_MAXCHI] = k;
 }
 
-// Centre j -> j+1: A_j = U S Vh, A_j <- U, A_{j+1} <- S Vh A_{j+1}.  Singular values at or below
-// cutoff * s_0 (numerical zeros) are dropped, no renormalisation.  `canonical`: the sites right of
-// j+1 are right-orthonormal, so the singular values are Schmidt values and the bond is also capped
-// at its Schmidt-rank bound d^min(b, n-b) (drops only rounding noise).  Right after an MPO the
-// right part is not orthonormal and no such cap applies; the kept count is then at most the
-// current bond dimension.
-__device__ void move_right(Smem& s, const Ctx& C, int j, bool canonical) {
+// Centre j -> j+1 without truncation (Sec. 2.4 canonical form): A_j = Q R (reduced QR of the
+// (chi_l d) x chi_r matrix), A_j <- Q, A_{j+1} <- R A_{j+1}; the bond keeps min(chi_l d, chi_r).
+__device__ void move_right(Smem& s, const Ctx& C, int j) {
+  const Engine& e = *C.e;
   const int d = C.d;
   const int cl = C.dims[j], cr = C.dims[j + 1], cr2 = C.dims[j + 2];
   double2* A = site_ptr(C, j);
   double2* A2 = site_ptr(C, j + 1);
-  Factor F = svd_factor(s, C, A, cl * d, cr, canonical ? C.e->bond_bound[j + 1] : (1 << 30), false);
-  const int k = F.k;
-  block_copy(A, F.U, (long long)cl * d * k);
-  for (long long idx = threadIdx.x; idx < (long long)k * cr; idx += blockDim.x)
-    F.Vh[idx] = cscale(F.Vh[idx], C.sing[idx / cr]);
+  double2* B = C.scr + e.sl.b;
+  double2* Q = C.scr + e.sl.u;
+  double2* R = C.scr + e.sl.vh;
+  double2* tmp = C.scr + e.sl.tmp;
+  const int m = cl * d, n = cr;
+  for (long long idx = threadIdx.x; idx < (long long)m * n; idx += blockDim.x) {
+    const int r = (int)(idx / n), c = (int)(idx % n);
+    B[(long long)c * m + r] = A[idx];
+  }
   __syncthreads();
-  double2* tmp = C.scr + C.e->sl.tmp;
-  block_matmul(tmp, F.Vh, A2, k, cr, d * cr2);
+  const int k = block_qr(s, B, m, n, Q, R, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
+  if (threadIdx.x == 0) C.stats[S_QR] += 1;
+  __syncthreads();
+  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
+    const int r = (int)(idx / k), c = (int)(idx % k);
+    A[idx] = Q[(long long)c * m + r];
+  }
+  block_matmul(tmp, R, A2, k, n, d * cr2);
   __syncthreads();
   block_copy(A2, tmp, (long long)k * d * cr2);
   if (threadIdx.x == 0) {
     C.dims[j + 1] = k;
     C.meta[M_OC] = j + 1;
+  }
+  __syncthreads();
+}
+
+// Centre j -> j-1 without truncation: M = A_j (chi_l x d chi_r) = L Q from the QR of M^H
+// (M^H = Q' R', M = R'^H Q'^H); A_j <- Q'^H, A_{j-1} <- A_{j-1} R'^H.
+__device__ void move_left_qr(Smem& s, const Ctx& C, int j) {
+  const Engine& e = *C.e;
+  const int d = C.d;
+  const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
+  double2* A = site_ptr(C, j);
+  double2* A0 = site_ptr(C, j - 1);
+  double2* B = C.scr + e.sl.b;
+  double2* Q = C.scr + e.sl.u;
+  double2* R = C.scr + e.sl.vh;
+  double2* tmp = C.scr + e.sl.tmp;
+  double2* RH = C.scr + e.sl.w;
+  const int m = d * cr, n = cl;   // M^H is m x n
+  for (long long idx = threadIdx.x; idx < (long long)n * m; idx += blockDim.x) {
+    const int a = (int)(idx / m), c = (int)(idx % m);      // M[a][c]
+    B[(long long)a * m + c] = cconj(A[idx]);
+  }
+  __syncthreads();
+  const int k = block_qr(s, B, m, n, Q, R, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
+  if (threadIdx.x == 0) C.stats[S_QR] += 1;
+  __syncthreads();
+  for (long long idx = threadIdx.x; idx < (long long)k * m; idx += blockDim.x) {
+    const int i = (int)(idx / m), c = (int)(idx % m);
+    A[idx] = cconj(Q[(long long)i * m + c]);
+  }
+  for (long long idx = threadIdx.x; idx < (long long)n * k; idx += blockDim.x) {
+    const int a = (int)(idx / k), i = (int)(idx % k);
+    RH[idx] = cconj(R[(long long)i * n + a]);
+  }
+  __syncthreads();
+  block_matmul(tmp, A0, RH, cl2 * d, n, k);
+  __syncthreads();
+  block_copy(A0, tmp, (long long)cl2 * d * k);
+  if (threadIdx.x == 0) {
+    C.dims[j] = k;
+    C.meta[M_OC] = j - 1;
   }
   __syncthreads();
 }
@@ -609,8 +788,8 @@ __device__ void move_center(Smem& s, const Ctx& C, int target) {
   while (true) {
     const int oc = C.meta[M_OC];
     __syncthreads();
-    if (oc < target) move_right(s, C, oc, true);
-    else if (oc > target) move_left(s, C, oc, 1 << 30, false);
+    if (oc < target) move_right(s, C, oc);
+    else if (oc > target) move_left_qr(s, C, oc);
     else break;
   }
 }
@@ -726,7 +905,7 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
     // canonicalise [f, l] left to right from f, then truncate right to left
     if (threadIdx.x == 0) C.meta[M_OC] = f;
     __syncthreads();
-    for (int j = f; j < l; ++j) move_right(s, C, j, false);
+    for (int j = f; j < l; ++j) move_right(s, C, j);
     double disc = 0;
     for (int j = l; j > f; --j) {
       disc += move_left(s, C, j, C.e->chi_max, true);
@@ -767,9 +946,9 @@ struct BlockGroup {
 
 // Householder reduction of a Hermitian m x m matrix (row-major, full storage, overwritten) to a
 // real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).  A column whose entries below
-// the subdiagonal are below 1e-16 |A|_F is taken as already reduced: reflecting such a column
-// underflows (h ~ |x|^2) and would poison the matrix, while dropping it moves eigenvalues by at
-// most that much.  Column k below the diagonal keeps the reflector v, row k right of it p and w.
+// the subdiagonal have norm below 1e-16 |A|_F is taken as already reduced (dropping them moves
+// eigenvalues by at most that much).  Column k below the diagonal keeps the reflector v, row k right
+// of it p and w.
 template <class Grp>
 __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, double* od) {
   double fro2 = 0;
@@ -777,20 +956,23 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
   fro2 = g.sum(fro2);
   for (int k = 0; k + 2 < m; ++k) {
     const int r = m - k - 1;
-    double nrm2 = 0;
-    for (int i = g.tid; i < r; i += g.n) nrm2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
-    nrm2 = g.sum(nrm2);
+    // the tail below x0 is summed on its own: |x|^2 - |x0|^2 cancels when x0 dominates and would
+    // hide a small tail (which, inside a degenerate eigenspace, moves eigenvalues at first order)
+    double tail2 = 0;
+    for (int i = 1 + g.tid; i < r; i += g.n) tail2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
+    tail2 = g.sum(tail2);
     const double2 x0 = A[(long long)(k + 1) * m + k];
     const double ax0 = hypot(x0.x, x0.y);
+    const double nrm2 = tail2 + ax0 * ax0;
     if (g.tid == 0) dg[k] = A[(long long)k * m + k].x;
     g.sync();
     const double alpha = sqrt(nrm2);
-    if (nrm2 - ax0 * ax0 <= 1e-32 * fro2) {
+    if (tail2 <= 1e-32 * fro2) {
       if (g.tid == 0) od[k] = ax0;
       g.sync();
       continue;
     }
-    const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    const double2 ph = unit_phase(x0);
     const double h = alpha * (alpha + ax0);  // v^H v / 2
     if (g.tid == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
     g.sync();
@@ -1016,18 +1198,13 @@ __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 // round 1 evaluates S_vN of the identity and of the class with the smallest S2, giving an upper bound
 // B on the best entropy; round 2 evaluates every other class with S2 <= B + tie_tol.  A class left out
 // has S_vN >= S2 > best + tie_tol, so the decision equals the one from evaluating every class.
-__device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, int* accepted) {
+// Cluster-wide choice of the class for one theta (shape chi_l x d x d x chi_r in global memory,
+// readable by every CTA).  Returns the chosen class on the leader (-1 on the other CTAs); the
+// leader's s.vn / s.evald hold the evaluated entropies and *nev their count.
+__device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out) {
   const Engine& e = *C.e;
   const bool leader = C.rank == 0;
-  const int d = C.d, dd = d * d;
-  double2* theta = C.scr + e.sl.theta;
-  double2* tmp = C.scr + e.sl.tmp;
-  if (leader) {
-    const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
-    block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
-  }
-  cluster_sync();
-  const int cl = C.dims[i], cr = C.dims[i + 2];
+  const int d = C.d;
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
   const bool prune = m > kPruneMin;
@@ -1060,7 +1237,7 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);
     cluster_sync();
   }
-  if (!leader) return;
+  if (!leader) return -1;
   if (threadIdx.x == 0) {
     double best = 1e300;
     int nev = 0;
@@ -1077,6 +1254,49 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
       }
     if (!(s.vn[kb] < s.vn[0] - e.tie_tol)) kb = 0;
     s.ival[4] = kb;
+    s.ival[5] = nev;
+  }
+  {
+    double* out = e.lastsc + (long long)C.c * (3 * kMaxK + 2 + 2 * kSmall);
+    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
+      out[k] = s.s2[k];
+      out[kMaxK + k] = s.vn[k];
+      out[2 * kMaxK + k] = s.evald[k];
+    }
+    if (threadIdx.x == 0) {
+      out[3 * kMaxK] = cl;
+      out[3 * kMaxK + 1] = cr;
+    }
+    if ((long long)rows * cols <= kSmall)
+      for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
+        out[3 * kMaxK + 2 + 2 * k] = theta[k].x;
+        out[3 * kMaxK + 3 + 2 * k] = theta[k].y;
+      }
+  }
+  __syncthreads();
+  *nev_out = s.ival[5];
+  return s.ival[4];
+}
+
+__device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, int* accepted) {
+  const Engine& e = *C.e;
+  const bool leader = C.rank == 0;
+  const int d = C.d, dd = d * d;
+  double2* theta = C.scr + e.sl.theta;
+  double2* tmp = C.scr + e.sl.tmp;
+  if (leader) {
+    const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
+    block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
+  }
+  cluster_sync();
+  const int cl = C.dims[i], cr = C.dims[i + 2];
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols;
+  int nev = 0;
+  const int kbsel = select_class(s, lead, C, theta, cl, cr, &nev);
+  if (!leader) return;
+  if (threadIdx.x == 0) {
+    const int kb = kbsel;
     C.stats[S_BONDS] += 1;
     C.stats[S_CANDS] += C.K;
     C.stats[S_VN] += nev;
@@ -1134,26 +1354,40 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
 
 // Alternating sweeps over the bonds of the last span; every CTA of the cluster runs the loop, only
 // the leader touches the MPS and the tableau.
-__device__ void disentangle(Smem& s, Smem* lead, const Ctx& C) {
+// sweep_cap > 0 overrides the handle's max_sweeps for this call; visit_cap > 0 stops after that
+// many bond visits (the centre is then left where the last split put it).
+__device__ void disentangle(Smem& s, Smem* lead, const Ctx& C, int sweep_cap, int visit_cap) {
   cluster_sync();
+  if (C.meta[M_STATUS] != 0) return;   // a failed circuit does no further work
   if (!C.meta[M_HAVE_SPAN]) return;
   const int f = C.meta[M_F], l = C.meta[M_L];
   if (l <= f) return;
-  for (int sweep = 0; sweep < C.e->max_sweeps; ++sweep) {
+  const int max_sweeps = sweep_cap > 0 ? sweep_cap : C.e->max_sweeps;
+  int visits = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     const bool ltr = (sweep & 1) == 0;
     if (C.rank == 0) move_center(s, C, ltr ? f : l);
     int acc = 0;
+    bool capped = false;
     for (int t = 0; t < l - f; ++t) {
+      if (visit_cap > 0 && visits >= visit_cap) {
+        capped = true;
+        break;
+      }
       const int i = ltr ? f + t : l - 1 - t;
       visit_bond(s, lead, C, i, ltr, &acc);
+      ++visits;
     }
+    if (capped) break;
     if (C.rank == 0 && threadIdx.x == 0) {
       C.stats[S_SWEEPS] += 1;
       s.bcast = acc;
     }
     cluster_sync();
     const int acc_all = lead->bcast;
-    if (acc_all == 0) break;
+    const int failed = C.meta[M_STATUS];
+    cluster_sync();   // every CTA has read bcast and the status before either changes
+    if (acc_all == 0 || failed != 0) break;
   }
 }
 
@@ -1173,10 +1407,10 @@ __device__ void run_op(Smem& s, Smem* lead, const Ctx& C, const gcamps_op& op) {
       if (C.rank == 0) apply_clifford(s, C, op.q0, op.q1, op.img);
       break;
     case GCAMPS_OP_NONCLIFFORD:
-      if (C.rank == 0) apply_nonclifford(s, C, op.q0, op.phases);
+      if (C.rank == 0 && C.meta[M_STATUS] == 0) apply_nonclifford(s, C, op.q0, op.phases);
       break;
     case GCAMPS_OP_DISENTANGLE:
-      disentangle(s, lead, C);
+      disentangle(s, lead, C, op.q0, op.q1);
       break;
     default:
       break;
@@ -1212,6 +1446,33 @@ __global__ void __launch_bounds__(kThreads) k_single(Engine e, gcamps_op op) {
   Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
   run_op(s, lead, C, op);
+  cluster_sync();
+}
+
+// Scores of every class on a caller-provided theta (chi_l, d, d, chi_r), through the same cluster
+// code as the disentangler: S2 of all classes and S_vN of all classes (no pruning).  Used to test
+// the scoring step on its own.
+__global__ void __launch_bounds__(kThreads) k_score_theta(Engine e, const double2* th, int cl, int cr,
+                                                          double* out_s2, double* out_vn, int* out_choice) {
+  __shared__ Smem s;
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, true);
+  cluster_sync();
+  if (c == 0 && rank == 0)
+    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
+      out_s2[k] = s.s2[k];
+      out_vn[k] = s.vn[k];
+    }
+  cluster_sync();
+  int nev = 0;
+  const int kb = select_class(s, lead, C, th, cl, cr, &nev);   // the disentangler's own choice
+  if (c == 0 && rank == 0 && threadIdx.x == 0) {
+    out_choice[0] = kb;
+    out_choice[1] = nev;
+  }
   cluster_sync();
 }
 
@@ -1509,6 +1770,11 @@ cudaError_t launch_cluster(void (*kern)(KArgs...), const Engine& e, cudaStream_t
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
+                               int* choice, cudaStream_t st) {
+  return launch_cluster(k_score_theta, e, st, e, th, cl, cr, s2, vn, choice);
 }
 
 cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st) {

@@ -522,7 +522,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   cly.total = cly.block + tcap + e.wcap + maxm + 64;
   e.tab_stride = 2LL * (4LL * n * n + 2LL * n);
   e.mps_stride = off[n];
-  e.sing_stride = 2 * maxm + 64;
+  e.sing_stride = 4 * maxm + 128;   // singular values | sort scratch / QR betas | QR diagonal
   e.iscr_stride = maxm + 64;
   // one device block, carved up
   auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -547,6 +547,8 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   bytes = align(bytes + (size_t)batch * gcx::kDecCap * 2 * sizeof(int));
   const size_t o_weyl = bytes;
   bytes = align(bytes + (size_t)batch * 2 * n);
+  const size_t o_last = bytes;
+  bytes = align(bytes + (size_t)batch * (3 * gcx::kMaxK + 2 + 2 * gcx::kSmall) * sizeof(double));
   const size_t o_scr = bytes;
   bytes = align(bytes + (size_t)batch * sl.total * sizeof(double2));
   const size_t o_cscr = bytes;
@@ -588,6 +590,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.dstats = (double*)(base + o_dstats);
   e.dec = (int*)(base + o_dec);
   e.weyl = (int8_t*)(base + o_weyl);
+  e.lastsc = (double*)(base + o_last);
   e.scr = (double2*)(base + o_scr);
   e.cscr = (double2*)(base + o_cscr);
   e.sing = (double*)(base + o_sing);
@@ -895,6 +898,29 @@ int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* c
   return device_status(h);
 }
 
+int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, int32_t* dims) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  const int n = h->e.n;
+  if (site < 0 || site >= n || !dims) return fail(h, GCAMPS_EINVAL, "bad site or null dims");
+  int dd[2];
+  GC_CUDA(h, cudaMemcpyAsync(dd, h->e.dims + (long long)circuit * (n + 1) + site, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
+  long long off = 0;
+  GC_CUDA(h, cudaMemcpyAsync(&off, h->e.site_off + site, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  dims[0] = dd[0];
+  dims[1] = h->e.d;
+  dims[2] = dd[1];
+  const long long nel = (long long)dd[0] * h->e.d * dd[1];
+  if (t) {
+    if (cap < nel) return fail(h, GCAMPS_EINVAL, "site buffer too small");
+    GC_CUDA(h, cudaMemcpy(t, h->e.mps + (long long)circuit * h->e.mps_stride + off, (size_t)nel * sizeof(double2),
+                          cudaMemcpyDeviceToHost));
+  }
+  return device_status(h);
+}
+
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
@@ -932,10 +958,76 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   st->accepted = s[gcx::S_ACC];
   st->sweeps = s[gcx::S_SWEEPS];
   st->vn_evaluations = s[gcx::S_VN];
+  st->svd_calls = s[gcx::S_SVD];
+  st->jacobi_sweeps = s[gcx::S_JSWEEPS];
+  st->jacobi_max_sweeps = s[gcx::S_JMAX];
+  st->qr_calls = s[gcx::S_QR];
   st->max_chi = (int32_t)s[gcx::S_MAXCHI];
   st->status = meta[gcx::M_STATUS];
   st->discarded_weight = ds[0];
   st->scoring_flops = ds[1];
+  return device_status(h);
+}
+
+int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* s2, double* vn,
+                       int32_t* choice) {
+  if (!h) return GCAMPS_EINVAL;
+  const int d = h->e.d;
+  if (!theta || !s2 || !vn || chi_l < 1 || chi_r < 1 || chi_l > h->e.maxdim / d || chi_r > h->e.maxdim / d)
+    return fail(h, GCAMPS_EINVAL, "bad theta shape or null pointer");
+  const size_t nel = (size_t)chi_l * d * d * chi_r;
+  double2* th = nullptr;
+  double* out = nullptr;
+  cudaError_t ce = cudaMalloc(&th, nel * sizeof(double2));
+  if (ce == cudaSuccess) ce = cudaMalloc(&out, (2 * gcx::kMaxK + 2) * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(th, theta, nel * sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  int* ch_dev = reinterpret_cast<int*>(out + 2 * gcx::kMaxK);
+  if (ce == cudaSuccess)
+    ce = gcx::launch_score_theta(h->e, th, chi_l, chi_r, out, out + gcx::kMaxK, ch_dev, h->stream);
+  std::vector<double> host(2 * gcx::kMaxK + 2);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(host.data(), out, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (th) cudaFree(th);
+  if (out) cudaFree(out);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "score_theta");
+  for (int k = 0; k < h->e.K; ++k) {
+    s2[k] = host[k];
+    vn[k] = host[gcx::kMaxK + k];
+  }
+  if (choice) std::memcpy(choice, &host[2 * gcx::kMaxK], 2 * sizeof(int32_t));
+  return device_status(h);
+}
+
+int gcamps_get_last_theta(gcamps_t* h, int circuit, double* theta, int32_t* shape) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  std::vector<double> buf(3 * gcx::kMaxK + 2 + 2 * gcx::kSmall);
+  GC_CUDA(h, cudaMemcpyAsync(buf.data(), h->e.lastsc + (long long)circuit * buf.size(), buf.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int cl = (int)buf[3 * gcx::kMaxK], cr = (int)buf[3 * gcx::kMaxK + 1], d = h->e.d;
+  if (shape) {
+    shape[0] = cl;
+    shape[1] = cr;
+  }
+  const long long nel = (long long)cl * d * d * cr;
+  if (theta && nel <= gcx::kSmall) std::memcpy(theta, &buf[3 * gcx::kMaxK + 2], (size_t)nel * 2 * sizeof(double));
+  return device_status(h);
+}
+
+int gcamps_get_last_scores(gcamps_t* h, int circuit, double* s2, double* vn, uint8_t* evaluated) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  std::vector<double> buf(3 * gcx::kMaxK + 2 + 2 * gcx::kSmall);
+  GC_CUDA(h, cudaMemcpyAsync(buf.data(), h->e.lastsc + (long long)circuit * buf.size(), buf.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < h->e.K; ++k) {
+    if (s2) s2[k] = buf[k];
+    if (vn) vn[k] = buf[gcx::kMaxK + k];
+    if (evaluated) evaluated[k] = (uint8_t)(buf[2 * gcx::kMaxK + k] != 0.0);
+  }
   return device_status(h);
 }
 

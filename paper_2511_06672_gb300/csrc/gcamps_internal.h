@@ -23,7 +23,8 @@ enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_DIAG_
             M_COUNT };
 // stats: S_VN counts exact von Neumann evaluations (the rest were excluded by the Renyi-2 bound)
 // stats[] counters per circuit (int64)
-enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN, S_COUNT };
+enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN, S_SVD, S_JSWEEPS, S_JMAX,
+            S_QR, S_COUNT };
 
 // Scratch areas of one circuit, as element offsets (double2) from its scratch base.
 struct ScratchLayout {
@@ -61,6 +62,7 @@ struct Engine {
   double* dstats;                           // [batch][2]: discarded weight, spare
   int* dec;                                 // [batch][kDecCap][2]
   int8_t* weyl;                             // [batch][2n]
+  double* lastsc;                           // [batch][3 * kMaxK + 2 + 2 * kSmall]: s2 | vn | evaluated | chi_l, chi_r | theta of the last visit
   double2* scr;     ScratchLayout sl;       // per-circuit scratch, stride sl.total
   double2* cscr;    CtaLayout cl;           // per-CTA scratch, stride cl.total
   double* sing;     long long sing_stride;  // singular values / eigenvalues
@@ -78,6 +80,8 @@ cudaError_t launch_expect(const Engine& e, int circuit, const int8_t* xz_dev, do
                           cudaStream_t st);
 cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, long long dim,
                                const int32_t* ys_dev, long long nys, void* work, cudaStream_t st);
+cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
+                               int* choice, cudaStream_t st);
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
                            cudaStream_t st);
 
