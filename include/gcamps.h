@@ -44,6 +44,7 @@ extern "C" {
 #define GCAMPS_ECUDA 3   /* a CUDA runtime call failed                                */
 #define GCAMPS_ENOCONV 4 /* a device iteration (Jacobi SVD, eigenvalues) hit its cap  */
 #define GCAMPS_ECHI 5    /* chi_max bound while discarding weight above strict_weight */
+#define GCAMPS_ESIZE 6   /* a size beyond the fixed maximum of gcamps_score_theta_noalloc */
 
 typedef struct gcamps gcamps_t;
 
@@ -202,6 +203,40 @@ int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, 
  * Renyi-2 pruning evaluated.  Synchronising. */
 int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* s2, double* vn,
                        int32_t* choice);
+
+/* The class scores of gcamps_score_theta for callers that cannot allocate device memory: code
+ * whose GPU memory belongs to another allocator (a framework's memory pool that has already
+ * reserved the device, or a fixed per-process memory budget), and latency-critical loops that
+ * cannot take the device-wide synchronisation cudaMalloc and cudaFree may cause.  The paper has no
+ * counterpart of this call; it is a deployment variant of the disentangler scoring.
+ *
+ * It needs no handle and allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).  Its working memory is one static device array of this library, 1,643,520 bytes, that
+ * every GPU which loads the library holds until the process exits.  That array fixes the largest
+ * tensor: chi_l d <= GCAMPS_NOALLOC_MAX_SIDE and d chi_r <= GCAMPS_NOALLOC_MAX_SIDE, i.e. chi <= 27
+ * for qutrits and chi <= 40 for qubits; a larger shape returns GCAMPS_ESIZE and launches nothing.
+ *
+ * Every pointer is device memory of the current device, owned by the caller.  theta_dev: chi_l x d
+ * x d x chi_r complex entries (interleaved re, im; row-major over (a, s, t, b)).  s2_dev, vn_dev:
+ * K = gcamps_num_candidates(d) doubles each, the Renyi-2 and von Neumann entropies of every class
+ * as in gcamps_score_theta.  choice_dev: 3 int32, the class the disentangler would apply (0 = none;
+ * a class is applied only if it lowers the entropy by more than tie_tol, ties to the lowest index),
+ * the number of exact entropies its Renyi-2 pruning evaluated, and the device status of the call
+ * (0, or GCAMPS_ENOCONV when an eigenvalue iteration hit its cap).  cuda_stream: the cudaStream_t
+ * to run on, NULL for the default stream.  Asynchronous: the outputs are valid once the stream has
+ * passed this call.
+ *
+ * The first call on a device, with that device current, does a one-time set-up: it looks up the
+ * device address of the static array and copies the class tables into static device memory
+ * (synchronous copies).  Make that first call before any stream capture.  All calls on a device
+ * share the one array and it keeps the last call's contents; each call clears the words that must
+ * start at zero itself.  Calls whose kernels overlap on the GPU (several streams, or several host
+ * threads at once) race on the array and give wrong results: serialise them.
+ * Returns GCAMPS_OK; GCAMPS_EINVAL (d not 2 or 3, a null pointer, chi < 1, tie_tol < 0 or NaN);
+ * GCAMPS_ESIZE; GCAMPS_ECUDA (set-up or launch failed). */
+#define GCAMPS_NOALLOC_MAX_SIDE 81
+int gcamps_score_theta_noalloc(int d, int chi_l, int chi_r, const double* theta_dev, double* s2_dev,
+                               double* vn_dev, int32_t* choice_dev, double tie_tol, void* cuda_stream);
 
 /* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded. */
 int gcamps_sync(gcamps_t* h);

@@ -15,6 +15,7 @@ from . import _native as N
 from ._native import OP_DTYPE, OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE
 
 __all__ = ["Simulator", "GcampsError", "sp4_images", "num_candidates", "candidate", "ops_from_gates",
+           "score_theta_noalloc",
            "OP_DTYPE", "OP_CLIFFORD", "OP_NONCLIFFORD", "OP_DISENTANGLE"]
 
 
@@ -54,6 +55,26 @@ def candidate(d: int, k: int):
     if rc:
         raise GcampsError(rc, "bad class index")
     return img, (u[0::2] + 1j * u[1::2]).reshape(d * d, d * d)
+
+
+def _dev_ptr(x) -> int:
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def score_theta_noalloc(d: int, chi_l: int, chi_r: int, theta_dev, s2_dev, vn_dev, choice_dev,
+                        tie_tol: float = 1e-10, stream=None) -> None:
+    """gcamps_score_theta_noalloc: class scores on caller-owned device buffers, with the library's
+    static working memory (no device allocation).  Buffers are torch CUDA tensors or raw device
+    addresses: theta (chi_l, d, d, chi_r) complex128, s2 and vn K float64, choice 3 int32.  stream:
+    a torch.cuda.Stream, a raw cudaStream_t, or None (default stream).  Asynchronous."""
+    lib = N.load()
+    st = getattr(stream, "cuda_stream", stream) or None
+    rc = lib.gcamps_score_theta_noalloc(d, chi_l, chi_r, _dev_ptr(theta_dev), _dev_ptr(s2_dev), _dev_ptr(vn_dev),
+                                        _dev_ptr(choice_dev), float(tie_tol), st)
+    if rc:
+        raise GcampsError(rc, "score_theta_noalloc: " + {N.EINVAL: "bad argument",
+                                                          N.ESIZE: f"chi d above {N.NOALLOC_MAX_SIDE}",
+                                                          N.ECUDA: "CUDA set-up or launch failed"}.get(rc, ""))
 
 
 def ops_from_gates(gates: Iterable, d: int, disentangle_after_t: bool = True) -> np.ndarray:

@@ -8,7 +8,8 @@ import numpy as np
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libgcamps.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI = 0, 1, 2, 3, 4, 5
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE = 0, 1, 2, 3, 4, 5, 6
+NOALLOC_MAX_SIDE = 81
 OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE = 1, 2, 3
 
 OP_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("img", "<i4", (20,)),
@@ -42,7 +43,7 @@ EXPORTS = [
     "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
     "gcamps_get_stats",
-    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
+    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
 ]
 
 _lib = None
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
         "gcamps_get_stats": (C.c_int, [vp, C.c_int, C.POINTER(Stats)]),
         "gcamps_get_decisions": (C.c_int, [vp, C.c_int, i32p, C.c_int32, i32p]),
         "gcamps_score_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp, i32p]),
+        "gcamps_score_theta_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_double, vp]),
         "gcamps_get_last_scores": (C.c_int, [vp, C.c_int, dp, dp, u8p]),
         "gcamps_get_last_theta": (C.c_int, [vp, C.c_int, dp, i32p]),
         "gcamps_sync": (C.c_int, [vp]),

@@ -999,6 +999,38 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
   return device_status(h);
 }
 
+int gcamps_score_theta_noalloc(int d, int chi_l, int chi_r, const double* theta_dev, double* s2_dev, double* vn_dev,
+                               int32_t* choice_dev, double tie_tol, void* cuda_stream) {
+  if ((d != 2 && d != 3) || !theta_dev || !s2_dev || !vn_dev || !choice_dev || chi_l < 1 || chi_r < 1 ||
+      !(tie_tol >= 0.0))
+    return GCAMPS_EINVAL;
+  if (chi_l * d > GCAMPS_NOALLOC_MAX_SIDE || chi_r * d > GCAMPS_NOALLOC_MAX_SIDE) return GCAMPS_ESIZE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GCAMPS_ECUDA;
+  if (dev < 0 || dev >= gcx::kStaticMaxDevices) return GCAMPS_ECUDA;
+  {
+    // Once per device, with that device current: the device addresses of the library's static
+    // arrays and the class tables of d = 2 and 3.
+    static std::mutex mu;
+    static bool ready[gcx::kStaticMaxDevices] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+      const Tables& t2 = tables(2);
+      const Tables& t3 = tables(3);
+      if (t2.u.size() != (size_t)gcx::kStaticK2 * 16 * 2 || t3.u.size() != (size_t)gcx::kStaticK3 * 81 * 2 ||
+          t2.img.size() != (size_t)gcx::kStaticK2 * 20 || t3.img.size() != (size_t)gcx::kStaticK3 * 20)
+        return GCAMPS_EINVAL;
+      if (gcx::static_setup(dev, t2.u.data(), t2.img.data(), t3.u.data(), t3.img.data()) != cudaSuccess)
+        return GCAMPS_ECUDA;
+      ready[dev] = true;
+    }
+  }
+  const cudaError_t ce = gcx::launch_score_theta_static(dev, d, tie_tol, reinterpret_cast<const double2*>(theta_dev),
+                                                        chi_l, chi_r, s2_dev, vn_dev, choice_dev,
+                                                        static_cast<cudaStream_t>(cuda_stream));
+  return ce == cudaSuccess ? GCAMPS_OK : GCAMPS_ECUDA;
+}
+
 int gcamps_get_last_theta(gcamps_t* h, int circuit, double* theta, int32_t* shape) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;

@@ -85,4 +85,22 @@ cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int c
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
                            cudaStream_t st);
 
+// gcamps_score_theta_noalloc: class scores with every scratch word in static device memory of this
+// library (no allocation).  theta is at most kStaticSide x kStaticSide (rows chi_l d, columns
+// d chi_r); kStaticCluster CTAs score it.
+constexpr int kStaticSide = 81;
+static_assert(kStaticSide == GCAMPS_NOALLOC_MAX_SIDE, "limit stated in gcamps.h");
+constexpr int kStaticCluster = 4;
+constexpr int kStaticMaxDevices = 64;
+constexpr int kStaticK2 = 20, kStaticK3 = 90;   // classes for d = 2, 3
+// One-time setup for `device`, which must be current: the static arrays' device addresses (checked)
+// and the class tables (unitaries [K][d^4] complex, images [K][20]) of d = 2 and d = 3, copied
+// synchronously.
+cudaError_t static_setup(int device, const double* u2, const int32_t* img2, const double* u3,
+                         const int32_t* img3);
+// Launches the scoring of theta (device memory) on stream st with the static scratch of `device`
+// (static_setup done).  s2, vn: K doubles; choice: class, exact evaluations, status.
+cudaError_t launch_score_theta_static(int device, int d, double tie_tol, const double2* th, int cl, int cr,
+                                      double* s2, double* vn, int32_t* choice, cudaStream_t st);
+
 }  // namespace gcx
