@@ -30,7 +30,19 @@ namespace {
 namespace cg = cooperative_groups;
 
 // Classes are scored with the Renyi-2 bound first when the Gram has more rows than this.
-constexpr int kPruneMin = 9;
+constexpr int kPruneMin = 1;
+// CTA-level scoring computes eigenvalues by bisection (one per thread) above this Gram size, and by
+// the serial implicit QR of one thread below it.
+constexpr int kBisectMin = 20;
+
+// (i, j), j <= i, of entry t of the row-major packed lower triangle (t = i (i + 1) / 2 + j).
+__device__ __forceinline__ void tri_index(int t, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  i = r;
+  j = t - r * (r + 1) / 2;
+}
 
 // ------------------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
@@ -94,6 +106,7 @@ struct Smem {
   uint8_t evald[kMaxK];       // vn[k] valid
   int list[kMaxK];            // classes to evaluate next (cluster leader)
   int nlist;
+  int rank0;                  // numerical rank of the identity class's Gram (cluster leader; -1 = none)
   int bcast;
   double red[kWarps * 4];
   double2 coef[4];            // MPO term coefficients c_m tau^{...}
@@ -376,7 +389,7 @@ __device__ void fold_candidate(Smem& s, const Ctx& C, int k, int q0) {
 // Orthogonalises the n columns of B (m x n, column-major) by complex Jacobi rotations applied
 // from the right, accumulating them in W (n x n, column-major, starts as I):  B_in W = B_out.
 // Round-robin ordering: in each round the n/2 column pairs are disjoint and handled by the
-// warps in parallel.  A pair is rotated while |b_i^H b_j| > tol * |b_i| |b_j|, unless one of the
+// warps in parallel.  A pair is rotated while |b_i^H b_j| > 1e-14 |b_i| |b_j|, unless one of the
 // two columns is numerically zero (|b|^2 <= 1e-30 |B|_F^2): the direction of such a column is
 // rounding noise, rotating it never settles, and its singular value lies below any truncation
 // cutoff.  Returns the number of sweeps, or -1 if `max_sweeps` were not enough.
@@ -388,12 +401,13 @@ __device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* 
   for (long long i = threadIdx.x; i < (long long)m * n; i += blockDim.x) fro += cabs2(B[i]);
   fro = block_sum(fro, s);
   const double zero_col = 1e-30 * fro;
+  const long long zc_bits = __double_as_longlong(zero_col);
   if (threadIdx.x == 0) s.flag = 0;
   __syncthreads();
   if (n <= 1) return 0;
   const int N = n + (n & 1);
   const int npairs = N / 2;
-  const double tol = 1e-14;
+  const double tol2 = 1e-28;   // rotate while |b_i^H b_j| > 1e-14 |b_i| |b_j|
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int round = 0; round < N - 1; ++round) {
       for (int p = warp; p < npairs; p += kWarps) {
@@ -415,14 +429,17 @@ __device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* 
         be = warp_sum(be);
         gr = warp_sum(gr);
         gi = warp_sum(gi);
-        const double g = hypot(gr, gi);
-        if (al <= zero_col || be <= zero_col) continue;
-        if (!(g > tol * sqrt(al) * sqrt(be)) || g < 1e-300) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t);
+        // al, be >= 0: compared as integers (off the FP64 pipe)
+        if (__double_as_longlong(al) <= zc_bits || __double_as_longlong(be) <= zc_bits) continue;
+        const double g2 = fma(gr, gr, gi * gi);
+        if (!(g2 > tol2 * al * be) || g2 < 1e-290) continue;   // |gamma| <= tol sqrt(al be)
+        const double ig = rsqrt(g2);                            // 1 / |gamma|
+        const double zeta = (be - al) * 0.5 * ig;
+        const double t = fabs(zeta) < 1e150 ? copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)))
+                                            : 0.5 / zeta;
+        const double cs = rsqrt(fma(t, t, 1.0));
         const double sn = cs * t;
-        const double2 e = make_double2(gr / g, gi / g);     // gamma / |gamma|
+        const double2 e = make_double2(gr * ig, gi * ig);      // gamma / |gamma|
         const double2 se = cscale(e, sn), sec = cscale(cconj(e), sn);
         // b_i' = cs b_i - sn conj(e) b_j ; b_j' = sn e b_i + cs b_j
         for (int r = lane; r < m; r += 32) {
@@ -996,9 +1013,9 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
       A[(long long)k * m + k + 1 + i] = make_double2(p.x - kr * v.x, p.y - kr * v.y);
     }
     g.sync();
-    for (int idx = g.tid; idx < r * r; idx += g.n) {
-      const int i = idx / r, j = idx % r;
-      if (j > i) continue;
+    for (int idx = g.tid; idx < r * (r + 1) / 2; idx += g.n) {
+      int i, j;
+      tri_index(idx, i, j);
       const double2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
       const double2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
       const double2 t = cadd(cmul(vi, cconj(wj)), cmul(wi, cconj(vj)));
@@ -1021,24 +1038,32 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
   g.sync();
 }
 
+// |v| > t for t >= 0, compared as integers (the bit patterns of non-negative doubles are ordered
+// like their values), which keeps these tests off the FP64 pipe.
+__device__ __forceinline__ bool abs_above(double v, long long t_bits) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) > t_bits;
+}
+
 // Eigenvalues of the symmetric tridiagonal (dg, od) by implicit QR steps with the Wilkinson
 // shift (bulge chased from the top of the unreduced block), deflating from the bottom when an
 // off-diagonal falls below eps * |T|.  Eigenvalues overwrite dg.  Returns false at the cap.
+// The rotation (c, s) = (x, z) / |(x, z)| uses one reciprocal square root instead of a hypot and
+// two divisions (a scaled hypot only where |(x, z)|^2 would leave the normal range).
 __device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
   if (m <= 1) return true;
   double tn = 0;
   for (int i = 0; i < m; ++i) tn += fabs(dg[i]);
   for (int i = 0; i + 1 < m; ++i) tn += fabs(od[i]);
-  const double thr = 2.220446049250313e-16 * tn;
+  const long long thr = __double_as_longlong(2.220446049250313e-16 * tn);
   int hi = m - 1, iters = 0;
   while (hi > 0) {
-    if (fabs(od[hi - 1]) <= thr) {
+    if (!abs_above(od[hi - 1], thr)) {
       od[hi - 1] = 0.0;
       --hi;
       continue;
     }
     int lo = hi - 1;
-    while (lo > 0 && fabs(od[lo - 1]) > thr) --lo;
+    while (lo > 0 && abs_above(od[lo - 1], thr)) --lo;
     if (++iters > 60 * m) return false;
     const double a = dg[hi - 1], b = od[hi - 1], c = dg[hi];
     const double delta = 0.5 * (a - c);
@@ -1046,11 +1071,21 @@ __device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
     const double mu = (den != 0.0) ? c - b * b / den : c - fabs(b);
     double x = dg[lo] - mu, z = od[lo];
     for (int k = lo; k < hi; ++k) {
-      const double rr = hypot(x, z);
-      double cs = 1.0, sn = 0.0;
-      if (rr > 0.0) {
-        cs = x / rr;
-        sn = z / rr;
+      const double r2 = fma(x, x, z * z);
+      double rr, cs, sn;
+      if (r2 > 1e-280 && r2 < 1e280) {
+        const double ir = rsqrt(r2);
+        rr = r2 * ir;
+        cs = x * ir;
+        sn = z * ir;
+      } else {
+        rr = hypot(x, z);
+        cs = 1.0;
+        sn = 0.0;
+        if (rr > 0.0) {
+          cs = x / rr;
+          sn = z / rr;
+        }
       }
       if (k > lo) od[k - 1] = rr;
       const double ak = dg[k], bk = od[k], ck = dg[k + 1];
@@ -1069,8 +1104,51 @@ __device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
   return true;
 }
 
+// Number of eigenvalues below x of the symmetric tridiagonal (dg, e2 = off-diagonal squared):
+// the count of negative pivots of T - x I = L D L^T (Sylvester's law of inertia), with pivots of
+// magnitude below pivmin replaced by -pivmin.
+__device__ __forceinline__ int sturm_count(const double* dg, const double* e2, int m, double x, double pivmin) {
+  const long long pm = __double_as_longlong(pivmin);
+  double q = dg[0] - x;
+  if (!abs_above(q, pm)) q = -pivmin;
+  int cnt = __double_as_longlong(q) < 0;
+  for (int i = 1; i < m; ++i) {
+    q = (dg[i] - x) - e2[i - 1] / q;
+    if (!abs_above(q, pm)) q = -pivmin;
+    cnt += __double_as_longlong(q) < 0;
+  }
+  return cnt;
+}
+
+// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by bisection, one
+// eigenvalue per thread of the group: eigenvalue j (ascending) is the point where the Sturm count
+// passes j.  The spectrum lies in [0, tr]; 56 halvings of that interval leave each eigenvalue
+// within 2^-56 tr.  od is overwritten with its squares; ev receives the m eigenvalues.
+template <class Grp>
+__device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m, double* ev) {
+  double tr = 0;
+  for (int i = g.tid; i < m; i += g.n) tr += dg[i];
+  tr = g.sum(tr);
+  for (int i = g.tid; i + 1 < m; i += g.n) od[i] = od[i] * od[i];
+  g.sync();
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, tr * tr);
+  const double span = fabs(tr) + 1e-300;
+  const double gl = -4.440892098500626e-16 * span, gu = tr + 4.440892098500626e-16 * span;
+  for (int j = g.tid; j < m; j += g.n) {
+    double lo = gl, hi = gu;
+    for (int it = 0; it < 56; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (sturm_count(dg, od, m, mid, pivmin) > j) hi = mid;
+      else lo = mid;
+    }
+    ev[j] = 0.5 * (lo + hi);
+  }
+  g.sync();
+}
+
 struct Score {
   double s2, vn;
+  int rank;   // eigenvalues above max(1e-12, 4 cutoff^2) tr G (von Neumann evaluations only)
   bool ok;
 };
 
@@ -1098,9 +1176,10 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   }
   g.sync();
   double tr = 0, fro = 0;
-  for (int idx = g.tid; idx < m * m; idx += g.n) {
-    const int i = idx / m, j = idx % m;
-    if (j > i) continue;
+  const int ntri = m * (m + 1) / 2;
+  for (int idx = g.tid; idx < ntri; idx += g.n) {
+    int i, j;
+    tri_index(idx, i, j);
     double2 acc = cz();
     if (rows <= cols) {
       const double2* ri = tp + (long long)i * cols;
@@ -1109,7 +1188,7 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
     } else {
       for (int r = 0; r < rows; ++r) acc = cfmac(tp[(long long)r * cols + i], tp[(long long)r * cols + j], acc);
     }
-    G[idx] = acc;
+    G[(long long)i * m + j] = acc;
     if (i == j) {
       tr += acc.x;
       fro += acc.x * acc.x;
@@ -1124,23 +1203,35 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   sc.ok = true;
   sc.s2 = (tr > 0.0 && fro > 0.0) ? -log(fro / (tr * tr)) : 0.0;
   sc.vn = sc.s2;
+  sc.rank = -1;
   if (!want_vn) return sc;
   g.sync();
   group_tridiag(g, G, m, dg, od);
-  double ent = 0.0, okv = 1.0;
-  if (g.tid == 0) {
-    okv = tridiag_eigenvalues(dg, od, m) ? 1.0 : 0.0;
-    double tot = 0;
-    for (int i = 0; i < m; ++i) tot += fmax(dg[i], 0.0);
-    if (tot > 0) {
-      const double inv = 1.0 / tot;
-      for (int i = 0; i < m; ++i) {
-        const double p = fmax(dg[i], 0.0) * inv;
-        if (p > 0) ent -= p * log(p);
-      }
+  double* ev = dg;
+  double okv = 1.0;
+  if (g.n > 32 && m > kBisectMin) {
+    ev = reinterpret_cast<double*>(G);   // G is dead after the reduction
+    tridiag_bisect(g, dg, od, m, ev);
+  } else {
+    if (g.tid == 0) okv = tridiag_eigenvalues(dg, od, m) ? 1.0 : 0.0;
+    g.sync();
+  }
+  // entropy -sum p ln p (p = lambda / tr) and the numerical rank, summed over the group
+  double tot = 0;
+  for (int i = g.tid; i < m; i += g.n) tot += fmax(ev[i], 0.0);
+  tot = g.sum(tot);
+  double ent = 0.0, rk = 0.0;
+  if (tot > 0) {
+    const double inv = 1.0 / tot;
+    const double rthr = fmax(1e-12, 4.0 * C.e->cutoff * C.e->cutoff);
+    for (int i = g.tid; i < m; i += g.n) {
+      const double p = fmax(ev[i], 0.0) * inv;
+      if (p > 0) ent -= p * log(p);
+      if (p > rthr) rk += 1.0;
     }
   }
-  sc.vn = g.bcast(ent);
+  sc.vn = g.sum(ent);
+  sc.rank = (int)g.sum(rk);
   sc.ok = g.bcast(okv) != 0.0;
   return sc;
 }
@@ -1167,6 +1258,7 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         if (want_vn) {
           lead->vn[k] = sc.vn;
           lead->evald[k] = 1;
+          if (k == 0) lead->rank0 = sc.rank;
         }
         if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
       }
@@ -1182,6 +1274,7 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         if (want_vn) {
           lead->vn[k] = sc.vn;
           lead->evald[k] = 1;
+          if (k == 0) lead->rank0 = sc.rank;
         }
         if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
       }
@@ -1287,6 +1380,7 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   if (leader) {
     const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
     block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
+    if (threadIdx.x == 0) s.rank0 = -1;
   }
   cluster_sync();
   const int cl = C.dims[i], cr = C.dims[i + 2];
@@ -1331,7 +1425,20 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     ++*accepted;
   }
   const int bb = e.bond_bound[i + 1];
-  Factor F = svd_factor(s, C, theta, rows, cols, e.chi_max < bb ? e.chi_max : bb, true);
+  const int cap = e.chi_max < bb ? e.chi_max : bb;
+  // Nothing applied and the identity class's Gram has exactly chi eigenvalues above
+  // max(1e-12, 4 cutoff^2) tr (theta has rank <= chi, the bond dimension): every one of those
+  // Schmidt values is above 1e-6 s_0 and above the cutoff, so the truncated SVD would keep the bond
+  // as it is.  A QR move of the centre gives the same state and bond dimension without it.
+  const int chim = C.dims[i + 1];
+  if (kb == 0 && s.rank0 == chim && chim <= cap) {
+    if (ltr) move_right(s, C, i);
+    else move_left_qr(s, C, i + 1);
+    note_chi(C, chim);
+    __syncthreads();
+    return;
+  }
+  Factor F = svd_factor(s, C, theta, rows, cols, cap, true);
   const int k = F.k;
   if (ltr) {
     for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
