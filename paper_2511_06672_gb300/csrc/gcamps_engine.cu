@@ -31,9 +31,8 @@ namespace cg = cooperative_groups;
 
 // Classes are scored with the Renyi-2 bound first when the Gram has more rows than this.
 constexpr int kPruneMin = 1;
-// CTA-level scoring computes eigenvalues by bisection (one per thread) above this Gram size, and by
-// the serial implicit QR of one thread below it.
-constexpr int kBisectMin = 20;
+// CTA-level eigenvalue bisection keeps the tridiagonal in shared memory up to this size.
+constexpr int kBTri = 256;
 
 // (i, j), j <= i, of entry t of the row-major packed lower triangle (t = i (i + 1) / 2 + j).
 __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
@@ -107,6 +106,11 @@ struct Smem {
   int list[kMaxK];            // classes to evaluate next (cluster leader)
   int nlist;
   int rank0;                  // numerical rank of the identity class's Gram (cluster leader; -1 = none)
+  int ord[kMaxK];             // rank of each class in ascending S2 (cluster leader)
+  double wtri[kWarps][64];    // per warp: tridiagonal diagonal [0, 32) | off-diagonal squared [32, 64)
+  float wtri32[kWarps][64];   // the same in FP32
+  double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
+  float btri32[2 * kBTri];
   int bcast;
   double red[kWarps * 4];
   double2 coef[4];            // MPO term coefficients c_m tau^{...}
@@ -1038,107 +1042,153 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
   g.sync();
 }
 
-// |v| > t for t >= 0, compared as integers (the bit patterns of non-negative doubles are ordered
-// like their values), which keeps these tests off the FP64 pipe.
-__device__ __forceinline__ bool abs_above(double v, long long t_bits) {
-  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) > t_bits;
+// Integer key with the order of the double v (no NaN): sorting keys sorts values, off the FP64 pipe.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
 }
 
-// Eigenvalues of the symmetric tridiagonal (dg, od) by implicit QR steps with the Wilkinson
-// shift (bulge chased from the top of the unreduced block), deflating from the bottom when an
-// off-diagonal falls below eps * |T|.  Eigenvalues overwrite dg.  Returns false at the cap.
-// The rotation (c, s) = (x, z) / |(x, z)| uses one reciprocal square root instead of a hypot and
-// two divisions (a scaled hypot only where |(x, z)|^2 would leave the normal range).
-__device__ bool tridiag_eigenvalues(double* dg, double* od, int m) {
-  if (m <= 1) return true;
-  double tn = 0;
-  for (int i = 0; i < m; ++i) tn += fabs(dg[i]);
-  for (int i = 0; i + 1 < m; ++i) tn += fabs(od[i]);
-  const long long thr = __double_as_longlong(2.220446049250313e-16 * tn);
-  int hi = m - 1, iters = 0;
-  while (hi > 0) {
-    if (!abs_above(od[hi - 1], thr)) {
-      od[hi - 1] = 0.0;
-      --hi;
-      continue;
-    }
-    int lo = hi - 1;
-    while (lo > 0 && abs_above(od[lo - 1], thr)) --lo;
-    if (++iters > 60 * m) return false;
-    const double a = dg[hi - 1], b = od[hi - 1], c = dg[hi];
-    const double delta = 0.5 * (a - c);
-    const double den = delta + copysign(hypot(delta, b), delta);
-    const double mu = (den != 0.0) ? c - b * b / den : c - fabs(b);
-    double x = dg[lo] - mu, z = od[lo];
-    for (int k = lo; k < hi; ++k) {
-      const double r2 = fma(x, x, z * z);
-      double rr, cs, sn;
-      if (r2 > 1e-280 && r2 < 1e280) {
-        const double ir = rsqrt(r2);
-        rr = r2 * ir;
-        cs = x * ir;
-        sn = z * ir;
-      } else {
-        rr = hypot(x, z);
-        cs = 1.0;
-        sn = 0.0;
-        if (rr > 0.0) {
-          cs = x / rr;
-          sn = z / rr;
-        }
-      }
-      if (k > lo) od[k - 1] = rr;
-      const double ak = dg[k], bk = od[k], ck = dg[k + 1];
-      const double cc = cs * cs, ss = sn * sn, c2 = 2.0 * cs * sn;
-      dg[k] = cc * ak + c2 * bk + ss * ck;
-      dg[k + 1] = ss * ak - c2 * bk + cc * ck;
-      od[k] = cs * sn * (ck - ak) + (cc - ss) * bk;
-      if (k + 1 < hi) {
-        const double fo = od[k + 1];
-        z = sn * fo;
-        od[k + 1] = cs * fo;
-        x = od[k];
-      }
-    }
-  }
-  return true;
-}
-
-// Number of eigenvalues below x of the symmetric tridiagonal (dg, e2 = off-diagonal squared):
-// the count of negative pivots of T - x I = L D L^T (Sylvester's law of inertia), with pivots of
-// magnitude below pivmin replaced by -pivmin.
-__device__ __forceinline__ int sturm_count(const double* dg, const double* e2, int m, double x, double pivmin) {
-  const long long pm = __double_as_longlong(pivmin);
-  double q = dg[0] - x;
-  if (!abs_above(q, pm)) q = -pivmin;
-  int cnt = __double_as_longlong(q) < 0;
+// Number of eigenvalues below x of the symmetric tridiagonal (dg, e2 = off-diagonal squared): the
+// number of sign changes along the leading principal minors f_0 = 1, f_1, ..., f_m of T - x I,
+// f_{i+1} = (d_i - x) f_i - e2_{i-1} f_{i-1} (Sturm sequence; a sign change is a negative LDL^T pivot
+// f_{i+1} / f_i, Sylvester's law of inertia).  A minor that is exactly zero counts as a negative pivot
+// (its sign is taken opposite to the previous one).  The pair (f_i, f_{i+1}) is rescaled by 2^-+500
+// whenever the larger leaves [2^-500, 2^500]; scaling by a positive power of two changes no sign.
+// Three FP64 instructions per step; the sign and exponent tests are integer operations.
+__device__ __forceinline__ int sturm_count(const double* dg, const double* e2, int m, double x) {
+  double f0 = 1.0, f1 = dg[0] - x;
+  long long b1 = __double_as_longlong(f1);
+  unsigned s1 = (b1 & 0x7fffffffffffffffLL) == 0 ? 1u : (unsigned)((unsigned long long)b1 >> 63);
+  int cnt = (int)s1;
   for (int i = 1; i < m; ++i) {
-    q = (dg[i] - x) - e2[i - 1] / q;
-    if (!abs_above(q, pm)) q = -pivmin;
-    cnt += __double_as_longlong(q) < 0;
+    double f2 = fma(dg[i] - x, f1, -e2[i - 1] * f0);
+    const long long b2 = __double_as_longlong(f2);
+    const int ex1 = (int)((b1 >> 52) & 0x7ff), ex2 = (int)((b2 >> 52) & 0x7ff);
+    const int ex = ex1 > ex2 ? ex1 : ex2;
+    if (ex > 1023 + 500) {
+      f1 *= 3.054936363499605e-151;   // 2^-500
+      f2 *= 3.054936363499605e-151;
+    } else if (ex < 1023 - 500) {
+      f1 *= 3.273390607896142e+150;   // 2^500
+      f2 *= 3.273390607896142e+150;
+    }
+    const long long c2 = __double_as_longlong(f2);
+    const unsigned s2 = (c2 & 0x7fffffffffffffffLL) == 0 ? (s1 ^ 1u) : (unsigned)((unsigned long long)c2 >> 63);
+    cnt += (int)(s2 != s1);
+    s1 = s2;
+    f0 = f1;
+    f1 = f2;
+    b1 = c2;
   }
   return cnt;
 }
 
-// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by bisection, one
-// eigenvalue per thread of the group: eigenvalue j (ascending) is the point where the Sturm count
-// passes j.  The spectrum lies in [0, tr]; 56 halvings of that interval leave each eigenvalue
-// within 2^-56 tr.  od is overwritten with its squares; ev receives the m eigenvalues.
+// FP32 version of sturm_count (rescaling by 2^-+40 outside [2^-40, 2^40]); it is exact for a matrix
+// within a few FP32 units of T, which bounds the bracket it gives (see tridiag_bisect).
+__device__ __forceinline__ int sturm_count32(const float* dg, const float* e2, int m, float x) {
+  float f0 = 1.0f, f1 = dg[0] - x;
+  int b1 = __float_as_int(f1);
+  unsigned s1 = (b1 & 0x7fffffff) == 0 ? 1u : ((unsigned)b1 >> 31);
+  int cnt = (int)s1;
+  for (int i = 1; i < m; ++i) {
+    float f2 = fmaf(dg[i] - x, f1, -e2[i - 1] * f0);
+    const int b2 = __float_as_int(f2);
+    const int ex1 = (b1 >> 23) & 0xff, ex2 = (b2 >> 23) & 0xff;
+    const int ex = ex1 > ex2 ? ex1 : ex2;
+    if (ex > 127 + 40) {
+      f1 *= 9.094947017729282e-13f;   // 2^-40
+      f2 *= 9.094947017729282e-13f;
+    } else if (ex < 127 - 40) {
+      f1 *= 1099511627776.0f;         // 2^40
+      f2 *= 1099511627776.0f;
+    }
+    const int c2 = __float_as_int(f2);
+    const unsigned s2 = (c2 & 0x7fffffff) == 0 ? (s1 ^ 1u) : ((unsigned)c2 >> 31);
+    cnt += (int)(s2 != s1);
+    s1 = s2;
+    f0 = f1;
+    f1 = f2;
+    b1 = c2;
+  }
+  return cnt;
+}
+
+// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by bisection, one eigenvalue
+// per thread of the group: eigenvalue j (ascending) is where the Sturm count passes j.  The spectrum
+// lies in [0, tr] (span = |tr|); each eigenvalue is located within 2^-50 span (an entropy error below
+// 1e-12 for the Gram sizes used here).
+//   sh, sh32: shared arrays of 2 cap entries for (diagonal | off-diagonal squared), or null.  With them
+//   (m <= cap) 24 FP32 halvings first bracket eigenvalue j; since an FP32 Sturm count is exact for a
+//   matrix within 8 FP32 units of span of T, the bracket padded by 40 units holds it, which two FP64
+//   counts confirm (else the full interval is used), and 33 FP64 halvings finish.  Without them, 50 FP64
+//   halvings of [0, span] on the global arrays.
+// Off-diagonal squares are at least 1e-300 span^2 (1e-20 span^2 in FP32), which moves no eigenvalue
+// by more than 1e-150 span (1e-10 span, inside the FP32 padding) and keeps an exactly zero minor from
+// zeroing the rest of the sequence.  od is overwritten with its squares; ev receives the m eigenvalues.
+// m <= 2 in closed form.
 template <class Grp>
-__device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m, double* ev) {
+__device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m, double* ev, double* sh,
+                               float* sh32, int cap) {
+  if (m <= 2) {
+    if (g.tid == 0) {
+      if (m == 1) {
+        ev[0] = dg[0];
+      } else {
+        const double mean = 0.5 * (dg[0] + dg[1]), r = hypot(0.5 * (dg[0] - dg[1]), od[0]);
+        ev[0] = mean - r;
+        ev[1] = mean + r;
+      }
+    }
+    g.sync();
+    return;
+  }
   double tr = 0;
   for (int i = g.tid; i < m; i += g.n) tr += dg[i];
   tr = g.sum(tr);
-  for (int i = g.tid; i + 1 < m; i += g.n) od[i] = od[i] * od[i];
-  g.sync();
-  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, tr * tr);
   const double span = fabs(tr) + 1e-300;
+  const double e2min = 1e-300 * span * span;
   const double gl = -4.440892098500626e-16 * span, gu = tr + 4.440892098500626e-16 * span;
+  const bool fast = sh != nullptr && m <= cap;
+  const double* D = dg;
+  const double* E = od;
+  if (fast) {
+    const float e2min32 = (float)(1e-20 * span * span);
+    for (int i = g.tid; i < m; i += g.n) {
+      sh[i] = dg[i];
+      sh32[i] = (float)dg[i];
+      if (i + 1 < m) {
+        const double e2 = fmax(od[i] * od[i], e2min);
+        sh[cap + i] = e2;
+        sh32[cap + i] = fmaxf((float)e2, e2min32);
+      }
+    }
+    D = sh;
+    E = sh + cap;
+  } else {
+    for (int i = g.tid; i + 1 < m; i += g.n) od[i] = fmax(od[i] * od[i], e2min);
+  }
+  g.sync();
   for (int j = g.tid; j < m; j += g.n) {
     double lo = gl, hi = gu;
-    for (int it = 0; it < 56; ++it) {
+    int nit = 50;
+    if (fast) {
+      float lo32 = (float)gl, hi32 = (float)gu;
+      for (int it = 0; it < 24; ++it) {
+        const float mid = 0.5f * (lo32 + hi32);
+        if (sturm_count32(sh32, sh32 + cap, m, mid) > j) hi32 = mid;
+        else lo32 = mid;
+      }
+      const double pad = 40.0 * 5.960464477539063e-08 * span;   // 40 FP32 units
+      const double a = (double)lo32 - pad, b = (double)hi32 + pad;
+      if (sturm_count(D, E, m, a) <= j && sturm_count(D, E, m, b) > j) {
+        lo = a;
+        hi = b;
+        nit = 33;
+      }
+    }
+    for (int it = 0; it < nit; ++it) {
       const double mid = 0.5 * (lo + hi);
-      if (sturm_count(dg, od, m, mid, pivmin) > j) hi = mid;
+      if (sturm_count(D, E, m, mid) > j) hi = mid;
       else lo = mid;
     }
     ev[j] = 0.5 * (lo + hi);
@@ -1157,7 +1207,7 @@ struct Score {
 // von Neumann entropy -sum p ln p from the eigenvalues of G (p = lambda / tr G).  S2 <= S_vN always.
 template <class Grp>
 __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
-                             double2* ws, long long gram_off, bool want_vn) {
+                             double2* ws, long long gram_off, bool want_vn, double* tri, float* tri32, int tricap) {
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
@@ -1207,15 +1257,8 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   if (!want_vn) return sc;
   g.sync();
   group_tridiag(g, G, m, dg, od);
-  double* ev = dg;
-  double okv = 1.0;
-  if (g.n > 32 && m > kBisectMin) {
-    ev = reinterpret_cast<double*>(G);   // G is dead after the reduction
-    tridiag_bisect(g, dg, od, m, ev);
-  } else {
-    if (g.tid == 0) okv = tridiag_eigenvalues(dg, od, m) ? 1.0 : 0.0;
-    g.sync();
-  }
+  double* ev = reinterpret_cast<double*>(G);   // G is dead after the reduction
+  tridiag_bisect(g, dg, od, m, ev, tri, tri32, tricap);
   // entropy -sum p ln p (p = lambda / tr) and the numerical rank, summed over the group
   double tot = 0;
   for (int i = g.tid; i < m; i += g.n) tot += fmax(ev[i], 0.0);
@@ -1232,7 +1275,7 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   }
   sc.vn = g.sum(ent);
   sc.rank = (int)g.sum(rk);
-  sc.ok = g.bcast(okv) != 0.0;
+  sc.ok = true;
   return sc;
 }
 
@@ -1249,10 +1292,13 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
   if (small) {
     WarpGroup g{lane};
     double2* ws = C.cta + e.cl.warp + (long long)warp * kSmallStride;
-    const int gw = C.rank * kWarps + warp, nw = C.csize * kWarps;
+    // consecutive list entries go to different CTAs, then to different warps: the first 4 csize
+    // entries land on distinct FP64 pipes (SM sub-partitions)
+    const int gw = warp * C.csize + C.rank, nw = C.csize * kWarps;
     for (int t = gw; t < cnt; t += nw) {
       const int k = list ? list[t] : t;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn);
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn,
+                                   s.wtri[warp], s.wtri32[warp], 32);
       if (lane == 0) {
         lead->s2[k] = sc.s2;
         if (want_vn) {
@@ -1268,7 +1314,8 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
     double2* ws = C.cta + e.cl.block;
     for (int t = C.rank; t < cnt; t += C.csize) {
       const int k = list ? list[t] : t;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn);
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn,
+                                   s.btri, s.btri32, kBTri);
       if (threadIdx.x == 0) {
         lead->s2[k] = sc.s2;
         if (want_vn) {
@@ -1288,8 +1335,9 @@ __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 // ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
 // One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
 // decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class;
-// round 1 evaluates S_vN of the identity and of the class with the smallest S2, giving an upper bound
-// B on the best entropy; round 2 evaluates every other class with S2 <= B + tie_tol.  A class left out
+// round 1 evaluates S_vN of the identity and of the classes with the smallest S2 (as many as the
+// cluster evaluates at once), giving an upper bound B on the best entropy; round 2 evaluates every
+// other class with S2 <= B + tie_tol (usually none: they are a prefix of the S2 order).  A class left out
 // has S_vN >= S2 > best + tie_tol, so the decision equals the one from evaluating every class.
 // Cluster-wide choice of the class for one theta (shape chi_l x d x d x chi_r in global memory,
 // readable by every CTA).  Returns the chosen class on the leader (-1 on the other CTAs); the
@@ -1301,18 +1349,32 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
   const bool prune = m > kPruneMin;
+  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
   score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, !prune);
   cluster_sync();
   if (prune) {
-    if (leader && threadIdx.x == 0) {
-      int kmin = 0;
-      for (int k = 0; k < C.K; ++k) {
+    if (leader) {
+      // round 1: the identity and the classes of smallest S2, one per FP64 pipe of the cluster
+      // (warp-level scoring) or one per CTA (CTA-level scoring)
+      const int L = (small ? 4 * C.csize : C.csize) - 1;
+      for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
         s.evald[k] = 0;
-        if (s.s2[k] < s.s2[kmin]) kmin = k;
+        const long long bk = order_key(s.s2[k]);
+        int r = 0;
+        for (int q = 0; q < C.K; ++q) {
+          const long long bq = order_key(s.s2[q]);
+          r += (bq < bk) || (bq == bk && q < k);
+        }
+        s.ord[k] = r;
       }
-      s.list[0] = 0;
-      s.nlist = 1;
-      if (kmin != 0) s.list[s.nlist++] = kmin;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int cnt = 1;
+        s.list[0] = 0;
+        for (int k = 1; k < C.K; ++k)
+          if (s.ord[k] < L) s.list[cnt++] = k;
+        s.nlist = cnt;
+      }
     }
     cluster_sync();
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);

@@ -63,7 +63,9 @@ CASES = [(3, 3, 3), (3, 9, 27), (3, 27, 27), (2, 4, 8), (2, 40, 40)]
 def test_noalloc_matches_handle_scoring_twice(G, d, cl, cr):
     import torch
     rng = np.random.default_rng(1000 * d + 10 * cl + cr)
-    sim = G.Simulator(12, d, chi_max=81)   # its scoring accepts chi up to 64 (d = 2) / 81 (d = 3)
+    # Same cluster size as the static variant (4 CTAs), so that the pruning evaluates the same classes;
+    # this handle's scoring accepts chi up to 64 (d = 2) / 81 (d = 3).
+    sim = G.Simulator(12, d, chi_max=81, cluster_size=4)
     stream = torch.cuda.Stream(device=0)
     try:
         # Two different tensors in a row: the second call runs on the array the first one left.
