@@ -181,8 +181,10 @@ int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, 
 /* Weyl string P = C^dag Z_k C of the last non-Clifford gate: x[n], z[n], r. */
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
 int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
-/* Scores of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class),
- * vn[k] (von Neumann entropy, valid where evaluated[k] = 1; the Renyi-2 bound excluded the others);
+/* Scores of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
+ * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact
+ * one with eta < 3 (d^3 + 6 d + max side) 2^-24), vn[k] (von Neumann entropy, valid where
+ * evaluated[k] = 1; the Renyi-2 bound excluded the others);
  * K = gcamps_num_candidates(d) entries each; any pointer may be NULL. */
 int gcamps_get_last_scores(gcamps_t* h, int circuit, double* s2, double* vn, uint8_t* evaluated);
 /* Two-site tensor scored at the last bond visit: shape[0..1] = (chi_l, chi_r); theta receives the
@@ -211,7 +213,7 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
  * counterpart of this call; it is a deployment variant of the disentangler scoring.
  *
  * It needs no handle and allocates nothing (no cudaMalloc, no cudaFree, no allocating library
- * routine).  Its working memory is one static device array of this library, 1,643,520 bytes, that
+ * routine).  Its working memory is one static device array of this library, 1,696,256 bytes, that
  * every GPU which loads the library holds until the process exits.  That array fixes the largest
  * tensor: chi_l d <= GCAMPS_NOALLOC_MAX_SIDE and d chi_r <= GCAMPS_NOALLOC_MAX_SIDE, i.e. chi <= 27
  * for qutrits and chi <= 40 for qubits; a larger shape returns GCAMPS_ESIZE and launches nothing.

@@ -69,6 +69,17 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
   return acc;
 }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+// FP32 complex: acc + a b and acc + a conj(b)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+  return acc;
+}
+__device__ __forceinline__ float2 ffmac2(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
+  return acc;
+}
 // x / |x|, and 1 for x = 0.  A subnormal x is first scaled by 2^600 (exact): its modulus carries only
 // a few significant bits, so the plain quotient has a modulus visibly different from 1 and a
 // Householder reflector built with it is no longer unitary.
@@ -107,6 +118,7 @@ struct Smem {
   int nlist;
   int rank0;                  // numerical rank of the identity class's Gram (cluster leader; -1 = none)
   int ord[kMaxK];             // rank of each class in ascending S2 (cluster leader)
+  double s2lo[kMaxK];         // lower bound of S2 from the FP32 screen (cluster leader)
   double wtri[kWarps][64];    // per warp: tridiagonal diagonal [0, 32) | off-diagonal squared [32, 64)
   float wtri32[kWarps][64];   // the same in FP32
   double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
@@ -125,6 +137,7 @@ struct Ctx {
   int c, n, d, K;
   int rank, csize;            // position in the circuit's cluster; rank 0 leads
   double2* cta;               // this CTA's scoring scratch
+  float2* th32;               // FP32 copy of the two-site tensor being scored
   uint8_t *fx, *fr, *ix, *ir;
   double2* mps;
   int* dims;
@@ -147,6 +160,7 @@ __device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   C.rank = rank;
   C.csize = e.csize;
   C.cta = e.cscr + ((long long)c * e.csize + rank) * e.cl.total;
+  C.th32 = reinterpret_cast<float2*>(e.scr + (long long)c * e.sl.total + e.sl.tmp);
   C.n = e.n;
   C.d = e.d;
   C.K = e.K;
@@ -1279,10 +1293,70 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   return sc;
 }
 
+// Renyi-2 entropy of class Q on theta in FP32, and a lower bound on the exact value.  theta' = Q theta
+// (FP32 inputs, d^2-term sums) is off by at most e1 |theta|_F with e1 = d (d^2 + 6) u (u = 2^-24),
+// and the Gram on the smaller side (sums of 2M + 4 rounded terms, M the longer side) by at most
+// (2M + 4) u |theta'|_F^2, so |G^ - G|_F <= eta tr G with eta = 2 e1 + e1^2 + (2M + 4) u (1 + e1)^2;
+// the same bound holds for the trace.  Then |ln |G^|_F - ln |G|_F| <= eta tr / |G|_F <= eta sqrt(m) and
+// |ln tr^ - ln tr| <= eta, so |S2^ - S2| <= 2 eta sqrt(m) + 2 eta.  The lower bound subtracts twice that
+// plus the rounding of the partial sums.  Outside 1e-30 < tr < 1e30 the lower bound is 0 (S2 >= 0).
+template <class Grp>
+__device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, int cr, const float2* Q, float2* X,
+                        double* s2_out, double* lo_out) {
+  const int d = C.d, dd = d * d;
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols, M = rows < cols ? cols : rows;
+  for (int idx = g.tid; idx < rows * cols; idx += g.n) {
+    const int rr = idx / cols, col = idx % cols;
+    const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
+    const float2* q = Q + (sd * d + t) * dd;
+    const float2* tp = th + (long long)a * dd * cr + b;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int v = 0; v < dd; ++v) acc = ffma2(q[v], tp[(long long)v * cr], acc);
+    X[idx] = acc;
+  }
+  g.sync();
+  float tr = 0.f, fro = 0.f;
+  const int ntri = m * (m + 1) / 2;
+  for (int idx = g.tid; idx < ntri; idx += g.n) {
+    int i, j;
+    tri_index(idx, i, j);
+    float2 acc = make_float2(0.f, 0.f);
+    if (rows <= cols) {
+      const float2* ri = X + (long long)i * cols;
+      const float2* rj = X + (long long)j * cols;
+      for (int c = 0; c < cols; ++c) acc = ffmac2(ri[c], rj[c], acc);
+    } else {
+      for (int r = 0; r < rows; ++r) acc = ffmac2(X[(long long)r * cols + i], X[(long long)r * cols + j], acc);
+    }
+    if (i == j) {
+      tr += acc.x;
+      fro = fmaf(acc.x, acc.x, fro);
+    } else {
+      fro = fmaf(2.f * acc.x, acc.x, fmaf(2.f * acc.y, acc.y, fro));
+    }
+  }
+  const double trd = g.sum((double)tr), frod = g.sum((double)fro);
+  double s2 = 0.0, lo = 0.0;
+  if (trd > 1e-30 && trd < 1e30 && frod > 0.0) {
+    const double u = 5.960464477539063e-08;
+    const double e1 = d * (dd + 6) * u;
+    const double eta = 2.0 * e1 + e1 * e1 + (2.0 * M + 4.0) * u * (1.0 + e1) * (1.0 + e1);
+    const double delta = 4.0 * eta * sqrt((double)m) + 4.0 * eta + ((double)m * m / 16.0 + 16.0) * u;
+    s2 = -log(frod / (trd * trd));
+    lo = s2 - delta;
+  }
+  *s2_out = s2;
+  *lo_out = lo;
+}
+
 // Scores classes list[0..cnt) (all K classes if list is null) on the whole cluster: small problems
 // one class per warp, large ones one class per CTA.  Results go to the leader CTA's shared memory.
+// mode kExact: S2 and S_vN in FP64; kScreen: S2 in FP32 with its lower bound (lead->s2lo).
+enum ScoreMode { kExact = 0, kScreen = 1 };
 __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
-                              const int* list, int cnt, bool want_vn) {
+                              const int* list, int cnt, int mode) {
+  const bool want_vn = mode == kExact;
   const Engine& e = *C.e;
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
@@ -1297,6 +1371,15 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
     const int gw = warp * C.csize + C.rank, nw = C.csize * kWarps;
     for (int t = gw; t < cnt; t += nw) {
       const int k = list ? list[t] : t;
+      if (mode == kScreen) {
+        double v, lo;
+        s2_fp32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws), &v, &lo);
+        if (lane == 0) {
+          lead->s2[k] = v;
+          lead->s2lo[k] = lo;
+        }
+        continue;
+      }
       const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn,
                                    s.wtri[warp], s.wtri32[warp], 32);
       if (lane == 0) {
@@ -1314,6 +1397,16 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
     double2* ws = C.cta + e.cl.block;
     for (int t = C.rank; t < cnt; t += C.csize) {
       const int k = list ? list[t] : t;
+      if (mode == kScreen) {
+        double v, lo;
+        s2_fp32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws), &v, &lo);
+        if (threadIdx.x == 0) {
+          lead->s2[k] = v;
+          lead->s2lo[k] = lo;
+        }
+        __syncthreads();
+        continue;
+      }
       const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn,
                                    s.btri, s.btri32, kBTri);
       if (threadIdx.x == 0) {
@@ -1334,7 +1427,8 @@ __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 
 // ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
 // One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
-// decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class;
+// decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class
+// from an FP32 screen with a rigorous lower bound s2lo (s2_fp32), and the rounds below use s2lo;
 // round 1 evaluates S_vN of the identity and of the classes with the smallest S2 (as many as the
 // cluster evaluates at once), giving an upper bound B on the best entropy; round 2 evaluates every
 // other class with S2 <= B + tie_tol (usually none: they are a prefix of the S2 order).  A class left out
@@ -1350,7 +1444,13 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
   const int m = rows < cols ? rows : cols;
   const bool prune = m > kPruneMin;
   const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
-  score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, !prune);
+  if (prune) {   // FP32 copy of theta for the screen, shared by the cluster
+    if (leader)
+      for (int i = threadIdx.x; i < rows * cols; i += blockDim.x)
+        C.th32[i] = make_float2((float)theta[i].x, (float)theta[i].y);
+    cluster_sync();
+  }
+  score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, prune ? kScreen : kExact);
   cluster_sync();
   if (prune) {
     if (leader) {
@@ -1359,10 +1459,10 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
       const int L = (small ? 4 * C.csize : C.csize) - 1;
       for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
         s.evald[k] = 0;
-        const long long bk = order_key(s.s2[k]);
+        const long long bk = order_key(s.s2lo[k]);
         int r = 0;
         for (int q = 0; q < C.K; ++q) {
-          const long long bq = order_key(s.s2[q]);
+          const long long bq = order_key(s.s2lo[q]);
           r += (bq < bk) || (bq == bk && q < k);
         }
         s.ord[k] = r;
@@ -1377,7 +1477,7 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
       }
     }
     cluster_sync();
-    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);
+    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
     cluster_sync();
     if (leader && threadIdx.x == 0) {
       double bound = 1e300;
@@ -1385,11 +1485,11 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
         if (s.evald[k]) bound = fmin(bound, s.vn[k]);
       int cnt = 0;
       for (int k = 0; k < C.K; ++k)
-        if (!s.evald[k] && s.s2[k] <= bound + e.tie_tol + 1e-12) s.list[cnt++] = k;
+        if (!s.evald[k] && s.s2lo[k] <= bound + e.tie_tol + 1e-12) s.list[cnt++] = k;
       s.nlist = cnt;
     }
     cluster_sync();
-    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, true);
+    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
     cluster_sync();
   }
   if (!leader) return -1;
@@ -1628,7 +1728,7 @@ __global__ void __launch_bounds__(kThreads) k_score_theta(Engine e, const double
   Ctx C = make_ctx(e, c, rank);
   Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
-  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, true);
+  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
   cluster_sync();
   if (c == 0 && rank == 0)
     for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
@@ -1999,20 +2099,23 @@ cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, l
 // gcamps_score_theta_noalloc runs the scoring and the class choice of k_score_theta with all of its
 // scratch in the static array below instead of a handle's allocation.  Per CTA: kWarps warp-level
 // buffers of kSmallStride entries and one CTA-level buffer (theta' of up to kStaticSide^2 entries,
-// its Gram, eigenvalue arrays); then the last-visit score record and the status words.
+// its Gram, eigenvalue arrays); then the last-visit score record, the status words and the FP32 copy
+// of theta used by the screen.
 constexpr long long kStaticTcap = (long long)kStaticSide * kStaticSide;
 constexpr long long kStaticCtaRaw = (long long)kWarps * kSmallStride + 2 * kStaticTcap + kStaticSide + 64;
 constexpr long long kStaticCta = (kStaticCtaRaw + 15) / 16 * 16;                  // 256-byte multiples
 constexpr long long kStaticScores = ((3LL * kMaxK + 2 + 2LL * kSmall + 1) / 2 + 15) / 16 * 16;
 constexpr long long kStaticMeta = 16;                                             // >= M_COUNT ints
-constexpr long long kStaticWords = kStaticCluster * kStaticCta + kStaticScores + kStaticMeta;
+constexpr long long kStaticTh32 = ((kStaticTcap + 1) / 2 + 15) / 16 * 16;          // float2 pairs
+constexpr long long kStaticWords = kStaticCluster * kStaticCta + kStaticScores + kStaticMeta + kStaticTh32;
 static_assert(2 * kStaticMeta >= M_COUNT, "status words");
-static_assert(kStaticWords * 16 == 1643520, "scratch size stated in gcamps.h");
-// 1,643,520 bytes, held by every device that loads the library.  Calls reuse it and it keeps the
+static_assert(kStaticWords * 16 == 1696256, "scratch size stated in gcamps.h");
+// 1,696,256 bytes, held by every device that loads the library.  Calls reuse it and it keeps the
 // last call's contents; only the status words must start at zero, and each call clears them itself.
 static __device__ __align__(256) double2 g_static_scratch[kStaticWords];
 // Class unitaries for d = 2 then d = 3 ([K][d^4]) and their images ([K][20]), set once per device.
 static __device__ __align__(256) double2 g_static_candU[kStaticK2 * 16 + kStaticK3 * 81];
+static __device__ __align__(256) float2 g_static_candU32[kStaticK2 * 16 + kStaticK3 * 81];
 static __device__ __align__(256) int32_t g_static_candImg[(kStaticK2 + kStaticK3) * 20];
 
 // Device addresses of the arrays above, per device (host code only sees host-side stand-ins under
@@ -2020,6 +2123,7 @@ static __device__ __align__(256) int32_t g_static_candImg[(kStaticK2 + kStaticK3
 struct StaticPtrs {
   double2* scratch;
   double2* candU;
+  float2* candU32;
   int32_t* candImg;
 };
 static StaticPtrs g_static_ptrs[kStaticMaxDevices];
@@ -2039,11 +2143,12 @@ __global__ void __launch_bounds__(kThreads) k_score_theta_static(Engine e, const
   C.K = e.K;
   C.cta = e.cscr + (long long)rank * e.cl.total;
   C.meta = e.meta;
+  C.th32 = reinterpret_cast<float2*>(e.cscr + kStaticCluster * kStaticCta + kStaticScores + kStaticMeta);
   Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
   if (rank == 0 && threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;   // status of this call only
   cluster_sync();
-  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, true);
+  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
   cluster_sync();
   if (rank == 0)
     for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
@@ -2067,6 +2172,13 @@ cudaError_t static_setup(int device, const double* u2, const int32_t* img2, cons
   StaticPtrs p = {};
   cudaError_t ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.scratch), g_static_scratch);
   if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candU), g_static_candU);
+  if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candU32), g_static_candU32);
+  if (ce == cudaSuccess) {
+    float u32[2 * (kStaticK2 * 16 + kStaticK3 * 81)];
+    for (int i = 0; i < 2 * kStaticK2 * 16; ++i) u32[i] = (float)u2[i];
+    for (int i = 0; i < 2 * kStaticK3 * 81; ++i) u32[2 * kStaticK2 * 16 + i] = (float)u3[i];
+    ce = cudaMemcpyToSymbol(g_static_candU32, u32, sizeof u32, 0);
+  }
   if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candImg), g_static_candImg);
   if (ce == cudaSuccess) ce = cudaMemcpyToSymbol(g_static_candU, u2, sizeof(double2) * kStaticK2 * 16, 0);
   if (ce == cudaSuccess)
@@ -2082,7 +2194,7 @@ cudaError_t launch_score_theta_static(int device, int d, double tie_tol, const d
                                       double* s2, double* vn, int32_t* choice, cudaStream_t st) {
   if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
   const StaticPtrs& p = g_static_ptrs[device];
-  if (!p.scratch || !p.candU || !p.candImg) return cudaErrorInitializationError;
+  if (!p.scratch || !p.candU || !p.candU32 || !p.candImg) return cudaErrorInitializationError;
   Engine e = {};
   e.d = d;
   e.K = d == 2 ? kStaticK2 : kStaticK3;
@@ -2098,6 +2210,7 @@ cudaError_t launch_score_theta_static(int device, int d, double tie_tol, const d
   e.lastsc = reinterpret_cast<double*>(p.scratch + kStaticCluster * kStaticCta);
   e.meta = reinterpret_cast<int*>(p.scratch + kStaticCluster * kStaticCta + kStaticScores);
   e.candU = p.candU + (d == 2 ? 0 : kStaticK2 * 16);
+  e.candU32 = p.candU32 + (d == 2 ? 0 : kStaticK2 * 16);
   e.candImg = p.candImg + (d == 2 ? 0 : kStaticK2 * 20);
   return launch_cluster(k_score_theta_static, e, st, e, th, cl, cr, s2, vn, choice);
 }

@@ -560,6 +560,8 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   const size_t o_candU = bytes;
   const int D = d * d;
   bytes = align(bytes + (size_t)e.K * D * D * sizeof(double2));
+  const size_t o_candU32 = bytes;
+  bytes = align(bytes + (size_t)e.K * D * D * sizeof(float2));
   const size_t o_candI = bytes;
   bytes = align(bytes + (size_t)e.K * 20 * sizeof(int32_t));
   const size_t o_aux = bytes;
@@ -596,6 +598,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.sing = (double*)(base + o_sing);
   e.iscr = (int*)(base + o_iscr);
   e.candU = (const double2*)(base + o_candU);
+  e.candU32 = (const float2*)(base + o_candU32);
   e.candImg = (const int32_t*)(base + o_candI);
   h->xz_dev = (int8_t*)(base + o_aux);
   h->out_dev = (double2*)(base + o_aux + align(gcx::kMaxN * 2));
@@ -607,6 +610,10 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
                          h->stream);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((void*)e.candU, tb.u.data(), tb.u.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         h->stream);
+  const std::vector<float> u32(tb.u.begin(), tb.u.end());   // lives until the synchronisation below
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.candU32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice,
                          h->stream);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((void*)e.candImg, tb.img.data(), tb.img.size() * sizeof(int32_t),

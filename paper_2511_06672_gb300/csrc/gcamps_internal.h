@@ -68,6 +68,7 @@ struct Engine {
   double* sing;     long long sing_stride;  // singular values / eigenvalues
   int* iscr;        long long iscr_stride;  // permutation scratch
   const double2* candU;                     // [K][d^4] class unitaries, row-major
+  const float2* candU32;                    // [K][d^4] the same in FP32 (screening)
   const int32_t* candImg;                   // [K][20] class images
 };
 
