@@ -35,6 +35,24 @@ SEEDS_PER_D = 8
 WORKLOAD = "gcamps-brickwork-n32-L24-T32-chi256-d2+d3-8seeds"
 METRIC = "T-gates/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the engine is FP64-ALU bound
+# GB300 FP32 (non-tensor) nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+ENGINE_SRC = os.path.join(ROOT, "paper_2511_06672_gb300", "csrc", "gcamps_engine.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_run_dram_bench_workload.txt")
+
+
+def engine_traffic():
+    """DRAM bytes per k_run launch from the committed ncu summary, if it was taken on this engine
+    source (sha256 recorded beside it); else None."""
+    import hashlib
+    try:
+        want = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()
+        kv = dict(line.strip().split("=", 1) for line in open(TRAFFIC_FILE) if "=" in line and not line.startswith("#"))
+        if kv.get("engine_sha256") == want:
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
 
 
 def progress(msg):
@@ -279,12 +297,17 @@ def main():
     cand_rate = cand_per_step * args.steps * world / total_time
     vn_frac = sum(st["vn_evaluations"] for d in (2, 3) for st in stats[d]) / max(1, cand_per_step)
     flops_per_launch = sum(st["scoring_flops"] for d in (2, 3) for st in stats[d]) / 2.0
+    screen_per_launch = sum(st["screen_flops"] for d in (2, 3) for st in stats[d]) / 2.0
     launch_s = sum(engine_times) / len(engine_times)
     achieved = flops_per_launch / launch_s / 1e12
+    screen_achieved = screen_per_launch / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": engine_traffic(),
                 "kernel": "k_run (engine, one launch per d)", "flops_per_launch": flops_per_launch,
-                "launch_ms": 1e3 * launch_s, "peak_source": "FP64 nominal, profiling recipe table"}
+                "launch_ms": 1e3 * launch_s, "peak_source": "FP64 nominal, profiling recipe table",
+                "fp32_screen": {"flops_per_launch": screen_per_launch, "achieved": screen_achieved,
+                                "peak": FP32_PEAK_TFLOPS, "frac": screen_achieved / FP32_PEAK_TFLOPS,
+                                "peak_source": "FP32 nominal from unit counts and the 2.07 GHz maximum clock"}}
 
     progress(f"timed steps: {[round(t, 3) for t in times]}")
     # end to end: host gate lists, copies and readback inside the timed region

@@ -77,12 +77,14 @@ typedef struct {
   int32_t max_chi;            /* largest bond dimension seen after any truncation           */
   int32_t status;             /* sticky device status: 0 or a GCAMPS_E* code                */
   double discarded_weight;    /* sum of discarded s_i^2 over all truncations                */
-  double scoring_flops;       /* algorithmic FP64 flops of candidate scoring (see below)    */
+  double scoring_flops;       /* algorithmic FP64 flops of exact class scoring (see below)  */
+  double screen_flops;        /* algorithmic FP32 flops of the Renyi-2 screen (see below)   */
 } gcamps_stats;
-/* scoring_flops counts, per scored class at a bond with R = chi_l d rows and C = d chi_r
- * columns (m = min(R, C), M = max(R, C)): 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram),
- * plus (16/3) m^3 (Householder tridiagonalisation) per exact von Neumann evaluation; the
- * eigenvalue iteration is not counted. */
+/* Per class at a bond with R = chi_l d rows and C = d chi_r columns (m = min(R, C),
+ * M = max(R, C)): scoring_flops adds 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram) +
+ * (16/3) m^3 (Householder tridiagonalisation) per exact von Neumann evaluation (FP64; the
+ * eigenvalue bisection is not counted); screen_flops adds 8 d^2 R C + 4 m (m + 1) M per class of
+ * the FP32 Renyi-2 screen (every class of every bond with m > 1). */
 
 /* One operation of a gate list (gcamps_run).  kind: */
 #define GCAMPS_OP_CLIFFORD 1     /* q0, q1 (-1 for one qudit), img as for apply_clifford   */

@@ -174,7 +174,7 @@ __device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   C.dims = e.dims + (long long)c * (n + 1);
   C.meta = e.meta + (long long)c * M_COUNT;
   C.stats = e.stats + (long long)c * S_COUNT;
-  C.dstats = e.dstats + (long long)c * 2;
+  C.dstats = e.dstats + (long long)c * 4;
   C.dec = e.dec + (long long)c * kDecCap * 2;
   C.weyl = e.weyl + (long long)c * 2 * n;
   C.scr = e.scr + (long long)c * e.sl.total;
@@ -1558,7 +1558,9 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     C.stats[S_VN] += nev;
     {
       const double R = rows, Cc = cols, mm = m, M = rows < cols ? cols : rows;
-      C.dstats[1] += C.K * (8.0 * dd * R * Cc + 4.0 * mm * (mm + 1.0) * M) + nev * (16.0 / 3.0) * mm * mm * mm;
+      const double per_class = 8.0 * dd * R * Cc + 4.0 * mm * (mm + 1.0) * M;
+      C.dstats[1] += nev * (per_class + (16.0 / 3.0) * mm * mm * mm);   // exact evaluations, FP64
+      if (m > kPruneMin) C.dstats[2] += C.K * per_class;                // FP32 screen of every class
     }
     const int nd = C.meta[M_NDEC];
     if (nd < kDecCap) {
@@ -1768,7 +1770,7 @@ __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
   for (int j = threadIdx.x; j <= n; j += blockDim.x) C.dims[j] = 1;
   if (threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;
   if (threadIdx.x < S_COUNT) C.stats[threadIdx.x] = (threadIdx.x == S_MAXCHI) ? 1 : 0;
-  if (threadIdx.x < 2) C.dstats[threadIdx.x] = 0.0;
+  if (threadIdx.x < 4) C.dstats[threadIdx.x] = 0.0;
 }
 
 // ------------------------------------------------------------------------------ readouts

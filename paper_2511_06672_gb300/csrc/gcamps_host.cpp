@@ -542,7 +542,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   const size_t o_stats = bytes;
   bytes = align(bytes + (size_t)batch * gcx::S_COUNT * sizeof(long long));
   const size_t o_dstats = bytes;
-  bytes = align(bytes + (size_t)batch * 2 * sizeof(double));
+  bytes = align(bytes + (size_t)batch * 4 * sizeof(double));
   const size_t o_dec = bytes;
   bytes = align(bytes + (size_t)batch * gcx::kDecCap * 2 * sizeof(int));
   const size_t o_weyl = bytes;
@@ -951,10 +951,10 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   if (rc) return rc;
   if (!st) return fail(h, GCAMPS_EINVAL, "null output");
   long long s[gcx::S_COUNT];
-  double ds[2];
+  double ds[4];
   int meta[gcx::M_COUNT];
   GC_CUDA(h, cudaMemcpyAsync(s, h->e.stats + (long long)circuit * gcx::S_COUNT, sizeof s, cudaMemcpyDeviceToHost, h->stream));
-  GC_CUDA(h, cudaMemcpyAsync(ds, h->e.dstats + (long long)circuit * 2, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(ds, h->e.dstats + (long long)circuit * 4, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
   GC_CUDA(h, cudaMemcpyAsync(meta, h->e.meta + (long long)circuit * gcx::M_COUNT, sizeof meta, cudaMemcpyDeviceToHost,
                              h->stream));
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -973,6 +973,7 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   st->status = meta[gcx::M_STATUS];
   st->discarded_weight = ds[0];
   st->scoring_flops = ds[1];
+  st->screen_flops = ds[2];
   return device_status(h);
 }
 

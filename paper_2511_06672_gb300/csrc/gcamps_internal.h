@@ -59,7 +59,7 @@ struct Engine {
   int* dims;                                // [batch][n+1]
   int* meta;                                // [batch][M_COUNT]
   long long* stats;                         // [batch][S_COUNT]
-  double* dstats;                           // [batch][2]: discarded weight, spare
+  double* dstats;                           // [batch][4]: discarded weight, FP64 scoring flops, FP32 screen flops, spare
   int* dec;                                 // [batch][kDecCap][2]
   int8_t* weyl;                             // [batch][2n]
   double* lastsc;                           // [batch][3 * kMaxK + 2 + 2 * kSmall]: s2 | vn | evaluated | chi_l, chi_r | theta of the last visit
