@@ -3,8 +3,11 @@
 Workload (one step = one pass of the whole hot path over one batch):
   qubit and qutrit circuits (d = 2 and d = 3), n = 32 qudits, 24 brickwork layers of random
   two-qudit Cliffords, 32 T gates (each followed by disentangling), chi_max = 256, SVD cutoff
-  1e-12, complex128; seeds 1..8 for each d (16 circuits per step, one CTA each).  Every step starts
-  from |0...0> with C = I (reset kernel) and runs the full gate list in one engine launch per d.
+  1e-12, complex128; seeds 1..8 for each d (16 circuits per step; one thread-block cluster per
+  circuit, 16 CTAs for qutrits and 4 for qubits: the qutrit circuits are the slow ones, and their
+  exact class evaluations spread over the cluster's CTAs).  Every step starts from |0...0> with
+  C = I (reset kernel) and runs the full gate list in one engine launch per d, the qutrit launch
+  first.
 
 value  : T gates of all circuits / device time of the timed steps (CUDA events on the engine's
          stream; L2 flushed with a 512 MiB write before every step, outside the event pair).
@@ -192,6 +195,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
+    ap.add_argument("--cluster-qubit", type=int, default=4, help="CTAs per qubit circuit (0: --cluster)")
+    ap.add_argument("--cluster-qutrit", type=int, default=16, help="CTAs per qutrit circuit (0: --cluster)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,9 +215,10 @@ def main():
     stream = torch.cuda.Stream()
     streams = {2: torch.cuda.Stream(), 3: torch.cuda.Stream()}   # the two handles run concurrently
     sims, ops_host, ops_dev, begin_dev = {}, {}, {}, {}
+    cluster = {2: args.cluster_qubit or args.cluster, 3: args.cluster_qutrit or args.cluster}
     for d in (2, 3):
         sims[d] = G.Simulator(N, d, chi_max=CHI, cutoff=CUTOFF, batch=SEEDS_PER_D, stream=streams[d],
-                              cluster_size=args.cluster)
+                              cluster_size=cluster[d])
         o, b = workload_ops(G, d, rank)
         # e2e inputs live in pinned host memory
         o_pin = torch.from_numpy(o.view(np.uint8).copy()).pin_memory().numpy().view(G.OP_DTYPE)
@@ -233,7 +239,7 @@ def main():
         around each engine launch on its stream."""
         fork = torch.cuda.Event()
         fork.record(stream)
-        for i, d in enumerate((2, 3)):
+        for i, d in enumerate((3, 2)):   # the slower qutrit launch first
             s = sims[d]
             streams[d].wait_event(fork)
             rc = lib.gcamps_reset(s._h)
@@ -335,7 +341,7 @@ def main():
         "config": {"workload": WORKLOAD, "n": N, "layers": LAYERS, "t_gates": T, "chi_max": CHI,
                    "cutoff": CUTOFF, "d": [2, 3], "circuits_per_rank": 2 * SEEDS_PER_D,
                    "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}",
-                   "cluster_ctas_per_circuit": args.cluster},
+                   "cluster_ctas_per_circuit": {"d2": cluster[2], "d3": cluster[3]}},
         "candidates_per_s": cand_rate,
         "vn_evaluated_fraction": vn_frac,
         "e2e": {"value": e2e_value, "unit": "T-gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
