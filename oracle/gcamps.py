@@ -14,7 +14,10 @@
 
 Readings where the paper is silent (shared with the CUDA library, which implements them in its
 own code):
-* score: von Neumann entropy (natural log) of the normalised Schmidt spectrum of Q theta;
+* score: von Neumann entropy (natural log) of the normalised Schmidt spectrum of Q theta
+  (score_kind 0); the Renyi-2 entropy -ln sum p^2 (score_kind 1); or the bond-dimension
+  criterion of Sec. 4 read as the number of Schmidt weights p above max(1e-12, 4 cutoff^2), ties
+  broken by the von Neumann entropy (score_kind 2);
 * accept: best score < score of the identity - tie_tol; ties within tie_tol of the minimum go to
   the lowest class index;
 * sweeps alternate direction (left to right first, centre starting at f), a split is done at
@@ -42,6 +45,25 @@ def entropy_from_singular_values(s: np.ndarray) -> float:
     return float(-np.sum(p * np.log(p)))
 
 
+def renyi2_from_singular_values(s: np.ndarray) -> float:
+    """-ln sum p^2 with p = s^2 / sum s^2 (Renyi entropy of order 2)."""
+    p = s.astype(float) ** 2
+    tot = p.sum()
+    if tot <= 0:
+        return 0.0
+    p = p / tot
+    return float(-np.log(np.sum(p * p)))
+
+
+def weight_rank(s: np.ndarray, cutoff: float) -> int:
+    """Number of Schmidt weights p = s^2 / sum s^2 above max(1e-12, 4 cutoff^2)."""
+    p = s.astype(float) ** 2
+    tot = p.sum()
+    if tot <= 0:
+        return 0
+    return int(np.sum(p / tot > max(1e-12, 4.0 * cutoff * cutoff)))
+
+
 def expansion_coefficients(phases, d: int) -> np.ndarray:
     """c_m with diag(e^{i phases}) = sum_m c_m Z^m: c_m = (1/d) sum_j e^{i phase_j} omega^{-m j}."""
     t = np.exp(1j * np.asarray(phases, dtype=float))
@@ -51,12 +73,15 @@ def expansion_coefficients(phases, d: int) -> np.ndarray:
 
 class GCAMPS:
     def __init__(self, n: int, d: int, chi_max: int, cutoff: float = 1e-14,
-                 max_sweeps: int = 8, tie_tol: float = 1e-10):
+                 max_sweeps: int = 8, tie_tol: float = 1e-10, score_kind: int = 0):
         if d not in (2, 3):
             raise ValueError("d must be 2 or 3")
         self.n, self.d = n, d
         self.chi_max, self.cutoff = chi_max, cutoff
         self.max_sweeps, self.tie_tol = max_sweeps, tie_tol
+        if score_kind not in (0, 1, 2):
+            raise ValueError("score_kind must be 0, 1 or 2")
+        self.score_kind = score_kind
         self.tab = Tableau(n, d)
         self.mps = MPS.zero_state(n, d)
         self.span = None
@@ -125,18 +150,46 @@ class GCAMPS:
         return disc
 
     # ---------------------------------------------------------------- disentangling
-    def score_bond(self, theta: np.ndarray) -> np.ndarray:
-        """Entropy of Q theta for every class Q (Schmidt values by SVD)."""
+    def schmidt_values(self, theta: np.ndarray):
+        """Schmidt values of Q theta across (a, s) | (t, b) for every class Q (SVD)."""
         cl, d, _, cr = theta.shape
         t = theta.reshape(cl, d * d, cr)
-        out = np.zeros(len(self.cands))
-        for k, (_s, _imgs, u) in enumerate(self.cands):
+        out = []
+        for _s, _imgs, u in self.cands:
             tq = np.einsum("uv,avb->aub", u, t).reshape(cl * d, d * cr)
-            out[k] = entropy_from_singular_values(np.linalg.svd(tq, compute_uv=False))
-        self.candidates_scored += len(self.cands)
+            out.append(np.linalg.svd(tq, compute_uv=False))
         return out
 
-    def choose(self, scores: np.ndarray) -> int:
+    def score_bond(self, theta: np.ndarray) -> np.ndarray:
+        """Von Neumann entropy of Q theta for every class Q (Schmidt values by SVD)."""
+        self.candidates_scored += len(self.cands)
+        return np.array([entropy_from_singular_values(sv_) for sv_ in self.schmidt_values(theta)])
+
+    def score_keys(self, theta: np.ndarray):
+        """Scores of every class under score_kind: an array of entropies (kinds 0 and 1), or
+        (rank, entropy) pairs (kind 2)."""
+        svs = self.schmidt_values(theta)
+        self.candidates_scored += len(self.cands)
+        if self.score_kind == 1:
+            return np.array([renyi2_from_singular_values(x) for x in svs])
+        vn = np.array([entropy_from_singular_values(x) for x in svs])
+        if self.score_kind == 0:
+            return vn
+        return np.array([weight_rank(x, self.cutoff) for x in svs]), vn
+
+    def choose(self, scores) -> int:
+        """Class to apply: the lowest index within tie_tol of the best score, if it beats the
+        identity (class 0) by more than tie_tol.  Kind 2 compares ranks first; the entropies
+        decide among the classes of the smallest rank and between equal ranks."""
+        if isinstance(scores, tuple):
+            rank, vn = scores
+            rmin = int(np.min(rank))
+            sel = rank == rmin
+            best = float(np.min(vn[sel]))
+            k = int(np.nonzero(sel & (vn <= best + self.tie_tol))[0][0])
+            if rank[k] < rank[0] or vn[k] < vn[0] - self.tie_tol:
+                return k
+            return 0
         best = float(np.min(scores))
         k = int(np.nonzero(scores <= best + self.tie_tol)[0][0])
         if scores[k] < scores[0] - self.tie_tol:
@@ -146,7 +199,7 @@ class GCAMPS:
     def visit(self, i: int, left_to_right: bool, forced=None) -> int:
         theta = self.mps.theta(i)
         if forced is None:
-            k = self.choose(self.score_bond(theta))
+            k = self.choose(self.score_keys(theta))
         else:
             k = forced
         if k:
