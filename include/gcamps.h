@@ -52,7 +52,11 @@ typedef struct gcamps gcamps_t;
 typedef struct {
   double cutoff;       /* keep singular values s_i > cutoff * s_0 (Sec. 2.4; default 1e-12)   */
   int max_sweeps;      /* disentangling sweeps per call (default 8)                           */
-  int score_kind;      /* 0 = von Neumann entropy of the Schmidt spectrum (only kind now)      */
+  int score_kind;      /* disentangler score (Sec. 3; Sec. 4 "bond-dimension criterion"):      */
+                       /* 0 = von Neumann entropy of the normalised Schmidt spectrum;         */
+                       /* 1 = Renyi-2 entropy -ln sum p^2;                                     */
+                       /* 2 = number of Schmidt weights p > max(1e-12, 4 cutoff^2), ties       */
+                       /*     broken by the von Neumann entropy                               */
   int precision;       /* 0 = FP64 everywhere (only mode now)                                  */
   double tie_tol;      /* accept Q only if S(Q) < S(I) - tie_tol; ties -> lowest index (1e-10) */
   double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
@@ -186,7 +190,8 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
 /* Scores of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
  * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact
  * one with eta < 3 (d^3 + 6 d + max side) 2^-24), vn[k] (von Neumann entropy, valid where
- * evaluated[k] = 1; the Renyi-2 bound excluded the others);
+ * evaluated[k] = 1 except for classes scored by Renyi-2 alone under score_kind 1, which read NaN;
+ * the bounds excluded the others);
  * K = gcamps_num_candidates(d) entries each; any pointer may be NULL. */
 int gcamps_get_last_scores(gcamps_t* h, int circuit, double* s2, double* vn, uint8_t* evaluated);
 /* Two-site tensor scored at the last bond visit: shape[0..1] = (chi_l, chi_r); theta receives the

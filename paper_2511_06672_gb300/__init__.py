@@ -120,12 +120,13 @@ class Simulator:
 
     def __init__(self, n: int, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
                  tie_tol: float = 1e-10, batch: int = 1, stream=None, strict_weight: float = 0.0,
-                 cluster_size: int = 8):
+                 cluster_size: int = 8, score_kind: int = 0):
         self._lib = N.load()
         o = N.Opts()
         self._lib.gcamps_default_opts(C.byref(o))
         o.cutoff, o.max_sweeps, o.tie_tol, o.strict_weight = cutoff, max_sweeps, tie_tol, strict_weight
         o.cluster_size = cluster_size
+        o.score_kind = score_kind
         s = _stream_handle(stream)
         o.cuda_stream = C.c_void_p(s) if s else None
         h = C.c_void_p()

@@ -119,6 +119,7 @@ struct Smem {
   int rank0;                  // numerical rank of the identity class's Gram (cluster leader; -1 = none)
   int ord[kMaxK];             // rank of each class in ascending S2 (cluster leader)
   double s2lo[kMaxK];         // lower bound of S2 from the FP32 screen (cluster leader)
+  int rk[kMaxK];              // weight rank of each exactly evaluated class (cluster leader)
   double wtri[kWarps][64];    // per warp: tridiagonal diagonal [0, 32) | off-diagonal squared [32, 64)
   float wtri32[kWarps][64];   // the same in FP32
   double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
@@ -1353,10 +1354,10 @@ __device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, in
 // Scores classes list[0..cnt) (all K classes if list is null) on the whole cluster: small problems
 // one class per warp, large ones one class per CTA.  Results go to the leader CTA's shared memory.
 // mode kExact: S2 and S_vN in FP64; kScreen: S2 in FP32 with its lower bound (lead->s2lo).
-enum ScoreMode { kExact = 0, kScreen = 1 };
+// kS2Exact: S2 in FP64 only (class 0 still gets kExact: its eigenvalues certify QR moves).
+enum ScoreMode { kExact = 0, kScreen = 1, kS2Exact = 2 };
 __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
                               const int* list, int cnt, int mode) {
-  const bool want_vn = mode == kExact;
   const Engine& e = *C.e;
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
@@ -1380,15 +1381,15 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         }
         continue;
       }
+      const bool want_vn = mode == kExact || k == 0;
       const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn,
                                    s.wtri[warp], s.wtri32[warp], 32);
       if (lane == 0) {
         lead->s2[k] = sc.s2;
-        if (want_vn) {
-          lead->vn[k] = sc.vn;
-          lead->evald[k] = 1;
-          if (k == 0) lead->rank0 = sc.rank;
-        }
+        lead->evald[k] = 1;
+        lead->vn[k] = want_vn ? sc.vn : CUDART_NAN;
+        lead->rk[k] = sc.rank;
+        if (k == 0) lead->rank0 = sc.rank;
         if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
       }
     }
@@ -1407,15 +1408,15 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         __syncthreads();
         continue;
       }
+      const bool want_vn = mode == kExact || k == 0;
       const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn,
                                    s.btri, s.btri32, kBTri);
       if (threadIdx.x == 0) {
         lead->s2[k] = sc.s2;
-        if (want_vn) {
-          lead->vn[k] = sc.vn;
-          lead->evald[k] = 1;
-          if (k == 0) lead->rank0 = sc.rank;
-        }
+        lead->evald[k] = 1;
+        lead->vn[k] = want_vn ? sc.vn : CUDART_NAN;
+        lead->rk[k] = sc.rank;
+        if (k == 0) lead->rank0 = sc.rank;
         if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
       }
       __syncthreads();
@@ -1452,62 +1453,113 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
   }
   score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, prune ? kScreen : kExact);
   cluster_sync();
+  const int kind = e.score_kind;
+  // weight-rank threshold (the same as the QR-move certificate) and the rank lower bound from S2:
+  // the weights above tau carry at least 1 - m tau of the trace, so sum p^2 >= (1 - m tau)^2 / rank and
+  // rank >= exp(S2 + 2 ln(1 - m tau)) >= exp(S2 - 2.01 m tau)
+  const double tau_w = fmax(1e-12, 4.0 * e.cutoff * e.cutoff);
+  auto rank_lo = [&](int k) -> int {
+    const double x = s.s2lo[k] - 2.01 * m * tau_w;
+    if (!(x > 0.0) || m * tau_w >= 0.25) return 0;
+    return (int)ceil(exp(x) * (1.0 - 1e-12));
+  };
   if (prune) {
-    if (leader) {
-      // round 1: the identity and the classes of smallest S2, one per FP64 pipe of the cluster
-      // (warp-level scoring) or one per CTA (CTA-level scoring)
-      const int L = (small ? 4 * C.csize : C.csize) - 1;
-      for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-        s.evald[k] = 0;
-        const long long bk = order_key(s.s2lo[k]);
-        int r = 0;
-        for (int q = 0; q < C.K; ++q) {
-          const long long bq = order_key(s.s2lo[q]);
-          r += (bq < bk) || (bq == bk && q < k);
+    if (kind == 1) {
+      // Renyi-2 score: exact S2 for every class whose lower bound is within tie_tol of the smallest
+      // upper bound (upper = screen value + the same margin), and for the identity
+      if (leader && threadIdx.x == 0) {
+        double ub = 1e300;
+        for (int k = 0; k < C.K; ++k) {
+          s.evald[k] = 0;
+          ub = fmin(ub, 2.0 * s.s2[k] - s.s2lo[k]);
         }
-        s.ord[k] = r;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
         int cnt = 1;
         s.list[0] = 0;
         for (int k = 1; k < C.K; ++k)
-          if (s.ord[k] < L) s.list[cnt++] = k;
+          if (s.s2lo[k] <= ub + e.tie_tol + 1e-12) s.list[cnt++] = k;
         s.nlist = cnt;
       }
+      cluster_sync();
+      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kS2Exact);
+      cluster_sync();
+    } else {
+      if (leader) {
+        // round 1: the identity and the classes of smallest S2 lower bound, one per FP64 pipe of the
+        // cluster (warp-level scoring) or one per CTA (CTA-level scoring)
+        const int L = (small ? 4 * C.csize : C.csize) - 1;
+        for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
+          s.evald[k] = 0;
+          const long long bk = order_key(s.s2lo[k]);
+          int r = 0;
+          for (int q = 0; q < C.K; ++q) {
+            const long long bq = order_key(s.s2lo[q]);
+            r += (bq < bk) || (bq == bk && q < k);
+          }
+          s.ord[k] = r;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int cnt = 1;
+          s.list[0] = 0;
+          for (int k = 1; k < C.K; ++k)
+            if (s.ord[k] < L) s.list[cnt++] = k;
+          s.nlist = cnt;
+        }
+      }
+      cluster_sync();
+      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
+      cluster_sync();
+      if (leader && threadIdx.x == 0) {
+        // round 2: every class the bounds cannot exclude.  Kind 0: S2 lower bound within tie_tol of the
+        // best exact entropy.  Kind 2: rank bound below the best exact rank, or equal to it with the S2
+        // bound within tie_tol of the best entropy among the classes of that rank.
+        int rmin = 1 << 30;
+        if (kind == 2)
+          for (int k = 0; k < C.K; ++k)
+            if (s.evald[k] && s.rk[k] < rmin) rmin = s.rk[k];
+        double bound = 1e300;
+        for (int k = 0; k < C.K; ++k)
+          if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) bound = fmin(bound, s.vn[k]);
+        int cnt = 0;
+        for (int k = 0; k < C.K; ++k) {
+          if (s.evald[k]) continue;
+          bool need = s.s2lo[k] <= bound + e.tie_tol + 1e-12;
+          if (kind == 2) {
+            const int rl = rank_lo(k);
+            need = rl < rmin || (rl == rmin && need);
+          }
+          if (need) s.list[cnt++] = k;
+        }
+        s.nlist = cnt;
+      }
+      cluster_sync();
+      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
+      cluster_sync();
     }
-    cluster_sync();
-    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
-    cluster_sync();
-    if (leader && threadIdx.x == 0) {
-      double bound = 1e300;
-      for (int k = 0; k < C.K; ++k)
-        if (s.evald[k]) bound = fmin(bound, s.vn[k]);
-      int cnt = 0;
-      for (int k = 0; k < C.K; ++k)
-        if (!s.evald[k] && s.s2lo[k] <= bound + e.tie_tol + 1e-12) s.list[cnt++] = k;
-      s.nlist = cnt;
-    }
-    cluster_sync();
-    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
-    cluster_sync();
   }
   if (!leader) return -1;
   if (threadIdx.x == 0) {
-    double best = 1e300;
-    int nev = 0;
+    // the decision over the exactly evaluated classes: key = S_vN (kind 0), S2 (kind 1), or the
+    // weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
+    // class is applied only if it beats the identity
+    int nev = 0, rmin = 1 << 30;
     for (int k = 0; k < C.K; ++k)
       if (s.evald[k]) {
-        best = fmin(best, s.vn[k]);
         ++nev;
+        if (s.rk[k] < rmin) rmin = s.rk[k];
       }
+    auto key = [&](int k) { return kind == 1 ? s.s2[k] : s.vn[k]; };
+    double best = 1e300;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) best = fmin(best, key(k));
     int kb = 0;
     for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && s.vn[k] <= best + e.tie_tol) {
+      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin) && key(k) <= best + e.tie_tol) {
         kb = k;
         break;
       }
-    if (!(s.vn[kb] < s.vn[0] - e.tie_tol)) kb = 0;
+    const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
+    if (!better) kb = 0;
     s.ival[4] = kb;
     s.ival[5] = nev;
   }
@@ -1559,7 +1611,9 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     {
       const double R = rows, Cc = cols, mm = m, M = rows < cols ? cols : rows;
       const double per_class = 8.0 * dd * R * Cc + 4.0 * mm * (mm + 1.0) * M;
-      C.dstats[1] += nev * (per_class + (16.0 / 3.0) * mm * mm * mm);   // exact evaluations, FP64
+      const double tri = (16.0 / 3.0) * mm * mm * mm;
+      // exact evaluations, FP64 (Renyi-2 scores need no eigenvalues except the identity's)
+      C.dstats[1] += e.score_kind == 1 ? nev * per_class + tri : nev * (per_class + tri);
       if (m > kPruneMin) C.dstats[2] += C.K * per_class;                // FP32 screen of every class
     }
     const int nd = C.meta[M_NDEC];

@@ -465,7 +465,8 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   gcamps_opts opts;
   gcamps_default_opts(&opts);
   if (o) opts = *o;
-  if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind != 0 || opts.precision != 0 ||
+  if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind < 0 || opts.score_kind > 2 ||
+      opts.precision != 0 ||
       !(opts.tie_tol >= 0.0))
     return GCAMPS_EINVAL;
   if (opts.cluster_size == 0) opts.cluster_size = 8;
@@ -482,6 +483,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.chi_max = chi_max;
   e.batch = batch;
   e.max_sweeps = opts.max_sweeps;
+  e.score_kind = opts.score_kind;
   e.cutoff = opts.cutoff;
   e.tie_tol = opts.tie_tol;
   e.strict_weight = opts.strict_weight;

@@ -48,6 +48,7 @@ struct CtaLayout {
 
 struct Engine {
   int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;
+  int score_kind;                 // 0 von Neumann, 1 Renyi-2, 2 weight rank then von Neumann
   double cutoff, tie_tol, strict_weight;
   long long tcap;                 // elements of the largest two-site matrix
   long long wcap;                 // elements of the largest Jacobi rotation matrix

@@ -88,3 +88,15 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = C.c_void_p()
     rc = lib.gcamps_create(4, 3, 8, None, C.byref(h))
     assert rc != 0 and not h.value
+
+
+def test_create_rejects_bad_options_before_touching_the_gpu(lib):
+    """Option validation (score_kind 0..2, power-of-two cluster size) happens on the host first."""
+    from paper_2511_06672_gb300 import _native as N
+    for field, value in (("score_kind", 3), ("score_kind", -1), ("cluster_size", 3), ("max_sweeps", -1)):
+        o = N.Opts()
+        lib.gcamps_default_opts(C.byref(o))
+        setattr(o, field, value)
+        h = C.c_void_p()
+        assert lib.gcamps_create(4, 3, 8, C.byref(o), C.byref(h)) == N.EINVAL
+        assert not h.value

@@ -344,3 +344,27 @@ def test_score_theta_householder_edge_cases(G, kind, cl, cr, seed, tol):
     assert 1 <= nev <= len(want)   # the Renyi-2 bound prunes at every size
     r2 = np.array([_renyi2(theta, u) for (_s, _i, u) in ref.cands])
     assert np.max(np.abs(s2 - r2)) < TOL
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("d,n,layers,t,seed,chi", [(3, 8, 10, 14, 41, 81), (2, 10, 10, 10, 3, 64),
+                                                   (3, 12, 12, 16, 31, 64)])
+def test_score_kinds_match_oracle(G, kind, d, n, layers, t, seed, chi):
+    """Renyi-2 (kind 1) and weight-rank (kind 2) scores: decisions and bond dimensions equal the
+    oracle's (which scores every class by SVD), and the state stays exact."""
+    gates = brickwork_circuit(n, d, layers, t, seed)
+    sim = G.Simulator(n, d, chi_max=chi, cutoff=1e-12, score_kind=kind)
+    sim.run(G.ops_from_gates(gates, d))
+    sim.sync()
+    ref = GCAMPS(n, d, chi_max=chi, cutoff=1e-12, score_kind=kind)
+    for gt in gates:
+        ref.apply_gate(gt)
+        if not hasattr(gt, "sp_index"):
+            ref.disentangle()
+    assert sim.decisions() == ref.decisions
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    assert any(k for _b, k in ref.decisions)
+    if d ** n <= 6561:
+        err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
+        assert err < TOL
+    sim.close()
