@@ -157,6 +157,119 @@ def cpu_oracle_sample(budget_s: float = 20.0):
         seed += 1
 
 
+def run_batched(args):
+    """The batched form: 256 independent qutrit circuits of uneven size (n and layers uniform in
+    [16, 48], n T gates each, chi_max = 128) in one handle; every step is one reset and one engine
+    launch over all of them, captured once in a CUDA graph and replayed.  The CTAs per circuit are
+    picked by measurement during the warm-up (2, 4 or 8: the autotuned shape)."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    from synth import batched_workload, brickwork_circuit
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    d, chi = 3, 128
+    count = args.batched_count
+    shapes = batched_workload(count, seed0=rank * count, n_range=(16, args.batched_nmax),
+                              layer_range=(16, args.batched_nmax))
+    ops, begin = [], [0]
+    for n, layers, t, seed in shapes:
+        o = G.ops_from_gates(brickwork_circuit(n, d, layers, t, seed), d)
+        ops.append(o)
+        begin.append(begin[-1] + len(o))
+    ops = np.concatenate(ops)
+    stream = torch.cuda.Stream()
+    sizes = [int(x) for x in args.batched_clusters.split(",")]
+    sim = G.Simulator([x[0] for x in shapes], d, chi_max=chi, cutoff=CUTOFF, stream=stream, cluster_size=max(sizes))
+    ops_dev = torch.from_numpy(ops.view(np.uint8)).to(f"cuda:{local}")
+    begin_dev = torch.from_numpy(np.array(begin, dtype=np.int32)).to(f"cuda:{local}")
+    lib = G._native.load()
+    torch.cuda.synchronize()
+
+    def step():
+        rc = lib.gcamps_reset(sim._h)
+        if rc == 0:
+            rc = lib.gcamps_run_device(sim._h, C.c_void_p(ops_dev.data_ptr()), C.c_void_p(begin_dev.data_ptr()))
+        if rc:
+            raise RuntimeError(lib.gcamps_last_error(sim._h).decode())
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    tune = {}
+    for cs in sizes:                 # autotune the CTAs per circuit on the workload itself
+        sim.set_cluster_size(cs)
+        tune[cs] = timed(step)
+        progress(f"batched: {cs} CTAs per circuit: {tune[cs]:.2f} s")
+    best = min(tune, key=tune.get)
+    sim.set_cluster_size(best)
+    graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step()
+        graph = g
+    except Exception as ex:          # run uncaptured if this torch build cannot capture the launch
+        progress(f"batched: graph capture failed ({ex}); launching directly")
+    def replay():
+        with torch.cuda.stream(stream):   # a graph replays on the current stream: make it the handle's
+            graph.replay()
+
+    run = replay if graph is not None else step
+    for _ in range(max(0, args.warmup - 3)):
+        timed(run)
+    sim.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = [timed(run) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total = sum(times)
+    if world > 1:
+        tt = torch.tensor([total], device=f"cuda:{local}", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total = float(tt.item())
+    stats = [sim.stats(c) for c in range(len(shapes))]
+    if any(st["status"] for st in stats):
+        raise RuntimeError("device status set")
+    tg = sum(st["t_gates"] for st in stats)
+    line = {
+        "metric": METRIC, "value": tg * args.steps * world / total, "unit": "T-gates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"gcamps-batched-{count}-qutrit-n16..{args.batched_nmax}-L16..{args.batched_nmax}-T=n-chi128",
+                   "circuits_per_rank": count,
+                   "d": d, "chi_max": chi, "cutoff": CUTOFF, "cluster_ctas_per_circuit": best,
+                   "autotune_s": {str(k): round(v, 3) for k, v in tune.items()},
+                   "graph_captured": graph is not None, "parallelism": f"replicas x{world}",
+                   "l2": "inputs (MPS, scratch) far larger than L2"},
+        "candidates_per_s": sum(st["candidates_scored"] for st in stats) * args.steps * world / total,
+        "max_chi": max(st["max_chi"] for st in stats),
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -192,6 +305,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "batched"],
+                    help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch")
+    ap.add_argument("--batched-count", type=int, default=64)
+    ap.add_argument("--batched-nmax", type=int, default=24, help="n and layers uniform in [16, this]")
+    ap.add_argument("--batched-clusters", default="8,4", help="CTAs per circuit tried by the autotuner")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
@@ -200,6 +318,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

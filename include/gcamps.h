@@ -130,7 +130,19 @@ int gcamps_candidate(int d, int k, int32_t* img, double* u);
  * gcamps_create is gcamps_create_batch with batch = 1. */
 int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
+/* Batch of circuits with their own qudit counts n[c] (2 <= n[c] <= 128), for many independent
+ * circuits of uneven size in one engine launch (gcamps_run with per-circuit op ranges).  Memory is
+ * reserved per circuit for its own n[c]; calls that apply to every circuit (apply_*, disentangle)
+ * require sites below the smallest n[c]; readouts use the circuit's own n[c]. */
+int gcamps_create_batch_uneven(int batch, const int32_t* n, int d, int chi_max, const gcamps_opts* o,
+                               gcamps_t** out);
 void gcamps_destroy(gcamps_t* h);
+/* Qudits of circuit `circuit` (-1 for a bad handle or index). */
+int gcamps_num_qudits(gcamps_t* h, int circuit);
+/* CTAs per circuit for the following launches: a power of two up to the cluster size the handle was
+ * created with (its per-CTA scratch is laid out for that many).  Synchronises the handle's stream.
+ * Used to pick the fastest cluster size for a workload by measurement. */
+int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
 
 /* C <- G C for a one- or two-qudit Clifford G (Sec. 3, top loop of Fig. 3): the tableau rows
  * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every

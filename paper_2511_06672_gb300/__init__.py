@@ -116,9 +116,10 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 class Simulator:
-    """psi = C|MPS> for ``batch`` independent circuits of n qudits (Sec. 3 of the paper)."""
+    """psi = C|MPS> for ``batch`` independent circuits of n qudits (Sec. 3 of the paper).  ``n`` may
+    be a sequence of per-circuit qudit counts (uneven batch; ``batch`` is then its length)."""
 
-    def __init__(self, n: int, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
+    def __init__(self, n, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
                  tie_tol: float = 1e-10, batch: int = 1, stream=None, strict_weight: float = 0.0,
                  cluster_size: int = 8, score_kind: int = 0):
         self._lib = N.load()
@@ -130,11 +131,24 @@ class Simulator:
         s = _stream_handle(stream)
         o.cuda_stream = C.c_void_p(s) if s else None
         h = C.c_void_p()
-        rc = self._lib.gcamps_create_batch(batch, n, d, chi_max, C.byref(o), C.byref(h))
+        if np.ndim(n) == 0:
+            nq = [int(n)] * batch
+            rc = self._lib.gcamps_create_batch(batch, int(n), d, chi_max, C.byref(o), C.byref(h))
+        else:
+            nq = [int(x) for x in n]
+            batch = len(nq)
+            na = np.ascontiguousarray(nq, dtype=np.int32)
+            rc = self._lib.gcamps_create_batch_uneven(batch, N.ptr(na, C.c_int32), d, chi_max, C.byref(o),
+                                                      C.byref(h))
         if rc:
             raise GcampsError(rc, "gcamps_create failed")
         self._h = h
-        self.n, self.d, self.chi_max, self.batch = n, d, chi_max, batch
+        self.nq = nq
+        self.n = max(nq)
+        self.d, self.chi_max, self.batch = d, chi_max, batch
+
+    def set_cluster_size(self, cluster_size: int):
+        self._c(self._lib.gcamps_set_cluster_size(self._h, cluster_size))
 
     # -- lifetime
     def close(self):
@@ -197,7 +211,7 @@ class Simulator:
         return complex(re.value, im.value)
 
     def statevector(self, circuit: int = 0) -> np.ndarray:
-        dim = self.d ** self.n
+        dim = self.d ** self.nq[circuit]
         re, im = np.zeros(dim), np.zeros(dim)
         self._c(self._lib.gcamps_statevector(self._h, circuit, N.ptr(re, C.c_double), N.ptr(im, C.c_double)))
         return re + 1j * im
@@ -209,21 +223,21 @@ class Simulator:
         return complex(re.value, im.value)
 
     def tableau(self, circuit: int = 0):
-        n = self.n
+        n = self.nq[circuit]
         e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
         p = np.zeros(2 * n, dtype=np.uint8)
         self._c(self._lib.gcamps_get_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
         return e, p
 
     def inverse_tableau(self, circuit: int = 0):
-        n = self.n
+        n = self.nq[circuit]
         e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
         p = np.zeros(2 * n, dtype=np.uint8)
         self._c(self._lib.gcamps_get_inverse_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
         return e, p
 
     def bond_dims(self, circuit: int = 0) -> list:
-        a = np.zeros(self.n - 1, dtype=np.int32)
+        a = np.zeros(self.nq[circuit] - 1, dtype=np.int32)
         self._c(self._lib.gcamps_get_bond_dims(self._h, circuit, N.ptr(a, C.c_int32)))
         return a.tolist()
 
@@ -243,8 +257,8 @@ class Simulator:
         return t.reshape(tuple(int(x) for x in dims))
 
     def last_weyl(self, circuit: int = 0):
-        x = np.zeros(self.n, dtype=np.int32)
-        z = np.zeros(self.n, dtype=np.int32)
+        x = np.zeros(self.nq[circuit], dtype=np.int32)
+        z = np.zeros(self.nq[circuit], dtype=np.int32)
         r = C.c_int32()
         self._c(self._lib.gcamps_get_last_weyl(self._h, circuit, N.ptr(x, C.c_int32), N.ptr(z, C.c_int32),
                                                C.byref(r)))

@@ -38,7 +38,8 @@ class Stats(C.Structure):
 EXPORTS = [
     "gcamps_default_opts", "gcamps_num_candidates", "gcamps_sp4_images", "gcamps_candidate",
     "gcamps_create",
-    "gcamps_create_batch", "gcamps_destroy", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
+    "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_destroy", "gcamps_num_qudits",
+    "gcamps_set_cluster_size", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
     "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
@@ -66,7 +67,10 @@ def load(path: str = LIB_PATH):
         "gcamps_candidate": (C.c_int, [C.c_int, C.c_int, i32p, dp]),
         "gcamps_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
         "gcamps_create_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
+        "gcamps_create_batch_uneven": (C.c_int, [C.c_int, i32p, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
         "gcamps_destroy": (None, [vp]),
+        "gcamps_num_qudits": (C.c_int, [vp, C.c_int]),
+        "gcamps_set_cluster_size": (C.c_int, [vp, C.c_int]),
         "gcamps_apply_clifford": (C.c_int, [vp, C.c_int, C.c_int, i32p]),
         "gcamps_apply_nonclifford": (C.c_int, [vp, C.c_int, dp]),
         "gcamps_disentangle": (C.c_int, [vp, C.POINTER(Stats)]),

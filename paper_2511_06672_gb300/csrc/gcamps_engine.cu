@@ -139,6 +139,8 @@ struct Ctx {
   int rank, csize;            // position in the circuit's cluster; rank 0 leads
   double2* cta;               // this CTA's scoring scratch
   float2* th32;               // FP32 copy of the two-site tensor being scored
+  const long long* site_off;  // this circuit's slot offsets
+  const int* bond_bound;      // this circuit's Schmidt-rank bounds
   uint8_t *fx, *fr, *ix, *ir;
   double2* mps;
   int* dims;
@@ -152,7 +154,7 @@ struct Ctx {
   int* perm;
 };
 
-__device__ __forceinline__ double2* site_ptr(const Ctx& C, int j) { return C.mps + C.e->site_off[j]; }
+__device__ __forceinline__ double2* site_ptr(const Ctx& C, int j) { return C.mps + C.site_off[j]; }
 
 __device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   Ctx C;
@@ -162,22 +164,24 @@ __device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   C.csize = e.csize;
   C.cta = e.cscr + ((long long)c * e.csize + rank) * e.cl.total;
   C.th32 = reinterpret_cast<float2*>(e.scr + (long long)c * e.sl.total + e.sl.tmp);
-  C.n = e.n;
+  const int n = e.nq[c];   // the circuit's tableau is stored compactly in its n_max-sized slot
+  C.n = n;
   C.d = e.d;
   C.K = e.K;
   uint8_t* t = e.tab + (long long)c * e.tab_stride;
-  const int n = e.n;
   C.fx = t;
   C.fr = t + 4 * n * n;
   C.ix = C.fr + 2 * n;
   C.ir = C.ix + 4 * n * n;
-  C.mps = e.mps + (long long)c * e.mps_stride;
-  C.dims = e.dims + (long long)c * (n + 1);
+  C.mps = e.mps + e.mps_base[c];
+  C.site_off = e.site_off + (long long)c * (e.n + 1);
+  C.bond_bound = e.bond_bound + (long long)c * (e.n + 1);
+  C.dims = e.dims + (long long)c * (e.n + 1);
   C.meta = e.meta + (long long)c * M_COUNT;
   C.stats = e.stats + (long long)c * S_COUNT;
   C.dstats = e.dstats + (long long)c * 4;
   C.dec = e.dec + (long long)c * kDecCap * 2;
-  C.weyl = e.weyl + (long long)c * 2 * n;
+  C.weyl = e.weyl + (long long)c * 2 * e.n;
   C.scr = e.scr + (long long)c * e.sl.total;
   C.sing = e.sing + (long long)c * e.sing_stride;
   C.perm = e.iscr + (long long)c * e.iscr_stride;
@@ -801,7 +805,7 @@ __device__ double move_left(Smem& s, const Ctx& C, int j, int cap, bool renorm) 
   const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
   double2* A = site_ptr(C, j);
   double2* A0 = site_ptr(C, j - 1);
-  const int bb = C.e->bond_bound[j];
+  const int bb = C.bond_bound[j];
   Factor F = svd_factor(s, C, A, cl, d * cr, cap < bb ? cap : bb, renorm);
   const int k = F.k;
   block_copy(A, F.Vh, (long long)k * d * cr);
@@ -1409,7 +1413,7 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         continue;
       }
       const bool want_vn = mode == kExact || k == 0;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.tcap, want_vn,
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.scap, want_vn,
                                    s.btri, s.btri32, kBTri);
       if (threadIdx.x == 0) {
         lead->s2[k] = sc.s2;
@@ -1642,7 +1646,7 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     if (threadIdx.x == 0) C.stats[S_ACC] += 1;
     ++*accepted;
   }
-  const int bb = e.bond_bound[i + 1];
+  const int bb = C.bond_bound[i + 1];
   const int cap = e.chi_max < bb ? e.chi_max : bb;
   // Nothing applied and the identity class's Gram has exactly chi eigenvalues above
   // max(1e-12, 4 cutoff^2) tr (theta has rank <= chi, the bond dimension): every one of those
@@ -1804,7 +1808,7 @@ __global__ void __launch_bounds__(kThreads) k_score_theta(Engine e, const double
 // |0...0> with C = I, counters cleared.
 __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
   Ctx C = make_ctx(e, blockIdx.x);
-  const int n = e.n, d = e.d;
+  const int n = C.n, d = e.d;
   for (int i = threadIdx.x; i < 4 * n * n; i += blockDim.x) {
     const int row = i / (2 * n), col = i % (2 * n);
     // row j < n: Z_j -> z column n + j; row n + j: X_j -> x column j
@@ -1836,7 +1840,7 @@ __global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8
   __shared__ int acc_r;
   Ctx C = make_ctx(e, c);
   init_tau(s, e.d);
-  const int n = e.n, d = e.d;
+  const int n = C.n, d = e.d;
   for (int j = threadIdx.x; j < n; j += blockDim.x) acc_x[j] = acc_z[j] = 0;
   if (threadIdx.x == 0) acc_r = 0;
   __syncthreads();
@@ -1913,7 +1917,7 @@ __global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond,
 // of dim * maxdim entries each (the partial contraction over sites 0..j has d^{j+1} chi_{j+1}).
 __global__ void __launch_bounds__(kThreads) k_mps_dense(Engine e, int c, double2* mv, double2* bufa, double2* bufb, long long dim) {
   Ctx C = make_ctx(e, c);
-  const int n = e.n, d = e.d;
+  const int n = C.n, d = e.d;
   double2* cur = bufa;
   double2* nxt = bufb;
   long long rowsn = d;
@@ -1938,7 +1942,7 @@ __global__ void k_weyl_of_labels(Engine e, int c, long long dim, int* aidx, uint
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= dim) return;
   Ctx C = make_ctx(e, c);
-  const int n = e.n, d = e.d;
+  const int n = C.n, d = e.d;
   int ax[kMaxN], az[kMaxN];
   for (int j = 0; j < n; ++j) ax[j] = az[j] = 0;
   int r = 0;
@@ -1982,7 +1986,7 @@ __global__ void __launch_bounds__(kThreads) k_stab_state(Engine e, int c, long l
   __shared__ Smem s;
   Ctx C = make_ctx(e, c);
   init_tau(s, e.d);
-  const int n = e.n, d = e.d;
+  const int n = C.n, d = e.d;
   for (long long y = threadIdx.x; y < dim; y += blockDim.x) {
     const unsigned long long h = mix64((unsigned long long)y * 2 + 1);
     const unsigned long long g = mix64((unsigned long long)y * 2 + 2);
@@ -2028,12 +2032,12 @@ __global__ void __launch_bounds__(kThreads) k_stab_state(Engine e, int c, long l
 }
 
 // psi(y) = sum_x M_x tau^{rho(x)} omega^{b(x).(y - a(x))} s0(y - a(x)) for the requested labels y.
-__global__ void k_apply_clifford_dense(Engine e, long long dim, const double2* mv, const double2* s0,
+__global__ void k_apply_clifford_dense(Engine e, int c, long long dim, const double2* mv, const double2* s0,
                                        const int* aidx, const uint8_t* bdig, const int* rho,
                                        const int32_t* ys, long long nys, double2* out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nys) return;
-  const int n = e.n, d = e.d;
+  const int n = e.nq[c], d = e.d;
   const long long y = ys ? ys[t] : t;
   int yd[kMaxN];
   {
@@ -2146,7 +2150,7 @@ cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, l
   const int blk = 128;
   k_weyl_of_labels<<<(unsigned)((dim + blk - 1) / blk), blk, 0, st>>>(e, circuit, dim, aidx, bdig, rho);
   k_stab_state<<<1, kThreads, 0, st>>>(e, circuit, dim, s0, w);
-  k_apply_clifford_dense<<<(unsigned)((nys + blk - 1) / blk), blk, 0, st>>>(e, dim, mv, s0, aidx, bdig, rho,
+  k_apply_clifford_dense<<<(unsigned)((nys + blk - 1) / blk), blk, 0, st>>>(e, circuit, dim, mv, s0, aidx, bdig, rho,
                                                                           ys_dev, nys, out_dev);
   return cudaGetLastError();
 }
@@ -2259,6 +2263,7 @@ cudaError_t launch_score_theta_static(int device, int d, double tie_tol, const d
   e.tie_tol = tie_tol;
   e.tcap = kStaticTcap;
   e.wcap = kStaticTcap;
+  e.scap = kStaticTcap;
   e.cscr = p.scratch;
   e.cl.warp = 0;
   e.cl.block = (long long)kWarps * kSmallStride;

@@ -346,6 +346,11 @@ bool valid_images(const int32_t* img, int nq, int d, std::string* why) {
 // ------------------------------------------------------------------------------------ handle
 struct gcamps {
   Engine e{};
+  std::vector<int> nq;                 // qudits of each circuit
+  std::vector<long long> site_off;     // [batch][n_max + 1] slot offsets within a circuit's block
+  std::vector<long long> mps_base;     // [batch] offset of each circuit's block
+  int nmin = 0;                        // smallest qudit count of the batch
+  int csize_alloc = 0;                 // cluster size the per-CTA scratch was laid out for
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
@@ -461,7 +466,21 @@ int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** ou
 int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out) {
   if (!out) return GCAMPS_EINVAL;
   *out = nullptr;
-  if (batch < 1 || n < 2 || n > gcx::kMaxN || (d != 2 && d != 3) || chi_max < 1) return GCAMPS_EINVAL;
+  if (batch < 1 || n < 2 || n > gcx::kMaxN) return GCAMPS_EINVAL;
+  const std::vector<int32_t> nv((size_t)batch, n);
+  return gcamps_create_batch_uneven(batch, nv.data(), d, chi_max, o, out);
+}
+
+int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max, const gcamps_opts* o,
+                               gcamps_t** out) {
+  if (!out) return GCAMPS_EINVAL;
+  *out = nullptr;
+  if (batch < 1 || !nqs || (d != 2 && d != 3) || chi_max < 1) return GCAMPS_EINVAL;
+  int n = 0;
+  for (int c = 0; c < batch; ++c) {
+    if (nqs[c] < 2 || nqs[c] > gcx::kMaxN) return GCAMPS_EINVAL;
+    n = std::max(n, (int)nqs[c]);
+  }
   gcamps_opts opts;
   gcamps_default_opts(&opts);
   if (o) opts = *o;
@@ -487,25 +506,35 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.cutoff = opts.cutoff;
   e.tie_tol = opts.tie_tol;
   e.strict_weight = opts.strict_weight;
-  // bond capacities: after the MPO a bond holds at most d * min(chi_max, Schmidt bound)
-  std::vector<long long> cap(n + 1, 1);
-  std::vector<int> bound(n + 1, 1);
-  long long maxdim = 1;
-  for (int b = 1; b < n; ++b) {
-    const long long sb = sat_pow(d, std::min(b, n - b), 1LL << 30);
-    bound[b] = (int)sb;
-    cap[b] = d * std::min<long long>(chi_max, sb);
-    maxdim = std::max(maxdim, cap[b]);
+  // bond capacities of each circuit: after the MPO a bond holds at most d * min(chi_max, Schmidt
+  // bound); slots of each circuit's sites laid out back to back, circuits one after another
+  h->nq.assign(nqs, nqs + batch);
+  h->nmin = *std::min_element(nqs, nqs + batch);
+  h->site_off.assign((size_t)batch * (n + 1), 0);
+  h->mps_base.assign((size_t)batch, 0);
+  std::vector<int> bound((size_t)batch * (n + 1), 1);
+  long long maxdim = 1, tcap = 1, mps_total = 0;
+  for (int c = 0; c < batch; ++c) {
+    const int nc = nqs[c];
+    std::vector<long long> cap(nc + 1, 1);
+    for (int b = 1; b < nc; ++b) {
+      const long long sb = sat_pow(d, std::min(b, nc - b), 1LL << 30);
+      bound[(size_t)c * (n + 1) + b] = (int)sb;
+      cap[b] = d * std::min<long long>(chi_max, sb);
+      maxdim = std::max(maxdim, cap[b]);
+    }
+    long long* off = &h->site_off[(size_t)c * (n + 1)];
+    for (int j = 0; j < nc; ++j) {
+      const long long sz = cap[j] * d * cap[j + 1];
+      off[j + 1] = off[j] + sz;
+      tcap = std::max(tcap, sz);
+      if (j + 2 <= nc) tcap = std::max(tcap, cap[j] * d * d * cap[j + 2]);
+    }
+    for (int j = nc + 1; j <= n; ++j) off[j] = off[nc];
+    h->mps_base[c] = mps_total;
+    mps_total += (off[nc] + 31) / 32 * 32;   // 512-byte aligned circuit blocks
   }
   e.maxdim = (int)maxdim;
-  std::vector<long long> off(n + 1, 0);
-  long long tcap = 1;
-  for (int j = 0; j < n; ++j) {
-    const long long sz = cap[j] * d * cap[j + 1];
-    off[j + 1] = off[j] + sz;
-    tcap = std::max(tcap, sz);
-    if (j + 2 <= n) tcap = std::max(tcap, cap[j] * d * d * cap[j + 2]);
-  }
   const long long maxm = (long long)d * maxdim;
   e.tcap = tcap;
   e.wcap = maxm * maxm;
@@ -518,12 +547,17 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   sl.tmp = sl.vh + tcap;
   sl.total = sl.tmp + tcap;
   e.csize = opts.cluster_size;
+  h->csize_alloc = opts.cluster_size;
   gcx::CtaLayout& cly = e.cl;
   cly.warp = 0;
   cly.block = (long long)gcx::kWarps * gcx::kSmallStride;
-  cly.total = cly.block + tcap + e.wcap + maxm + 64;
+  // CTA-level scoring sees theta only after compression (every bond <= chi_max), so theta' and its
+  // Gram hold at most (d chi_max)^2 entries each
+  const long long sside = (long long)d * std::min<long long>(chi_max, maxdim);
+  e.scap = sside * sside;
+  cly.total = cly.block + 2 * e.scap + sside + 64;
   e.tab_stride = 2LL * (4LL * n * n + 2LL * n);
-  e.mps_stride = off[n];
+
   e.sing_stride = 4 * maxm + 128;   // singular values | sort scratch / QR betas | QR diagonal
   e.iscr_stride = maxm + 64;
   // one device block, carved up
@@ -532,11 +566,15 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   const size_t o_tab = bytes;
   bytes = align(bytes + (size_t)batch * e.tab_stride);
   const size_t o_mps = bytes;
-  bytes = align(bytes + (size_t)batch * e.mps_stride * sizeof(double2));
+  bytes = align(bytes + (size_t)mps_total * sizeof(double2));
   const size_t o_off = bytes;
-  bytes = align(bytes + (size_t)(n + 1) * sizeof(long long));
+  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(long long));
   const size_t o_bound = bytes;
-  bytes = align(bytes + (size_t)(n + 1) * sizeof(int));
+  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(int));
+  const size_t o_nq = bytes;
+  bytes = align(bytes + (size_t)batch * sizeof(int));
+  const size_t o_base = bytes;
+  bytes = align(bytes + (size_t)batch * sizeof(long long));
   const size_t o_dims = bytes;
   bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(int));
   const size_t o_meta = bytes;
@@ -588,6 +626,8 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   e.mps = (double2*)(base + o_mps);
   e.site_off = (const long long*)(base + o_off);
   e.bond_bound = (const int*)(base + o_bound);
+  e.nq = (const int*)(base + o_nq);
+  e.mps_base = (const long long*)(base + o_base);
   e.dims = (int*)(base + o_dims);
   e.meta = (int*)(base + o_meta);
   e.stats = (long long*)(base + o_stats);
@@ -605,11 +645,16 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   h->xz_dev = (int8_t*)(base + o_aux);
   h->out_dev = (double2*)(base + o_aux + align(gcx::kMaxN * 2));
   h->cnt_dev = (int*)(h->out_dev + 2);
-  cudaError_t ce = cudaMemcpyAsync((void*)e.site_off, off.data(), (size_t)(n + 1) * sizeof(long long),
+  cudaError_t ce = cudaMemcpyAsync((void*)e.site_off, h->site_off.data(), h->site_off.size() * sizeof(long long),
                                    cudaMemcpyHostToDevice, h->stream);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync((void*)e.bond_bound, bound.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+    ce = cudaMemcpyAsync((void*)e.bond_bound, bound.data(), bound.size() * sizeof(int), cudaMemcpyHostToDevice,
                          h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.nq, h->nq.data(), h->nq.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.mps_base, h->mps_base.data(), h->mps_base.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice, h->stream);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((void*)e.candU, tb.u.data(), tb.u.size() * sizeof(double), cudaMemcpyHostToDevice,
                          h->stream);
@@ -645,7 +690,7 @@ const char* gcamps_last_error(gcamps_t* h) { return h ? h->err.c_str() : "null h
 
 int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img) {
   if (!h) return GCAMPS_EINVAL;
-  const int n = h->e.n;
+  const int n = h->nmin;   // applied to every circuit
   if (!img || q0 < 0 || q0 >= n || q1 >= n || q1 == q0 || q1 < -1)
     return fail(h, GCAMPS_EINVAL, "bad qudit indices or null images");
   const int nq = q1 < 0 ? 1 : 2;
@@ -663,7 +708,7 @@ int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img) {
 
 int gcamps_apply_nonclifford(gcamps_t* h, int site, const double* phases) {
   if (!h) return GCAMPS_EINVAL;
-  if (!phases || site < 0 || site >= h->e.n) return fail(h, GCAMPS_EINVAL, "bad site or null phases");
+  if (!phases || site < 0 || site >= h->nmin) return fail(h, GCAMPS_EINVAL, "bad site or null phases");
   gcamps_op op;
   std::memset(&op, 0, sizeof op);
   op.kind = GCAMPS_OP_NONCLIFFORD;
@@ -687,11 +732,11 @@ int gcamps_disentangle(gcamps_t* h, gcamps_stats* st) {
   return GCAMPS_OK;
 }
 
-static int validate_ops(gcamps_t* h, const gcamps_op* ops, int nops) {
+// Ops i in [0, nops) run on circuits with at least n qudits.
+static int validate_ops(gcamps_t* h, const gcamps_op* ops, int nops, int n) {
   std::string why;
   for (int i = 0; i < nops; ++i) {
     const gcamps_op& op = ops[i];
-    const int n = h->e.n;
     switch (op.kind) {
       case GCAMPS_OP_CLIFFORD: {
         if (op.q0 < 0 || op.q0 >= n || op.q1 >= n || op.q1 == op.q0 || op.q1 < -1)
@@ -721,7 +766,13 @@ int gcamps_run(gcamps_t* h, const gcamps_op* ops, int nops, const int32_t* begin
     for (int c = 0; c < h->e.batch; ++c)
       if (begin[c + 1] < begin[c] || begin[c + 1] > nops) return fail(h, GCAMPS_EINVAL, "bad begin offsets");
   }
-  int rc = validate_ops(h, ops, nops);
+  int rc = GCAMPS_OK;
+  if (begin) {
+    for (int c = 0; c < h->e.batch && !rc; ++c)
+      rc = validate_ops(h, ops + begin[c], begin[c + 1] - begin[c], h->nq[c]);
+  } else {
+    rc = validate_ops(h, ops, nops, h->nmin);
+  }
   if (rc) return rc;
   if (nops == 0) return GCAMPS_OK;
   if ((size_t)nops > h->ops_cap) {
@@ -757,6 +808,20 @@ int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begi
   return GCAMPS_OK;
 }
 
+int gcamps_num_qudits(gcamps_t* h, int circuit) {
+  if (!h || circuit < 0 || circuit >= h->e.batch) return -1;
+  return h->nq[circuit];
+}
+
+int gcamps_set_cluster_size(gcamps_t* h, int cluster_size) {
+  if (!h) return GCAMPS_EINVAL;
+  if (cluster_size < 1 || cluster_size > h->csize_alloc || (cluster_size & (cluster_size - 1)))
+    return fail(h, GCAMPS_EINVAL, "cluster size must be a power of two up to the one the handle was created with");
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->e.csize = cluster_size;
+  return GCAMPS_OK;
+}
+
 int gcamps_sync(gcamps_t* h) {
   if (!h) return GCAMPS_EINVAL;
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -778,7 +843,7 @@ static int check_circuit(gcamps_t* h, int circuit) {
 int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* re, double* im) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  const int n = h->e.n, d = h->e.d;
+  const int n = h->nq[circuit], d = h->e.d;
   if (!x || !z || !re || !im) return fail(h, GCAMPS_EINVAL, "null argument");
   std::vector<int8_t> xz(2 * n);
   for (int j = 0; j < n; ++j) {
@@ -797,7 +862,7 @@ int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t
 }
 
 static int statevector_impl(gcamps_t* h, int circuit, const int32_t* ys, long long nys, double* re, double* im) {
-  const int n = h->e.n, d = h->e.d;
+  const int n = h->nq[circuit], d = h->e.d;
   long long dim = 1;
   for (int j = 0; j < n; ++j) {
     dim *= d;
@@ -837,7 +902,7 @@ int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im) {
   if (rc) return rc;
   if (!re || !im) return fail(h, GCAMPS_EINVAL, "null output");
   long long dim = 1;
-  for (int j = 0; j < h->e.n; ++j) {
+  for (int j = 0; j < h->nq[circuit]; ++j) {
     dim *= h->e.d;
     if (dim > (1LL << 20)) return fail(h, GCAMPS_EINVAL, "d^n above 2^20: dense readout not supported");
   }
@@ -849,7 +914,7 @@ int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re
   if (rc) return rc;
   if (!digits || !re || !im) return fail(h, GCAMPS_EINVAL, "null argument");
   long long y = 0;
-  for (int j = 0; j < h->e.n; ++j) {
+  for (int j = 0; j < h->nq[circuit]; ++j) {
     if (digits[j] < 0 || digits[j] >= h->e.d) return fail(h, GCAMPS_EINVAL, "digit out of range");
     y = y * h->e.d + digits[j];
     if (y > (1LL << 30)) return fail(h, GCAMPS_EINVAL, "d^n above 2^20: dense readout not supported");
@@ -861,7 +926,7 @@ int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re
 int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  const int n = h->e.n;
+  const int n = h->nq[circuit];
   const uint8_t* t = h->e.tab + (long long)circuit * h->e.tab_stride;
   if (exps) GC_CUDA(h, cudaMemcpyAsync(exps, t, 4 * n * n, cudaMemcpyDeviceToHost, h->stream));
   if (phase) GC_CUDA(h, cudaMemcpyAsync(phase, t + 4 * n * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
@@ -872,7 +937,7 @@ int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) 
 int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  const int n = h->e.n;
+  const int n = h->nq[circuit];
   const uint8_t* t = h->e.tab + (long long)circuit * h->e.tab_stride + 4 * n * n + 2 * n;
   if (exps) GC_CUDA(h, cudaMemcpyAsync(exps, t, 4 * n * n, cudaMemcpyDeviceToHost, h->stream));
   if (phase) GC_CUDA(h, cudaMemcpyAsync(phase, t + 4 * n * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
@@ -884,9 +949,9 @@ int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
   if (!chi) return fail(h, GCAMPS_EINVAL, "null output");
-  const int n = h->e.n;
+  const int n = h->nq[circuit];
   std::vector<int> dims(n + 1);
-  GC_CUDA(h, cudaMemcpyAsync(dims.data(), h->e.dims + (long long)circuit * (n + 1), (n + 1) * sizeof(int),
+  GC_CUDA(h, cudaMemcpyAsync(dims.data(), h->e.dims + (long long)circuit * (h->e.n + 1), (n + 1) * sizeof(int),
                              cudaMemcpyDeviceToHost, h->stream));
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int j = 0; j < n - 1; ++j) chi[j] = dims[j + 1];
@@ -896,7 +961,7 @@ int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
 int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  if (!s || !count || bond < 0 || bond >= h->e.n - 1) return fail(h, GCAMPS_EINVAL, "bad bond or null output");
+  if (!s || !count || bond < 0 || bond >= h->nq[circuit] - 1) return fail(h, GCAMPS_EINVAL, "bad bond or null output");
   if (!h->schmidt_dev) GC_CUDA(h, cudaMalloc(&h->schmidt_dev, (size_t)(h->e.d * h->e.maxdim + 64) * sizeof(double)));
   GC_CUDA(h, gcx::launch_schmidt(h->e, circuit, bond, h->schmidt_dev, h->cnt_dev, h->stream));
   int cnt = 0;
@@ -910,13 +975,12 @@ int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* c
 int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, int32_t* dims) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  const int n = h->e.n;
+  const int n = h->nq[circuit];
   if (site < 0 || site >= n || !dims) return fail(h, GCAMPS_EINVAL, "bad site or null dims");
   int dd[2];
-  GC_CUDA(h, cudaMemcpyAsync(dd, h->e.dims + (long long)circuit * (n + 1) + site, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                             h->stream));
-  long long off = 0;
-  GC_CUDA(h, cudaMemcpyAsync(&off, h->e.site_off + site, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(dd, h->e.dims + (long long)circuit * (h->e.n + 1) + site, 2 * sizeof(int),
+                             cudaMemcpyDeviceToHost, h->stream));
+  const long long off = h->mps_base[circuit] + h->site_off[(size_t)circuit * (h->e.n + 1) + site];
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
   dims[0] = dd[0];
   dims[1] = h->e.d;
@@ -924,7 +988,7 @@ int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, 
   const long long nel = (long long)dd[0] * h->e.d * dd[1];
   if (t) {
     if (cap < nel) return fail(h, GCAMPS_EINVAL, "site buffer too small");
-    GC_CUDA(h, cudaMemcpy(t, h->e.mps + (long long)circuit * h->e.mps_stride + off, (size_t)nel * sizeof(double2),
+    GC_CUDA(h, cudaMemcpy(t, h->e.mps + off, (size_t)nel * sizeof(double2),
                           cudaMemcpyDeviceToHost));
   }
   return device_status(h);
@@ -933,10 +997,11 @@ int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, 
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
-  const int n = h->e.n;
+  const int n = h->nq[circuit];
   std::vector<int8_t> w(2 * n);
   std::vector<int> meta(gcx::M_COUNT);
-  GC_CUDA(h, cudaMemcpyAsync(w.data(), h->e.weyl + (long long)circuit * 2 * n, 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(w.data(), h->e.weyl + (long long)circuit * 2 * h->e.n, 2 * n, cudaMemcpyDeviceToHost,
+                             h->stream));
   GC_CUDA(h, cudaMemcpyAsync(meta.data(), h->e.meta + (long long)circuit * gcx::M_COUNT, gcx::M_COUNT * sizeof(int),
                              cudaMemcpyDeviceToHost, h->stream));
   GC_CUDA(h, cudaStreamSynchronize(h->stream));

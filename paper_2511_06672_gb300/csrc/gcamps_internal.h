@@ -47,16 +47,19 @@ struct CtaLayout {
 };
 
 struct Engine {
-  int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;
+  int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;   // n: largest qudit count of the batch
   int score_kind;                 // 0 von Neumann, 1 Renyi-2, 2 weight rank then von Neumann
   double cutoff, tie_tol, strict_weight;
   long long tcap;                 // elements of the largest two-site matrix
   long long wcap;                 // elements of the largest Jacobi rotation matrix
+  long long scap;                 // elements of the largest scored theta' (and Gram): (d chi_max)^2
   // per-circuit state, circuit c at base + c * stride
   uint8_t* tab;     long long tab_stride;   // fwd exps | fwd phase | inv exps | inv phase
-  double2* mps;     long long mps_stride;   // site slots
-  const long long* site_off;                // [n] slot offsets (shared by all circuits)
-  const int* bond_bound;                    // [n+1] Schmidt-rank bound d^min(b, n-b) of bond b
+  const int* nq;                            // [batch] qudits of each circuit (<= n)
+  double2* mps;                             // site slots of all circuits
+  const long long* mps_base;                // [batch] offset of each circuit's slots in mps
+  const long long* site_off;                // [batch][n+1] slot offsets within the circuit's block
+  const int* bond_bound;                    // [batch][n+1] Schmidt-rank bound d^min(b, n_c-b) of bond b
   int* dims;                                // [batch][n+1]
   int* meta;                                // [batch][M_COUNT]
   long long* stats;                         // [batch][S_COUNT]

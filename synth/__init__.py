@@ -14,4 +14,5 @@ from .circuits import (  # noqa: F401
     Clifford2,
     Diag,
     param_phase_circuit,
+    batched_workload,
 )

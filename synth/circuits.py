@@ -145,3 +145,17 @@ def param_phase_circuit(n: int, d: int, layers: int, ngates: int, seed: int) -> 
             ph = (0.0, th) if d == 2 else (0.0, th, -th)
             out.append(Diag(site, ph, k))
     return out, thetas
+
+
+def batched_workload(count: int, seed0: int = 0, n_range=(16, 48), layer_range=(16, 48)):
+    """Shapes of a batch of independent circuits: circuit ``i`` uses seed ``seed0 + i`` and draws,
+    from a SplitMix64 stream seeded with ``seed0 + i`` xor a fixed tag (so that the shapes do not
+    reuse the gate stream), its qudit count ``n`` and its layer count uniformly in the given
+    inclusive ranges; it has ``t = n`` non-Clifford gates.  Returns a list of (n, layers, t, seed)."""
+    out = []
+    for i in range(count):
+        rng = SplitMix64((seed0 + i) ^ 0x5EED5EED5EED5EED)
+        n = n_range[0] + rng.uniform_int(n_range[1] - n_range[0] + 1)
+        layers = layer_range[0] + rng.uniform_int(layer_range[1] - layer_range[0] + 1)
+        out.append((n, layers, n, seed0 + i))
+    return out

@@ -368,3 +368,36 @@ def test_score_kinds_match_oracle(G, kind, d, n, layers, t, seed, chi):
         err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
         assert err < TOL
     sim.close()
+
+
+def test_uneven_batch_matches_oracle_per_circuit(G):
+    """One handle with circuits of different qudit counts (the batched form): each circuit's
+    tableau, decisions, bond dimensions and state equal the oracle's run of that circuit alone, and
+    a smaller cluster size set after creation gives the same results."""
+    d = 3
+    ns = [5, 8, 6, 7, 4]
+    gates = [brickwork_circuit(n, d, n, n, 100 + n) for n in ns]
+    ops, begin = [], [0]
+    for n, g in zip(ns, gates):
+        o = G.ops_from_gates(g, d)
+        ops.append(o)
+        begin.append(begin[-1] + len(o))
+    sim = G.Simulator(ns, d, chi_max=81, cutoff=1e-12, cluster_size=4)
+    assert sim.batch == len(ns) and [sim._lib.gcamps_num_qudits(sim._h, c) for c in range(len(ns))] == ns
+    for csize in (4, 2):
+        sim.set_cluster_size(csize)
+        sim.reset()
+        sim.run(np.concatenate(ops), begin)
+        sim.sync()
+        for c, (n, g) in enumerate(zip(ns, gates)):
+            ref = oracle_run(g, n, d, 81, 1e-12)
+            e, p = sim.tableau(c)
+            re_, rp = ref.tab.exps_phase()
+            assert np.array_equal(e, re_) and np.array_equal(p, rp)
+            assert sim.decisions(c) == ref.decisions
+            assert sim.bond_dims(c) == ref.mps.bond_dims()
+            err, _ = sv.same_up_to_phase(sim.statevector(c), sv.run(g, n, d))
+            assert err < TOL
+    with pytest.raises(G.GcampsError):
+        sim.set_cluster_size(8)          # above the size the scratch was laid out for
+    sim.close()
