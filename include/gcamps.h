@@ -45,6 +45,7 @@ extern "C" {
 #define GCAMPS_ENOCONV 4 /* a device iteration (Jacobi SVD, eigenvalues) hit its cap  */
 #define GCAMPS_ECHI 5    /* chi_max bound while discarding weight above strict_weight */
 #define GCAMPS_ESIZE 6   /* a size beyond the fixed maximum of gcamps_score_theta_noalloc */
+#define GCAMPS_ESNAP 7   /* the adjoint snapshot arena (opts.snapshot_entries) is full      */
 
 typedef struct gcamps gcamps_t;
 
@@ -62,6 +63,10 @@ typedef struct {
   double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
   int cluster_size;    /* CTAs (one thread-block cluster) per circuit: 1, 2, 4, 8 or 16; 0 = 8   */
+  int64_t snapshot_entries;   /* per circuit: complex entries of the arena that keeps the MPS  */
+                              /* after every non-Clifford gate for gcamps_expect_gradient    */
+                              /* (0 = no snapshots, no gradients; default 0)                 */
+  int32_t snapshot_max_gates; /* per circuit: most non-Clifford gates kept (0 with the above) */
 } gcamps_opts;
 
 /* Per-circuit counters since creation (or gcamps_reset). */
@@ -175,6 +180,22 @@ int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begi
  * the real part.  circuit selects the batch entry. */
 int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z,
                        double* re, double* im);
+
+/* Phase gradient of O = Re <psi| W |psi> = <psi| (W + W^dag)/2 |psi>, W = (x)_j X_j^{x_j} Z_j^{z_j},
+ * with respect to the phases of every non-Clifford gate k applied since the last reset
+ * (gate k = diag(exp(i phi_{k,j})), j = 0..d-1; Sec. 2.3.2 writes the T gate through R_Z(theta), so
+ * theta-parametrised gates get d/dtheta by the chain rule).  Adjoint method through the MPO
+ * applications (Sec. 3): the handle must be created with snapshots (opts.snapshot_entries,
+ * snapshot_max_gates); the state after each gate's MPO is kept on the device, and the backward pass
+ * runs in the forward run's own Clifford frames (undoing each disentangler, applying the inverse
+ * gate's MPO), so it is exact when no truncation discards weight.  value: O; grad: d doubles per gate
+ * (gate-major), at most cap_gates gates copied; *ngates: gates recorded.  Synchronising; uses a
+ * workspace circuit slot, so one gradient at a time per handle.  GCAMPS_ESNAP if the arena was full;
+ * GCAMPS_ECHI if chi_max made the backward pass discard weight (the backward state carries the
+ * observable evolved back through the later gates and can need a larger bond dimension than the
+ * forward state; the gradient would not be exact). */
+int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* value,
+                           double* grad, int32_t cap_gates, int32_t* ngates);
 
 /* Dense C|MPS> (d^n amplitudes, d^n <= 2^20) up to one global phase (a Clifford given by its
  * images has no defined phase): C|y> = prod_j D_j^{y_j} C|0>, with C|0> the common +1

@@ -15,7 +15,7 @@ from . import _native as N
 from ._native import OP_DTYPE, OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE
 
 __all__ = ["Simulator", "GcampsError", "sp4_images", "num_candidates", "candidate", "ops_from_gates",
-           "score_theta_noalloc",
+           "score_theta_noalloc", "weyl_expectation",
            "OP_DTYPE", "OP_CLIFFORD", "OP_NONCLIFFORD", "OP_DISENTANGLE"]
 
 
@@ -121,13 +121,15 @@ class Simulator:
 
     def __init__(self, n, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
                  tie_tol: float = 1e-10, batch: int = 1, stream=None, strict_weight: float = 0.0,
-                 cluster_size: int = 8, score_kind: int = 0):
+                 cluster_size: int = 8, score_kind: int = 0, snapshot_entries: int = 0,
+                 snapshot_max_gates: int = 0):
         self._lib = N.load()
         o = N.Opts()
         self._lib.gcamps_default_opts(C.byref(o))
         o.cutoff, o.max_sweeps, o.tie_tol, o.strict_weight = cutoff, max_sweeps, tie_tol, strict_weight
         o.cluster_size = cluster_size
         o.score_kind = score_kind
+        o.snapshot_entries, o.snapshot_max_gates = snapshot_entries, snapshot_max_gates
         s = _stream_handle(stream)
         o.cuda_stream = C.c_void_p(s) if s else None
         h = C.c_void_p()
@@ -146,6 +148,7 @@ class Simulator:
         self.nq = nq
         self.n = max(nq)
         self.d, self.chi_max, self.batch = d, chi_max, batch
+        self._snap_max = snapshot_max_gates
 
     def set_cluster_size(self, cluster_size: int):
         self._c(self._lib.gcamps_set_cluster_size(self._h, cluster_size))
@@ -209,6 +212,18 @@ class Simulator:
         self._c(self._lib.gcamps_expect_weyl(self._h, circuit, N.ptr(xa, C.c_int32), N.ptr(za, C.c_int32),
                                              C.byref(re), C.byref(im)))
         return complex(re.value, im.value)
+
+    def expect_gradient(self, x, z, circuit: int = 0):
+        """(Re<W>, gradient [gates, d]) with respect to the phases of every non-Clifford gate since the
+        last reset (adjoint pass of the library; needs a handle with snapshots)."""
+        xa = np.ascontiguousarray(x, dtype=np.int32)
+        za = np.ascontiguousarray(z, dtype=np.int32)
+        cap = max(1, self._snap_max)
+        g = np.zeros(cap * self.d)
+        val, ng = C.c_double(), C.c_int32()
+        self._c(self._lib.gcamps_expect_gradient(self._h, circuit, N.ptr(xa, C.c_int32), N.ptr(za, C.c_int32),
+                                                 C.byref(val), N.ptr(g, C.c_double), cap, C.byref(ng)))
+        return val.value, g[: ng.value * self.d].reshape(ng.value, self.d).copy()
 
     def statevector(self, circuit: int = 0) -> np.ndarray:
         dim = self.d ** self.nq[circuit]
@@ -305,3 +320,48 @@ class Simulator:
         a = np.zeros(2 * max(cnt.value, 1), dtype=np.int32)
         self._c(self._lib.gcamps_get_decisions(self._h, circuit, N.ptr(a, C.c_int32), cnt.value, C.byref(cnt)))
         return [(int(a[2 * i]), int(a[2 * i + 1])) for i in range(min(cnt.value, len(a) // 2))]
+
+
+def weyl_expectation(phases, sim: "Simulator", gates, x, z, circuit: int = 0):
+    """Re<W> of a parametrised circuit as a differentiable torch function of the phases of its
+    non-Clifford gates.
+
+    phases: tensor [gates, d] (row k = phases of the k-th diagonal gate of ``gates``, in order; the
+    other fields of those gates are kept); gates: synth gate list; sim: a Simulator with snapshots
+    (one circuit is run, ``circuit``).  The forward runs the circuit through the library and the
+    backward returns the library's adjoint gradient (gcamps_expect_gradient).  Binding only: both
+    directions run in the library's kernels."""
+    import torch
+
+    class _Expect(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, ph):
+            import dataclasses
+            p = ph.detach().cpu().numpy().astype(np.float64)
+            k = 0
+            gl = []
+            for g in gates:
+                if hasattr(g, "sp_index"):
+                    gl.append(g)
+                else:
+                    gl.append(dataclasses.replace(g, phases=tuple(float(v) for v in p[k])))
+                    k += 1
+            sim.reset()
+            ops = ops_from_gates(gl, sim.d)
+            if sim.batch > 1:
+                begin = [0] * (sim.batch + 1)
+                for c in range(circuit + 1, sim.batch + 1):
+                    begin[c] = len(ops)
+                sim.run(ops, begin)
+            else:
+                sim.run(ops)
+            val, grad = sim.expect_gradient(x, z, circuit)
+            ctx.save_for_backward(torch.as_tensor(grad, dtype=ph.dtype, device=ph.device))
+            return torch.as_tensor(val, dtype=ph.dtype, device=ph.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad
+
+    return _Expect.apply(phases)

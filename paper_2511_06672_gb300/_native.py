@@ -8,7 +8,7 @@ import numpy as np
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libgcamps.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE, ESNAP = 0, 1, 2, 3, 4, 5, 6, 7
 NOALLOC_MAX_SIDE = 81
 OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE = 1, 2, 3
 
@@ -20,7 +20,8 @@ assert OP_DTYPE.itemsize == 128
 class Opts(C.Structure):
     _fields_ = [("cutoff", C.c_double), ("max_sweeps", C.c_int), ("score_kind", C.c_int),
                 ("precision", C.c_int), ("tie_tol", C.c_double), ("strict_weight", C.c_double),
-                ("cuda_stream", C.c_void_p), ("cluster_size", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("cluster_size", C.c_int),
+                ("snapshot_entries", C.c_int64), ("snapshot_max_gates", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -41,7 +42,7 @@ EXPORTS = [
     "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_destroy", "gcamps_num_qudits",
     "gcamps_set_cluster_size", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
-    "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
+    "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
     "gcamps_get_stats",
     "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         "gcamps_run": (C.c_int, [vp, vp, C.c_int, i32p]),
         "gcamps_run_device": (C.c_int, [vp, vp, vp]),
         "gcamps_expect_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, dp, dp]),
+        "gcamps_expect_gradient": (C.c_int, [vp, C.c_int, i32p, i32p, dp, dp, C.c_int32, i32p]),
         "gcamps_statevector": (C.c_int, [vp, C.c_int, dp, dp]),
         "gcamps_amplitude": (C.c_int, [vp, C.c_int, i32p, dp, dp]),
         "gcamps_get_tableau": (C.c_int, [vp, C.c_int, u8p, u8p]),

@@ -835,13 +835,14 @@ __device__ void move_center(Smem& s, const Ctx& C, int target) {
 }
 
 // ------------------------------------------------- non-Clifford step (Sec. 2.3.1, Sec. 2.4, Sec. 3)
-// P = C^dag Z_site C is row `site` of the inverse tableau; diag(t) = sum_m c_m Z^m with
-// c_m = (1/d) sum_j t_j omega^{-mj}; C^dag diag(t) C = sum_m c_m P^m is applied as an MPO of bond
-// dimension d that is diagonal in m.  (X^a Z^b)_{s s'} = omega^{b s'} delta_{s, s'+a}, so each
-// MPO tensor is a gather with phases.
-__device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double* phases) {
+// sum_m c_m P^m for a Weyl string P = tau^r (x)_j X_j^{x_j} Z_j^{z_j} (row: x in [0, n), z in [n, 2n))
+// and base coefficients c_m in s.coef[0..d), applied to the circuit's MPS as an MPO of bond dimension
+// d that is diagonal in m, over the support span [f, l] of P, then [f, l] recompressed (Sec. 2.4).
+// (X^a Z^b)_{s s'} = omega^{b s'} delta_{s, s'+a}, so each MPO tensor is a gather with phases.
+// record: this is the circuit's non-Clifford step (span, string and counters are kept); the adjoint
+// passes false.  The identity string (f > l) sets EINVAL.
+__device__ void mpo_apply(Smem& s, const Ctx& C, const uint8_t* row, int r, bool record) {
   const int n = C.n, d = C.d;
-  const uint8_t* row = C.ix + (long long)site * 2 * n;
   // support span and sum_j x_j z_j
   if (threadIdx.x == 0) {
     s.ival[0] = n;
@@ -851,8 +852,10 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const int x = row[j], z = row[n + j];
-    C.weyl[j] = (int8_t)x;
-    C.weyl[n + j] = (int8_t)z;
+    if (record) {
+      C.weyl[j] = (int8_t)x;
+      C.weyl[n + j] = (int8_t)z;
+    }
     if (x | z) {
       atomicMin(&s.ival[0], j);
       atomicMax(&s.ival[1], j);
@@ -862,7 +865,6 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
   __syncthreads();
   const int f = s.ival[0], l = s.ival[1];
   const int sxz = s.ival[2] % d;
-  const int r = C.ir[site];
   __syncthreads();
   if (f > l) {  // a row of a valid tableau is never the identity
     if (threadIdx.x == 0) set_status(C, GCAMPS_EINVAL);
@@ -870,23 +872,17 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
     return;
   }
   if (threadIdx.x == 0) {
-    C.meta[M_WEYL_R] = r;
-    C.meta[M_F] = f;
-    C.meta[M_L] = l;
-    C.meta[M_HAVE_SPAN] = 1;
-    C.stats[S_T] += 1;
-    // coefficients of the d MPO terms, including the phase of P^m:
-    // (tau^r W)^m = tau^{r m} omega^{sxz m(m-1)/2} W(m x, m z)
+    if (record) {
+      C.meta[M_WEYL_R] = r;
+      C.meta[M_F] = f;
+      C.meta[M_L] = l;
+      C.meta[M_HAVE_SPAN] = 1;
+      C.stats[S_T] += 1;
+    }
+    // the phase of P^m: (tau^r W)^m = tau^{r m} omega^{sxz m(m-1)/2} W(m x, m z)
     for (int m = 0; m < d; ++m) {
-      double re = 0, im = 0;
-      for (int j = 0; j < d; ++j) {
-        double sn, cs;
-        sincos(phases[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
-        re += cs;
-        im += sn;
-      }
       const int ph = (r * m + 2 * sxz * (m * (m - 1) / 2)) % (2 * d);
-      s.coef[m] = cmul(make_double2(re / d, im / d), s.tau[ph]);
+      s.coef[m] = cmul(s.coef[m], s.tau[ph]);
     }
   }
   __syncthreads();
@@ -957,6 +953,67 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
     }
   }
   __syncthreads();
+}
+
+// Snapshot of the MPS right after non-Clifford gate k (for the adjoint): the site tensors packed in the
+// circuit's arena, and a header with the arena offset, the gate's site, the string's phase r, the
+// first decision index of the disentangling that follows, the bond dimensions and the string.
+__device__ void take_snapshot(Smem& s, const Ctx& C, int site, const double* phases) {
+  const Engine& e = *C.e;
+  const int n = C.n, d = C.d;
+  const int k = C.meta[M_NSNAP];
+  long long need = 0;
+  for (int j = 0; j < n; ++j) need += (long long)C.dims[j] * d * C.dims[j + 1];
+  const long long off = C.meta[M_SNAPOFF];
+  __syncthreads();
+  if (k >= e.snap_max || off + need > e.snap_stride) {
+    if (threadIdx.x == 0) set_status(C, GCAMPS_ESNAP);
+    __syncthreads();
+    return;
+  }
+  int* hd = e.snap_hdr + ((long long)C.c * e.snap_max + k) * kSnapHdr;
+  double2* dst = e.snap + (long long)C.c * e.snap_stride + off;
+  long long pos = 0;
+  for (int j = 0; j < n; ++j) {
+    const long long nel = (long long)C.dims[j] * d * C.dims[j + 1];
+    block_copy(dst + pos, site_ptr(C, j), nel);
+    pos += nel;
+  }
+  const uint8_t* row = C.ix + (long long)site * 2 * n;
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) hd[kSnapDims + j] = C.dims[j];
+  for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) hd[kSnapDims + kMaxN + 1 + j] = row[j];
+  if (threadIdx.x == 0) {
+    hd[0] = (int)off;
+    hd[1] = site;
+    hd[2] = C.ir[site];
+    hd[3] = C.meta[M_NDEC];
+    double* ph = e.snap_ph + ((long long)C.c * e.snap_max + k) * 4;
+    for (int j = 0; j < d; ++j) ph[j] = phases[j];
+    C.meta[M_NSNAP] = k + 1;
+    C.meta[M_SNAPOFF] = (int)(off + need);
+  }
+  __syncthreads();
+}
+
+// Diagonal non-Clifford gate diag(e^{i phases[j]}) on `site`: P = C^dag Z_site C is row `site` of the
+// inverse tableau; diag(t) = sum_m c_m Z^m with c_m = (1/d) sum_j t_j omega^{-mj}; C^dag diag(t) C =
+// sum_m c_m P^m goes through mpo_apply.
+__device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double* phases) {
+  const int n = C.n, d = C.d;
+  if (threadIdx.x == 0)
+    for (int m = 0; m < d; ++m) {
+      double re = 0, im = 0;
+      for (int j = 0; j < d; ++j) {
+        double sn, cs;
+        sincos(phases[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
+        re += cs;
+        im += sn;
+      }
+      s.coef[m] = make_double2(re / d, im / d);
+    }
+  __syncthreads();
+  mpo_apply(s, C, C.ix + (long long)site * 2 * n, C.ir[site], true);
+  if (C.e->snap && C.meta[M_STATUS] == 0) take_snapshot(s, C, site, phases);
 }
 
 // --------------------------------------------------------------- candidate scoring (Sec. 3)
@@ -1805,6 +1862,185 @@ __global__ void __launch_bounds__(kThreads) k_score_theta(Engine e, const double
   cluster_sync();
 }
 
+__device__ void conj_weyl(Smem& s, const Ctx& C, const int8_t* xz, int* acc_x, int* acc_z, int* acc_r);
+
+// ---------------------------------------------------------------- adjoint phase gradient
+// <B| W(m a, m b) |M> for two MPS on the same n sites, W(a, b) = (x)_j X_j^{a_j} Z_j^{b_j} (no phase):
+// B's sites through site_ptr(CB, j) and CB.dims, M packed at mbase with bond dimensions mdims and
+// site offsets moff.  Transfer matrices E[a, a'] left to right, scratch in CB.
+__device__ double2 overlap_weyl(Smem& s, const Ctx& CB, const double2* mbase, const int* mdims,
+                                const long long* moff, const uint8_t* row, int mp) {
+  const Engine& e = *CB.e;
+  const int n = CB.n, d = CB.d;
+  double2* E = CB.scr + e.sl.b;
+  double2* T = CB.scr + e.sl.tmp;
+  double2* E2 = CB.scr + e.sl.u;
+  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int bl = CB.dims[j], br = CB.dims[j + 1], ml = mdims[j], mr = mdims[j + 1];
+    const double2* A = site_ptr(CB, j);
+    const double2* M = mbase + moff[j];
+    const int ax = (mp * row[j]) % d, bz = (mp * row[n + j]) % d;
+    // T[a, s, b'] = sum_{a'} E[a, a'] omega^{bz (s - ax)} M[a', s - ax, b']
+    for (long long idx = threadIdx.x; idx < (long long)bl * d * mr; idx += blockDim.x) {
+      const int bp = (int)(idx % mr), sd = (int)((idx / mr) % d), a = (int)(idx / ((long long)mr * d));
+      const int sp = (sd - ax + d) % d;
+      double2 acc = cz();
+      for (int ap = 0; ap < ml; ++ap) acc = cfma(E[(long long)a * ml + ap], M[((long long)ap * d + sp) * mr + bp], acc);
+      T[idx] = cmul(s.tau[(2 * bz * sp) % (2 * d)], acc);
+    }
+    __syncthreads();
+    // E'[b, b'] = sum_{a, s} conj(A[a, s, b]) T[a, s, b']
+    for (long long idx = threadIdx.x; idx < (long long)br * mr; idx += blockDim.x) {
+      const int b = (int)(idx / mr), bp = (int)(idx % mr);
+      double2 acc = cz();
+      for (int a = 0; a < bl; ++a)
+        for (int sd = 0; sd < d; ++sd)
+          acc = cfmac(A[((long long)a * d + sd) * br + b], T[((long long)a * d + sd) * mr + bp], acc);
+      E2[idx] = acc;
+    }
+    __syncthreads();
+    block_copy(E, E2, (long long)br * mr);
+    __syncthreads();
+  }
+  const double2 v = E[0];
+  __syncthreads();
+  return v;
+}
+
+// theta <- Q_q^dag theta on sites (i, i+1) of CB's MPS (undoing an applied disentangler), split by SVD
+// with the centre left at i + 1.
+__device__ void undo_disentangler(Smem& s, const Ctx& CB, int i, int q) {
+  const Engine& e = *CB.e;
+  const int d = CB.d, dd = d * d;
+  move_center(s, CB, i);
+  const int cl = CB.dims[i], ch = CB.dims[i + 1], cr = CB.dims[i + 2];
+  double2* theta = CB.scr + e.sl.theta;
+  double2* tmp = CB.scr + e.sl.tmp;
+  block_matmul(theta, site_ptr(CB, i), site_ptr(CB, i + 1), cl * d, ch, d * cr);
+  __syncthreads();
+  const double2* Q = e.candU + (long long)q * dd * dd;
+  const long long total = (long long)cl * dd * cr;
+  for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int b = (int)(idx % cr), u = (int)((idx / cr) % dd);
+    const long long a = idx / ((long long)cr * dd);
+    double2 acc = cz();
+    for (int v = 0; v < dd; ++v) acc = cfmac(Q[v * dd + u], theta[(a * dd + v) * cr + b], acc);   // conj(Q[v][u])
+    tmp[idx] = acc;
+  }
+  __syncthreads();
+  block_copy(theta, tmp, total);
+  __syncthreads();
+  const int bb = CB.bond_bound[i + 1];
+  Factor F = svd_factor(s, CB, theta, cl * d, d * cr, e.chi_max < bb ? e.chi_max : bb, false);
+  const int k = F.k;
+  for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
+    F.Vh[idx] = cscale(F.Vh[idx], CB.sing[idx / (d * cr)]);
+  __syncthreads();
+  block_copy(site_ptr(CB, i), F.U, (long long)cl * d * k);
+  block_copy(site_ptr(CB, i + 1), F.Vh, (long long)k * d * cr);
+  if (threadIdx.x == 0) {
+    CB.dims[i + 1] = k;
+    CB.meta[M_OC] = i + 1;
+  }
+  __syncthreads();
+}
+
+// d Re<W> / d phi_{k,j} for every recorded non-Clifford gate k of circuit cf (gate k =
+// diag(e^{i phi_{k,j}})), by the adjoint method in the forward run's own Clifford frames:
+//   lambda_K = O psi with O = (W + W^dag)/2 = C (P + P^dag)/2 C^dag, P = C^dag W C (final frame);
+//   for k = K-1 .. 0: undo the disentanglers applied after gate k (Q^dag, reverse order), which puts
+//   lambda in the frame C'_k of gate k's MPO; take g_{k,j} = -2 Im <lambda| Pi_j |phi_k> with
+//   phi_k = snapshot k and Pi_j = (1/d) sum_m omega^{-mj} P_k^m (P_k = gate k's string); apply
+//   D_k^dag = sum_m c_m(-phi) P_k^m.  Cliffords between gates only change the frame.
+// Circuit slot cb holds lambda (its first n sites).  grad: d doubles per gate.
+__global__ void __launch_bounds__(kThreads) k_adjoint(Engine e, int cf, int cb, const int8_t* xz, double* grad) {
+  __shared__ Smem s;
+  __shared__ int ax[kMaxN], az[kMaxN], ar;
+  __shared__ uint8_t row[2 * kMaxN];
+  __shared__ long long moff[kMaxN + 1];
+  Ctx F = make_ctx(e, cf);
+  Ctx B = make_ctx(e, cb);
+  const int n = F.n, d = e.d;
+  B.n = n;   // the workspace slot has room for n_max >= n sites
+  init_tau(s, d);
+  for (int j = 0; j < n; ++j) block_copy(site_ptr(B, j), site_ptr(F, j), (long long)F.dims[j] * d * F.dims[j + 1]);
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) B.dims[j] = F.dims[j];
+  if (threadIdx.x < M_COUNT) B.meta[threadIdx.x] = 0;
+  if (threadIdx.x < 4) B.dstats[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) B.meta[M_OC] = F.meta[M_OC];
+  conj_weyl(s, F, xz, ax, az, &ar);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    row[j] = (uint8_t)ax[j];
+    row[n + j] = (uint8_t)az[j];
+  }
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < d; ++m) s.coef[m] = cz();
+    s.coef[1].x += 0.5;
+    s.coef[d - 1].x += 0.5;   // P^(d-1) = P^dag
+  }
+  __syncthreads();
+  bool has_w = false;
+  for (int j = 0; j < n; ++j) has_w |= (row[j] | row[n + j]) != 0;
+  if (has_w) mpo_apply(s, B, row, ar, false);
+  const int K = F.meta[M_NSNAP];
+  const int ndec = F.meta[M_NDEC];
+  for (int k = K - 1; k >= 0 && B.meta[M_STATUS] == 0; --k) {
+    const int* hd = e.snap_hdr + ((long long)cf * e.snap_max + k) * kSnapHdr;
+    const int dec0 = hd[3];
+    const int dec1 = k + 1 < K ? hd[kSnapHdr + 3] : ndec;
+    if (dec1 > kDecCap) {
+      if (threadIdx.x == 0) set_status(B, GCAMPS_EINVAL);
+      __syncthreads();
+      break;
+    }
+    for (int idx = dec1 - 1; idx >= dec0; --idx) {
+      const int bond = F.dec[2 * idx], q = F.dec[2 * idx + 1];
+      if (q) undo_disentangler(s, B, bond, q);
+    }
+    // gate k's string, phase and snapshot
+    for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) row[j] = (uint8_t)hd[kSnapDims + kMaxN + 1 + j];
+    if (threadIdx.x == 0) {
+      long long o = 0;
+      for (int j = 0; j < n; ++j) {
+        moff[j] = o;
+        o += (long long)hd[kSnapDims + j] * d * hd[kSnapDims + j + 1];
+      }
+      int sxz = 0;
+      for (int j = 0; j < n; ++j) sxz += row[j] * row[n + j];
+      s.ival[6] = sxz % d;
+    }
+    __syncthreads();
+    const int rk = hd[2], sxz = s.ival[6];
+    const double2* mbase = e.snap + (long long)cf * e.snap_stride + hd[0];
+    double2 proj[3] = {cz(), cz(), cz()};
+    for (int m = 0; m < d; ++m) {
+      const double2 ov = overlap_weyl(s, B, mbase, hd + kSnapDims, moff, row, m);
+      const double2 pm = cmul(s.tau[(rk * m + 2 * sxz * (m * (m - 1) / 2)) % (2 * d)], ov);   // <B|P^m|M>
+      for (int j = 0; j < d; ++j) proj[j] = cadd(proj[j], cscale(cmul(s.tau[(2 * d - (2 * m * j) % (2 * d)) % (2 * d)], pm), 1.0 / d));
+    }
+    if (threadIdx.x == 0)
+      for (int j = 0; j < d; ++j) grad[(long long)k * d + j] = -2.0 * proj[j].y;
+    // D_k^dag = sum_m c_m(-phi) P_k^m
+    const double* ph = e.snap_ph + ((long long)cf * e.snap_max + k) * 4;
+    if (threadIdx.x == 0)
+      for (int m = 0; m < d; ++m) {
+        double re = 0, im = 0;
+        for (int j = 0; j < d; ++j) {
+          double sn, cs;
+          sincos(-ph[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
+          re += cs;
+          im += sn;
+        }
+        s.coef[m] = make_double2(re / d, im / d);
+      }
+    __syncthreads();
+    mpo_apply(s, B, row, rk, false);
+  }
+}
+
 // |0...0> with C = I, counters cleared.
 __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
   Ctx C = make_ctx(e, blockIdx.x);
@@ -1834,15 +2070,13 @@ __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
 // ------------------------------------------------------------------------------ readouts
 // <MPS| P' |MPS> with P' = C^dag W C = tau^r (x)_j X^{a_j} Z^{b_j}: the inverse-tableau rows are
 // multiplied in the order of W = prod_j X_j^{x_j} Z_j^{z_j}, then transfer matrices left to right.
-__global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8_t* xz, double2* out) {
-  __shared__ Smem s;
-  __shared__ int acc_x[kMaxN], acc_z[kMaxN];
-  __shared__ int acc_r;
-  Ctx C = make_ctx(e, c);
-  init_tau(s, e.d);
-  const int n = C.n, d = e.d;
+// P' = C^dag W C for W = (x)_j X_j^{x_j} Z_j^{z_j} (xz = x | z): the inverse-tableau rows multiplied in
+// the order of W with the Weyl product rule; exponents into acc_x, acc_z and the phase (units of tau)
+// into *acc_r, all in shared memory.
+__device__ void conj_weyl(Smem& s, const Ctx& C, const int8_t* xz, int* acc_x, int* acc_z, int* acc_r) {
+  const int n = C.n, d = C.d;
   for (int j = threadIdx.x; j < n; j += blockDim.x) acc_x[j] = acc_z[j] = 0;
-  if (threadIdx.x == 0) acc_r = 0;
+  if (threadIdx.x == 0) *acc_r = 0;
   __syncthreads();
   for (int q = 0; q < n; ++q) {
     for (int kind = 0; kind < 2; ++kind) {
@@ -1858,11 +2092,21 @@ __global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8
           acc_x[j] = (acc_x[j] + R[j]) % d;
           acc_z[j] = (acc_z[j] + R[n + j]) % d;
         }
-        if (threadIdx.x == 0) acc_r = (acc_r + C.ir[rowi] + 2 * tot) % (2 * d);
+        if (threadIdx.x == 0) *acc_r = (*acc_r + C.ir[rowi] + 2 * tot) % (2 * d);
         __syncthreads();
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8_t* xz, double2* out) {
+  __shared__ Smem s;
+  __shared__ int acc_x[kMaxN], acc_z[kMaxN];
+  __shared__ int acc_r;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  const int n = C.n, d = e.d;
+  conj_weyl(s, C, xz, acc_x, acc_z, &acc_r);
   // transfer matrices: E (chi x chi) starts as [[1]]
   double2* E = C.scr + e.sl.b;
   double2* T = C.scr + e.sl.tmp;
@@ -2125,6 +2369,11 @@ cudaError_t launch_reset(const Engine& e, cudaStream_t st) {
 
 cudaError_t launch_expect(const Engine& e, int circuit, const int8_t* xz_dev, double2* out_dev, cudaStream_t st) {
   k_expect<<<1, kThreads, 0, st>>>(e, circuit, xz_dev, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const Engine& e, int cf, int cb, const int8_t* xz_dev, double* grad_dev, cudaStream_t st) {
+  k_adjoint<<<1, kThreads, 0, st>>>(e, cf, cb, xz_dev, grad_dev);
   return cudaGetLastError();
 }
 

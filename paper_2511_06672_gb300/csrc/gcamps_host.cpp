@@ -351,6 +351,7 @@ struct gcamps {
   std::vector<long long> mps_base;     // [batch] offset of each circuit's block
   int nmin = 0;                        // smallest qudit count of the batch
   int csize_alloc = 0;                 // cluster size the per-CTA scratch was laid out for
+  double* grad_dev = nullptr;          // adjoint output (snapshot_max_gates x 4 doubles)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
@@ -426,6 +427,8 @@ void gcamps_default_opts(gcamps_opts* o) {
   o->strict_weight = 0.0;
   o->cuda_stream = nullptr;
   o->cluster_size = 8;
+  o->snapshot_entries = 0;
+  o->snapshot_max_gates = 0;
 }
 
 int gcamps_num_candidates(int d) {
@@ -485,7 +488,8 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   gcamps_default_opts(&opts);
   if (o) opts = *o;
   if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind < 0 || opts.score_kind > 2 ||
-      opts.precision != 0 ||
+      opts.precision != 0 || opts.snapshot_entries < 0 || opts.snapshot_max_gates < 0 ||
+      (opts.snapshot_entries > 0) != (opts.snapshot_max_gates > 0) || opts.snapshot_entries > (1LL << 31) - 1 ||
       !(opts.tie_tol >= 0.0))
     return GCAMPS_EINVAL;
   if (opts.cluster_size == 0) opts.cluster_size = 8;
@@ -508,14 +512,18 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.strict_weight = opts.strict_weight;
   // bond capacities of each circuit: after the MPO a bond holds at most d * min(chi_max, Schmidt
   // bound); slots of each circuit's sites laid out back to back, circuits one after another
+  // with adjoint snapshots one more circuit slot (index batch, n_max qudits) holds the backward state
+  const bool snap = opts.snapshot_entries > 0;
+  const int nslots = batch + (snap ? 1 : 0);
   h->nq.assign(nqs, nqs + batch);
+  if (snap) h->nq.push_back(n);
   h->nmin = *std::min_element(nqs, nqs + batch);
-  h->site_off.assign((size_t)batch * (n + 1), 0);
-  h->mps_base.assign((size_t)batch, 0);
-  std::vector<int> bound((size_t)batch * (n + 1), 1);
+  h->site_off.assign((size_t)nslots * (n + 1), 0);
+  h->mps_base.assign((size_t)nslots, 0);
+  std::vector<int> bound((size_t)nslots * (n + 1), 1);
   long long maxdim = 1, tcap = 1, mps_total = 0;
-  for (int c = 0; c < batch; ++c) {
-    const int nc = nqs[c];
+  for (int c = 0; c < nslots; ++c) {
+    const int nc = h->nq[c];
     std::vector<long long> cap(nc + 1, 1);
     for (int b = 1; b < nc; ++b) {
       const long long sb = sat_pow(d, std::min(b, nc - b), 1LL << 30);
@@ -564,39 +572,39 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   const size_t o_tab = bytes;
-  bytes = align(bytes + (size_t)batch * e.tab_stride);
+  bytes = align(bytes + (size_t)nslots * e.tab_stride);
   const size_t o_mps = bytes;
   bytes = align(bytes + (size_t)mps_total * sizeof(double2));
   const size_t o_off = bytes;
-  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(long long));
+  bytes = align(bytes + (size_t)nslots * (n + 1) * sizeof(long long));
   const size_t o_bound = bytes;
-  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * (n + 1) * sizeof(int));
   const size_t o_nq = bytes;
-  bytes = align(bytes + (size_t)batch * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * sizeof(int));
   const size_t o_base = bytes;
-  bytes = align(bytes + (size_t)batch * sizeof(long long));
+  bytes = align(bytes + (size_t)nslots * sizeof(long long));
   const size_t o_dims = bytes;
-  bytes = align(bytes + (size_t)batch * (n + 1) * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * (n + 1) * sizeof(int));
   const size_t o_meta = bytes;
-  bytes = align(bytes + (size_t)batch * gcx::M_COUNT * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * gcx::M_COUNT * sizeof(int));
   const size_t o_stats = bytes;
-  bytes = align(bytes + (size_t)batch * gcx::S_COUNT * sizeof(long long));
+  bytes = align(bytes + (size_t)nslots * gcx::S_COUNT * sizeof(long long));
   const size_t o_dstats = bytes;
-  bytes = align(bytes + (size_t)batch * 4 * sizeof(double));
+  bytes = align(bytes + (size_t)nslots * 4 * sizeof(double));
   const size_t o_dec = bytes;
-  bytes = align(bytes + (size_t)batch * gcx::kDecCap * 2 * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * gcx::kDecCap * 2 * sizeof(int));
   const size_t o_weyl = bytes;
-  bytes = align(bytes + (size_t)batch * 2 * n);
+  bytes = align(bytes + (size_t)nslots * 2 * n);
   const size_t o_last = bytes;
-  bytes = align(bytes + (size_t)batch * (3 * gcx::kMaxK + 2 + 2 * gcx::kSmall) * sizeof(double));
+  bytes = align(bytes + (size_t)nslots * (3 * gcx::kMaxK + 2 + 2 * gcx::kSmall) * sizeof(double));
   const size_t o_scr = bytes;
-  bytes = align(bytes + (size_t)batch * sl.total * sizeof(double2));
+  bytes = align(bytes + (size_t)nslots * sl.total * sizeof(double2));
   const size_t o_cscr = bytes;
-  bytes = align(bytes + (size_t)batch * e.csize * cly.total * sizeof(double2));
+  bytes = align(bytes + (size_t)nslots * e.csize * cly.total * sizeof(double2));
   const size_t o_sing = bytes;
-  bytes = align(bytes + (size_t)batch * e.sing_stride * sizeof(double));
+  bytes = align(bytes + (size_t)nslots * e.sing_stride * sizeof(double));
   const size_t o_iscr = bytes;
-  bytes = align(bytes + (size_t)batch * e.iscr_stride * sizeof(int));
+  bytes = align(bytes + (size_t)nslots * e.iscr_stride * sizeof(int));
   const size_t o_candU = bytes;
   const int D = d * d;
   bytes = align(bytes + (size_t)e.K * D * D * sizeof(double2));
@@ -604,6 +612,14 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   bytes = align(bytes + (size_t)e.K * D * D * sizeof(float2));
   const size_t o_candI = bytes;
   bytes = align(bytes + (size_t)e.K * 20 * sizeof(int32_t));
+  const size_t o_snap = bytes;
+  if (snap) bytes = align(bytes + (size_t)batch * opts.snapshot_entries * sizeof(double2));
+  const size_t o_shdr = bytes;
+  if (snap) bytes = align(bytes + (size_t)batch * opts.snapshot_max_gates * gcx::kSnapHdr * sizeof(int));
+  const size_t o_sph = bytes;
+  if (snap) bytes = align(bytes + (size_t)batch * opts.snapshot_max_gates * 4 * sizeof(double));
+  const size_t o_grad = bytes;
+  if (snap) bytes = align(bytes + (size_t)opts.snapshot_max_gates * 4 * sizeof(double));
   const size_t o_aux = bytes;
   bytes = align(bytes + (size_t)(gcx::kMaxN * 2 + 64) + 4096);
   if (opts.cuda_stream) {
@@ -641,6 +657,14 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.iscr = (int*)(base + o_iscr);
   e.candU = (const double2*)(base + o_candU);
   e.candU32 = (const float2*)(base + o_candU32);
+  if (snap) {
+    e.snap = (double2*)(base + o_snap);
+    e.snap_stride = opts.snapshot_entries;
+    e.snap_hdr = (int*)(base + o_shdr);
+    e.snap_max = opts.snapshot_max_gates;
+    e.snap_ph = (double*)(base + o_sph);
+    h->grad_dev = (double*)(base + o_grad);
+  }
   e.candImg = (const int32_t*)(base + o_candI);
   h->xz_dev = (int8_t*)(base + o_aux);
   h->out_dev = (double2*)(base + o_aux + align(gcx::kMaxN * 2));
@@ -859,6 +883,55 @@ int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t
   *re = r.x;
   *im = r.y;
   return device_status(h);
+}
+
+int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* value,
+                           double* grad, int32_t cap_gates, int32_t* ngates) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (!h->e.snap) return fail(h, GCAMPS_EINVAL, "handle created without snapshots (opts.snapshot_entries)");
+  const int n = h->nq[circuit], d = h->e.d;
+  if (!x || !z || !value || !ngates || cap_gates < 0 || (cap_gates > 0 && !grad))
+    return fail(h, GCAMPS_EINVAL, "null argument");
+  double re = 0, im = 0;
+  rc = gcamps_expect_weyl(h, circuit, x, z, &re, &im);   // also checks x, z and the device status
+  if (rc) return rc;
+  *value = re;
+  int meta[gcx::M_COUNT];
+  GC_CUDA(h, cudaMemcpyAsync(meta, h->e.meta + (long long)circuit * gcx::M_COUNT, sizeof meta, cudaMemcpyDeviceToHost,
+                             h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int K = meta[gcx::M_NSNAP];
+  *ngates = K;
+  std::vector<int8_t> xz(2 * n);
+  for (int j = 0; j < n; ++j) {
+    xz[j] = (int8_t)x[j];
+    xz[n + j] = (int8_t)z[j];
+  }
+  GC_CUDA(h, cudaMemcpyAsync(h->xz_dev, xz.data(), xz.size(), cudaMemcpyHostToDevice, h->stream));
+  const int ws = h->e.batch;   // workspace slot
+  GC_CUDA(h, gcx::launch_adjoint(h->e, circuit, ws, h->xz_dev, h->grad_dev, h->stream));
+  int wmeta[gcx::M_COUNT];
+  double wdisc = 0.0;
+  GC_CUDA(h, cudaMemcpyAsync(wmeta, h->e.meta + (long long)ws * gcx::M_COUNT, sizeof wmeta, cudaMemcpyDeviceToHost,
+                             h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(&wdisc, h->e.dstats + (long long)ws * 4, sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  const int ncopy = std::min(K, (int)cap_gates);
+  std::vector<double> g((size_t)std::max(ncopy, 1) * d);
+  if (ncopy > 0)
+    GC_CUDA(h, cudaMemcpyAsync(g.data(), h->grad_dev, (size_t)ncopy * d * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (wmeta[gcx::M_STATUS]) return fail(h, wmeta[gcx::M_STATUS], "adjoint pass failed (device status)");
+  // the backward state carries the observable evolved back through the later gates and can need
+  // more bond dimension than the forward state: if chi_max made it discard weight, the gradient is
+  // not exact
+  if (wdisc > 1e-16)
+    return fail(h, GCAMPS_ECHI, "adjoint pass truncated (discarded weight " + std::to_string(wdisc) +
+                                    "): raise chi_max");
+  if (ncopy > 0) std::memcpy(grad, g.data(), (size_t)ncopy * d * sizeof(double));
+  return GCAMPS_OK;
 }
 
 static int statevector_impl(gcamps_t* h, int circuit, const int32_t* ys, long long nys, double* re, double* im) {

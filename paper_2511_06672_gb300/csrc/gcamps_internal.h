@@ -20,7 +20,14 @@ constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
 
 // meta[] words per circuit
 enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_DIAG_WHERE, M_DIAG_A, M_DIAG_B,
-            M_COUNT };
+            M_NSNAP, M_SNAPOFF, M_COUNT };
+
+// Adjoint snapshots: header of snapshot k of circuit c at snap_hdr + (c snap_max + k) kSnapHdr:
+// [0] arena offset, [1] gate site, [2] phase r of its string, [3] first decision index of the
+// disentangling after it, [kSnapDims ..] bond dimensions (n + 1), then the string (x | z, 2 n).
+constexpr int kSnapDims = 8;
+constexpr int kSnapHdr = 400;
+static_assert(kSnapDims + (kMaxN + 1) + 2 * kMaxN <= kSnapHdr, "snapshot header");
 // stats: S_VN counts exact von Neumann evaluations (the rest were excluded by the Renyi-2 bound)
 // stats[] counters per circuit (int64)
 enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN, S_SVD, S_JSWEEPS, S_JMAX,
@@ -73,6 +80,10 @@ struct Engine {
   int* iscr;        long long iscr_stride;  // permutation scratch
   const double2* candU;                     // [K][d^4] class unitaries, row-major
   const float2* candU32;                    // [K][d^4] the same in FP32 (screening)
+  // adjoint snapshots (null when the handle keeps none): per circuit an arena of snap_stride entries
+  double2* snap;    long long snap_stride;
+  int* snap_hdr;    int snap_max;           // [batch + 1][snap_max][kSnapHdr]
+  double* snap_ph;                          // [batch + 1][snap_max][4] gate phases
   const int32_t* candImg;                   // [K][20] class images
 };
 
@@ -89,6 +100,9 @@ cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int c
                                int* choice, cudaStream_t st);
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
                            cudaStream_t st);
+// Adjoint gradient of Re<W> for circuit cf, using circuit slot cb as the backward workspace:
+// xz_dev = W's exponents (x | z, 2 n int8); grad_dev receives d doubles per recorded gate.
+cudaError_t launch_adjoint(const Engine& e, int cf, int cb, const int8_t* xz_dev, double* grad_dev, cudaStream_t st);
 
 // gcamps_score_theta_noalloc: class scores with every scratch word in static device memory of this
 // library (no allocation).  theta is at most kStaticSide x kStaticSide (rows chi_l d, columns
