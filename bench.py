@@ -270,6 +270,63 @@ def run_batched(args):
     return 0
 
 
+def run_gradient(args):
+    """The differentiation form: qutrits n = 24, 20 layers, 48 parametrised gates
+    diag(1, e^{i th}, e^{-i th}) (synth.param_phase_circuit, seed 1), chi_max = 256; one step = a forward
+    run with snapshots and the adjoint gradient of Re<Z_0 Z_12> with respect to every gate's phases.
+    Reports gradients/s, the split between the two passes, and whether the backward pass stayed exact
+    (GCAMPS_ECHI otherwise)."""
+    import numpy as np
+    import torch
+    from synth import param_phase_circuit
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    d, n, layers, ngates, chi = 3, 24, 20, 48, 256
+    gates, _ = param_phase_circuit(n, d, layers, ngates, 1 + rank)
+    ops = G.ops_from_gates(gates, d)
+    x = np.zeros(n, dtype=np.int32)
+    z = np.zeros(n, dtype=np.int32)
+    z[0] = z[12] = 1
+    sim = G.Simulator(n, d, chi_max=chi, cutoff=1e-12, snapshot_entries=1 << 27, snapshot_max_gates=ngates)
+    fwd, bwd, exact, err = [], [], True, ""
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        sim.reset()
+        sim.run(ops)
+        sim.sync()
+        t1 = time.perf_counter()
+        try:
+            val, grad = sim.expect_gradient(x, z)
+        except G.GcampsError as ex:
+            exact, err = False, str(ex)
+            val, grad = float("nan"), None
+        t2 = time.perf_counter()
+        progress(f"gradient step {i}: forward {t1 - t0:.2f} s, adjoint {t2 - t1:.2f} s")
+        if i >= args.warmup:
+            fwd.append(t1 - t0)
+            bwd.append(t2 - t1)
+        if not exact:
+            break
+    st = sim.stats()
+    total = sum(fwd) + sum(bwd)
+    line = {
+        "metric": "gradients/s", "value": len(fwd) / total if exact and total > 0 else None, "unit": "gradients/s",
+        "n_gpus": 1, "steps": len(fwd), "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(fwd)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gcamps-gradient-qutrit-n24-L20-48params-chi256", "observable": "Re<Z_0 Z_12>",
+                   "timing": "host wall clock around synchronising calls"},
+        "forward_s": float(np.mean(fwd)) if fwd else None, "adjoint_s": float(np.mean(bwd)) if bwd else None,
+        "value_re": val, "exact": exact, "error": err, "max_chi": st["max_chi"],
+        "forward_discarded_weight": st["discarded_weight"],
+    }
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -305,7 +362,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
-    ap.add_argument("--workload", default="bench", choices=["bench", "batched"],
+    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient"],
                     help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch")
     ap.add_argument("--batched-count", type=int, default=64)
     ap.add_argument("--batched-nmax", type=int, default=24, help="n and layers uniform in [16, this]")
@@ -320,6 +377,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "gradient":
+        return run_gradient(args)
 
     import numpy as np
     import torch
