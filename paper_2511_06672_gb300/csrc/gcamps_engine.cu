@@ -1189,15 +1189,15 @@ __device__ __forceinline__ int sturm_count32(const float* dg, const float* e2, i
   return cnt;
 }
 
-// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by bisection, one eigenvalue
-// per thread of the group: eigenvalue j (ascending) is where the Sturm count passes j.  The spectrum
+// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by multisection, P lanes per
+// eigenvalue (see below): eigenvalue j (ascending) is where the Sturm count passes j.  The spectrum
 // lies in [0, tr] (span = |tr|); each eigenvalue is located within 2^-50 span (an entropy error below
 // 1e-12 for the Gram sizes used here).
 //   sh, sh32: shared arrays of 2 cap entries for (diagonal | off-diagonal squared), or null.  With them
-//   (m <= cap) 24 FP32 halvings first bracket eigenvalue j; since an FP32 Sturm count is exact for a
-//   matrix within 8 FP32 units of span of T, the bracket padded by 40 units holds it, which two FP64
-//   counts confirm (else the full interval is used), and 33 FP64 halvings finish.  Without them, 50 FP64
-//   halvings of [0, span] on the global arrays.
+//   (m <= cap) FP32 steps worth 24 halvings first bracket eigenvalue j; since an FP32 Sturm count is
+//   exact for a matrix within 8 FP32 units of span of T, the bracket padded by 40 units holds it, which
+//   two FP64 counts confirm (else the full interval is used), and FP64 steps worth 33 halvings finish.
+//   Without them, FP64 steps worth 50 halvings of [0, span] on the global arrays.
 // Off-diagonal squares are at least 1e-300 span^2 (1e-20 span^2 in FP32), which moves no eigenvalue
 // by more than 1e-150 span (1e-10 span, inside the FP32 padding) and keeps an exactly zero minor from
 // zeroing the rest of the sequence.  od is overwritten with its squares; ev receives the m eigenvalues.
@@ -1244,30 +1244,74 @@ __device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m
     for (int i = g.tid; i + 1 < m; i += g.n) od[i] = fmax(od[i] * od[i], e2min);
   }
   g.sync();
-  for (int j = g.tid; j < m; j += g.n) {
+  // Multisection: P lanes of a warp share eigenvalue j and count at P interior points of its
+  // interval, which then shrinks by P + 1 per step (P as large as the group's warps allow).  All
+  // lanes of a warp run the same number of steps (the group's outcome is combined by a ballot).
+  const int nw = (g.n + 31) / 32;
+  int P = 1;
+  for (int p = 8; p >= 1; --p)
+    if (nw * (32 / p) >= m) {
+      P = p;
+      break;
+    }
+  const int per_warp = 32 / P;
+  const int lane = g.tid & 31, warp = g.tid >> 5;
+  const int grp = lane / P, pidx = lane % P;
+  const unsigned gmask = ((1u << P) - 1u) << (grp < per_warp ? grp * P : 0);
+  constexpr double kLog2[9] = {0.0, 1.0, 1.584962500721156, 2.0, 2.321928094887362, 2.584962500721156,
+                               2.807354922057604, 3.0, 3.169925001442312};
+  const int it32 = (int)ceil(24.0 / kLog2[P] - 1e-9);
+  const int it64 = (int)ceil(33.0 / kLog2[P] - 1e-9);
+  const int itfull = (int)ceil(50.0 / kLog2[P] - 1e-9);
+  for (int base = 0; base < m; base += nw * per_warp) {
+    const int jr = base + warp * per_warp + grp;
+    const bool active = grp < per_warp && jr < m;
+    const int j = active ? jr : 0;
     double lo = gl, hi = gu;
-    int nit = 50;
+    int nit = itfull;
     if (fast) {
       float lo32 = (float)gl, hi32 = (float)gu;
-      for (int it = 0; it < 24; ++it) {
-        const float mid = 0.5f * (lo32 + hi32);
-        if (sturm_count32(sh32, sh32 + cap, m, mid) > j) hi32 = mid;
-        else lo32 = mid;
+      for (int it = 0; it < it32; ++it) {
+        const float step = (hi32 - lo32) / (float)(P + 1);
+        const float x = lo32 + (float)(pidx + 1) * step;
+        const bool flag = active && sturm_count32(sh32, sh32 + cap, m, x) > j;
+        const unsigned bits = (__ballot_sync(0xffffffffu, flag) & gmask) >> (grp < per_warp ? grp * P : 0);
+        const int ps = bits ? __ffs(bits) - 1 : P;
+        const float nlo = ps == 0 ? lo32 : lo32 + (float)ps * step;
+        const float nhi = ps == P ? hi32 : lo32 + (float)(ps + 1) * step;
+        lo32 = nlo;
+        hi32 = nhi;
       }
       const double pad = 40.0 * 5.960464477539063e-08 * span;   // 40 FP32 units
       const double a = (double)lo32 - pad, b = (double)hi32 + pad;
-      if (sturm_count(D, E, m, a) <= j && sturm_count(D, E, m, b) > j) {
+      bool ok;
+      if (P == 1) {
+        ok = !active || (sturm_count(D, E, m, a) <= j && sturm_count(D, E, m, b) > j);
+      } else {
+        bool mine = true;
+        if (active && pidx == 0) mine = sturm_count(D, E, m, a) <= j;
+        if (active && pidx == 1) mine = sturm_count(D, E, m, b) > j;
+        const unsigned fails = __ballot_sync(0xffffffffu, !mine) & gmask;
+        ok = !active || fails == 0u;
+      }
+      if (__all_sync(0xffffffffu, ok)) {
         lo = a;
         hi = b;
-        nit = 33;
+        nit = it64;
       }
     }
     for (int it = 0; it < nit; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(D, E, m, mid) > j) hi = mid;
-      else lo = mid;
+      const double step = (hi - lo) / (double)(P + 1);
+      const double x = lo + (double)(pidx + 1) * step;
+      const bool flag = active && sturm_count(D, E, m, x) > j;
+      const unsigned bits = (__ballot_sync(0xffffffffu, flag) & gmask) >> (grp < per_warp ? grp * P : 0);
+      const int ps = bits ? __ffs(bits) - 1 : P;
+      const double nlo = ps == 0 ? lo : lo + (double)ps * step;
+      const double nhi = ps == P ? hi : lo + (double)(ps + 1) * step;
+      lo = nlo;
+      hi = nhi;
     }
-    ev[j] = 0.5 * (lo + hi);
+    if (active && pidx == 0) ev[j] = 0.5 * (lo + hi);
   }
   g.sync();
 }
