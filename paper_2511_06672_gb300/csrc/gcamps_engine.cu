@@ -1098,9 +1098,11 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
       tri_index(idx, i, j);
       const double2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
       const double2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
-      const double2 t = cadd(cmul(vi, cconj(wj)), cmul(wi, cconj(vj)));
+      // a - (vi conj(wj) + wi conj(vj)), as eight fused multiply-adds
       double2* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
-      const double2 nv = csub(*a, t);
+      double2 nv = *a;
+      nv.x = fma(-vi.x, wj.x, fma(-vi.y, wj.y, fma(-wi.x, vj.x, fma(-wi.y, vj.y, nv.x))));
+      nv.y = fma(-vi.y, wj.x, fma(vi.x, wj.y, fma(-wi.y, vj.x, fma(wi.x, vj.y, nv.y))));
       *a = nv;
       if (j != i) A[(long long)(k + 1 + j) * m + (k + 1 + i)] = cconj(nv);
     }
