@@ -62,6 +62,28 @@ def progress(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
+def rank_seeds(rank: int, per_rank: int = SEEDS_PER_D):
+    """Seeds of one rank's circuits: each rank runs its own circuits (weak scaling, no collective on the
+    data path)."""
+    return [1 + s + rank * per_rank for s in range(per_rank)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank time over all ranks (the value itself for one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step: float, steps: int, world: int, max_time_s: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return units_per_rank_step * steps * world / max_time_s
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -125,8 +147,7 @@ def workload_ops(G, d, rank):
     from synth import brickwork_circuit
     import numpy as np
     ops, begin = [], [0]
-    for s in range(SEEDS_PER_D):
-        seed = 1 + s + rank * SEEDS_PER_D
+    for seed in rank_seeds(rank):
         o = G.ops_from_gates(brickwork_circuit(N, d, LAYERS, T, seed), d)
         ops.append(o)
         begin.append(begin[-1] + len(o))
@@ -238,17 +259,13 @@ def run_batched(args):
     times = [timed(run) for _ in range(args.steps)]
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total = sum(times)
-    if world > 1:
-        tt = torch.tensor([total], device=f"cuda:{local}", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(sum(times), device=f"cuda:{local}")
     stats = [sim.stats(c) for c in range(len(shapes))]
     if any(st["status"] for st in stats):
         raise RuntimeError("device status set")
     tg = sum(st["t_gates"] for st in stats)
     line = {
-        "metric": METRIC, "value": tg * args.steps * world / total, "unit": "T-gates/s", "n_gpus": world,
+        "metric": METRIC, "value": aggregate_rate(tg, args.steps, world, total), "unit": "T-gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"gcamps-batched-{count}-qutrit-n16..{args.batched_nmax}-L16..{args.batched_nmax}-T=n-chi128",
@@ -465,12 +482,7 @@ def main():
         engine_times.extend(a.elapsed_time(b) / 1e3 for a, b in inner)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([sum(times)], device=f"cuda:{local}", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_time = float(tt.item())
-    else:
-        total_time = sum(times)
+    total_time = max_over_ranks(sum(times), device=f"cuda:{local}")
     stats = {d: [sims[d].stats(c) for c in range(SEEDS_PER_D)] for d in (2, 3)}
     for d in (2, 3):
         for st in stats[d]:
@@ -478,8 +490,8 @@ def main():
                 raise RuntimeError(f"device status {st['status']}")
     tg_per_step = sum(st["t_gates"] for d in (2, 3) for st in stats[d])
     cand_per_step = sum(st["candidates_scored"] for d in (2, 3) for st in stats[d])
-    value = tg_per_step * args.steps * world / total_time
-    cand_rate = cand_per_step * args.steps * world / total_time
+    value = aggregate_rate(tg_per_step, args.steps, world, total_time)
+    cand_rate = aggregate_rate(cand_per_step, args.steps, world, total_time)
     vn_frac = sum(st["vn_evaluations"] for d in (2, 3) for st in stats[d]) / max(1, cand_per_step)
     flops_per_launch = sum(st["scoring_flops"] for d in (2, 3) for st in stats[d]) / 2.0
     screen_per_launch = sum(st["screen_flops"] for d in (2, 3) for st in stats[d]) / 2.0
