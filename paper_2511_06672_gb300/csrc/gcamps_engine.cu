@@ -1407,7 +1407,8 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
 // (2M + 4) u |theta'|_F^2, so |G^ - G|_F <= eta tr G with eta = 2 e1 + e1^2 + (2M + 4) u (1 + e1)^2;
 // the same bound holds for the trace.  Then |ln |G^|_F - ln |G|_F| <= eta tr / |G|_F <= eta sqrt(m) and
 // |ln tr^ - ln tr| <= eta, so |S2^ - S2| <= 2 eta sqrt(m) + 2 eta.  The lower bound subtracts twice that
-// plus the rounding of the partial sums.  Outside 1e-30 < tr < 1e30 the lower bound is 0 (S2 >= 0).
+// plus the rounding of the partial sums.  Outside 1e-12 < tr < 1e12 (where FP32 squares of the Gram
+// entries could underflow or overflow and break the bound) the lower bound is 0 (S2 >= 0).
 template <class Grp>
 __device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, int cr, const float2* Q, float2* X,
                         double* s2_out, double* lo_out) {
@@ -1446,7 +1447,7 @@ __device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, in
   }
   const double trd = g.sum((double)tr), frod = g.sum((double)fro);
   double s2 = 0.0, lo = 0.0;
-  if (trd > 1e-30 && trd < 1e30 && frod > 0.0) {
+  if (trd > 1e-12 && trd < 1e12 && frod > 0.0) {
     const double u = 5.960464477539063e-08;
     const double e1 = d * (dd + 6) * u;
     const double eta = 2.0 * e1 + e1 * e1 + (2.0 * M + 4.0) * u * (1.0 + e1) * (1.0 + e1);

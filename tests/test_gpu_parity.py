@@ -401,3 +401,23 @@ def test_uneven_batch_matches_oracle_per_circuit(G):
     with pytest.raises(G.GcampsError):
         sim.set_cluster_size(8)          # above the size the scratch was laid out for
     sim.close()
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1e9])
+def test_score_theta_of_badly_scaled_tensors(G, scale):
+    """Entropies do not depend on the scale of theta; far from unit norm the FP32 screen gives no
+    bound and every class is evaluated exactly, so scores and choice still equal the oracle's."""
+    d, cl, cr = 3, 9, 9
+    rng = np.random.default_rng(21)
+    shape = (cl * d, d * cr)
+    r = 4
+    m = (rng.standard_normal((shape[0], r)) + 1j * rng.standard_normal((shape[0], r))) @ \
+        (rng.standard_normal((r, shape[1])) + 1j * rng.standard_normal((r, shape[1])))
+    theta = (m / np.linalg.norm(m) * scale).reshape(cl, d, d, cr)
+    ref = GCAMPS(8, d, chi_max=81)
+    want = ref.score_bond(theta)
+    sim = G.Simulator(8, d, chi_max=81)
+    s2, vn, choice, nev = sim.score_theta(theta)
+    assert np.max(np.abs(vn - want)) < TOL
+    assert choice == ref.choose(want)
+    sim.close()
