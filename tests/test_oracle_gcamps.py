@@ -137,3 +137,40 @@ def test_planted_transpose_mistake_is_caught(monkeypatch):
     g, psi = run_both(3, 6, 6, 6, 1, chi_max=64, cutoff=1e-14)
     err, _ = sv.same_up_to_phase(g.statevector(), psi)
     assert err > 1e-6
+
+
+def test_replay_of_recorded_decisions_reproduces_the_run():
+    """Replay mode (forced decisions, used to compare runs whose decisions could legitimately differ):
+    feeding back the recorded decisions reproduces tableau, bond dimensions and state exactly; forcing
+    'apply nothing' everywhere gives other decisions but the same physical state (Sec. 3: the fold
+    C~ = C Q^dag never changes psi)."""
+    d, n = 3, 6
+    gates = brickwork_circuit(n, d, 6, 6, 13)
+    a = G.GCAMPS(n, d, chi_max=64, cutoff=1e-14)
+    per_gate = []
+    for gt in gates:
+        a.apply_gate(gt)
+        if not hasattr(gt, "sp_index"):
+            start = len(a.decisions)
+            a.disentangle()
+            per_gate.append([k for _b, k in a.decisions[start:]])
+    assert any(any(x) for x in per_gate)
+    b = G.GCAMPS(n, d, chi_max=64, cutoff=1e-14)
+    c = G.GCAMPS(n, d, chi_max=64, cutoff=1e-14)
+    it = iter(per_gate)
+    for gt in gates:
+        b.apply_gate(gt)
+        c.apply_gate(gt)
+        if not hasattr(gt, "sp_index"):
+            b.disentangle(forced=next(it))
+            c.disentangle(forced=[0] * 64)
+    assert b.decisions == a.decisions
+    ea, pa = a.tab.exps_phase()
+    eb, pb = b.tab.exps_phase()
+    assert np.array_equal(ea, eb) and np.array_equal(pa, pb)
+    assert b.mps.bond_dims() == a.mps.bond_dims()
+    assert np.array_equal(b.statevector(), a.statevector())
+    assert all(k == 0 for _b, k in c.decisions)
+    psi = sv.run(gates, n, d)
+    assert sv.same_up_to_phase(c.statevector(), psi)[0] < 1e-10
+    assert sv.same_up_to_phase(a.statevector(), psi)[0] < 1e-10
