@@ -421,3 +421,69 @@ def test_score_theta_of_badly_scaled_tensors(G, scale):
     assert np.max(np.abs(vn - want)) < TOL
     assert choice == ref.choose(want)
     sim.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_two_qudit_circuits(G, d):
+    """The smallest system (n = 2, one bond): T gates and disentangling against the dense state."""
+    n = 2
+    for seed in (1, 2, 3):
+        gates = brickwork_circuit(n, d, 4, 4, seed)
+        sim = gpu_run(G, gates, n, d, 9, 1e-14)
+        ref = oracle_run(gates, n, d, 9, 1e-14)
+        assert sim.decisions() == ref.decisions
+        assert sim.bond_dims() == ref.mps.bond_dims()
+        err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
+        assert err < TOL
+        sim.close()
+
+
+def test_chi_max_one_truncates_to_a_product_state(G):
+    """chi_max = 1: every truncation keeps one Schmidt value; both sides keep the same product state
+    and discard the same weight."""
+    d, n = 3, 5
+    gates = brickwork_circuit(n, d, 5, 5, 11)
+    sim = gpu_run(G, gates, n, d, 1, 1e-12)
+    ref = oracle_run(gates, n, d, 1, 1e-12)
+    assert sim.bond_dims() == ref.mps.bond_dims() == [1] * (n - 1)
+    assert sim.decisions() == ref.decisions
+    assert abs(sim.stats()["discarded_weight"] - ref.discarded) < 1e-10
+    err, _ = sv.same_up_to_phase(sim.statevector(), ref.statevector())
+    assert err < 1e-9
+    sim.close()
+
+
+def test_empty_gate_list_leaves_the_initial_state(G):
+    d, n = 3, 4
+    sim = G.Simulator(n, d, chi_max=9)
+    sim.run(np.zeros(0, dtype=G.OP_DTYPE))
+    sim.sync()
+    e, p = sim.tableau()
+    ref = oracle_run([], n, d, 9, 1e-12)
+    re_, rp = ref.tab.exps_phase()
+    assert np.array_equal(e, re_) and np.array_equal(p, rp)
+    assert sim.bond_dims() == [1] * (n - 1) and sim.decisions() == []
+    psi = sim.statevector()
+    assert abs(abs(psi[0]) - 1.0) < 1e-14 and np.sum(np.abs(psi[1:])) < 1e-14
+    sim.close()
+
+
+def test_largest_qudit_count_clifford_tableau(G):
+    """n = 128 (the largest supported): a Clifford-only brickwork gives the oracle's tableau bit for bit,
+    and a T gate then reads its Weyl string from the inverse tableau."""
+    d, n = 2, 128
+    gates = [g for g in brickwork_circuit(n, d, 6, 1, 3) if hasattr(g, "sp_index")]
+    sim = G.Simulator(n, d, chi_max=4, cutoff=1e-12)
+    sim.run(G.ops_from_gates(gates, d))
+    sim.sync()
+    ref = clifford_oracle_tableau(gates, n, d)
+    e, p = sim.tableau()
+    assert np.array_equal(e, ref[0]) and np.array_equal(p, ref[1])
+    sim.close()
+
+
+def clifford_oracle_tableau(gates, n, d):
+    g = GCAMPS(n, d, chi_max=4, cutoff=1e-12)
+    for gt in gates:
+        g.apply_gate(gt)
+    return g.tab.exps_phase()
