@@ -42,7 +42,7 @@ extern "C" {
 #define GCAMPS_EINVAL 1  /* bad argument, non-symplectic images, unsupported d       */
 #define GCAMPS_ENOMEM 2  /* device or host allocation failed                         */
 #define GCAMPS_ECUDA 3   /* a CUDA runtime call failed                                */
-#define GCAMPS_ENOCONV 4 /* a device iteration (Jacobi SVD, eigenvalues) hit its cap  */
+#define GCAMPS_ENOCONV 4 /* a device iteration (the Jacobi SVD's sweeps) hit its cap   */
 #define GCAMPS_ECHI 5    /* chi_max bound while discarding weight above strict_weight */
 #define GCAMPS_ESIZE 6   /* a size beyond the fixed maximum of gcamps_score_theta_noalloc */
 #define GCAMPS_ESNAP 7   /* the adjoint snapshot arena (opts.snapshot_entries) is full      */
@@ -92,7 +92,7 @@ typedef struct {
 /* Per class at a bond with R = chi_l d rows and C = d chi_r columns (m = min(R, C),
  * M = max(R, C)): scoring_flops adds 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram) +
  * (16/3) m^3 (Householder tridiagonalisation) per exact von Neumann evaluation (FP64; the
- * eigenvalue bisection is not counted); screen_flops adds 8 d^2 R C + 4 m (m + 1) M per class of
+ * eigenvalue multisection is not counted); screen_flops adds 8 d^2 R C + 4 m (m + 1) M per class of
  * the FP32 Renyi-2 screen (every class of every bond with m > 1). */
 
 /* One operation of a gate list (gcamps_run).  kind: */
@@ -264,7 +264,7 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
  * as in gcamps_score_theta.  choice_dev: 3 int32, the class the disentangler would apply (0 = none;
  * a class is applied only if it lowers the entropy by more than tie_tol, ties to the lowest index),
  * the number of exact entropies its Renyi-2 pruning evaluated, and the device status of the call
- * (0, or GCAMPS_ENOCONV when an eigenvalue iteration hit its cap).  cuda_stream: the cudaStream_t
+ * (0 or a GCAMPS_E* code; the eigenvalue search runs a fixed number of steps, so 0 in practice).  cuda_stream: the cudaStream_t
  * to run on, NULL for the default stream.  Asynchronous: the outputs are valid once the stream has
  * passed this call.
  *

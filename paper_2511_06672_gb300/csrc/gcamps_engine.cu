@@ -31,7 +31,7 @@ namespace cg = cooperative_groups;
 
 // Classes are scored with the Renyi-2 bound first when the Gram has more rows than this.
 constexpr int kPruneMin = 1;
-// CTA-level eigenvalue bisection keeps the tridiagonal in shared memory up to this size.
+// CTA-level eigenvalue multisection keeps the tridiagonal in shared memory up to this size.
 constexpr int kBTri = 256;
 
 // (i, j), j <= i, of entry t of the row-major packed lower triangle (t = i (i + 1) / 2 + j).
