@@ -17,6 +17,10 @@ Multi-GPU: circuits are independent; each rank runs the same per-rank batch with
 (weak scaling, no collective on the data path).
 
 --impl reference runs the FP64 CPU oracle on a bounded sample of the same workload.
+
+Other workloads (--workload): batched (uneven qutrit circuits in one graph-captured launch),
+gradient (forward run + adjoint gradient), chi-layers (the bond dimension after every layer of the
+Fig. 4 circuit family, the experiment of Fig. 5a; with --impl reference the oracle runs it).
 """
 from __future__ import annotations
 
@@ -344,6 +348,122 @@ def run_gradient(args):
     return 0
 
 
+def bond_dims_per_layer(layer_items, run_layer, bond_dims, budget_s: float = float("inf")):
+    """Run a circuit one layer at a time (``run_layer`` on each item) and read the bond dimensions
+    after every layer; stops early once ``budget_s`` seconds have passed.  Returns (dims per layer,
+    seconds per layer)."""
+    dims, secs = [], []
+    t0 = time.perf_counter()
+    for item in layer_items:
+        t1 = time.perf_counter()
+        run_layer(item)
+        dims.append([int(c) for c in bond_dims()])
+        secs.append(time.perf_counter() - t1)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return dims, secs
+
+
+def scaled_max_chi(dims_per_layer, n: int, d: int):
+    """Largest bond dimension after each layer over the largest Schmidt rank d^floor(n/2) of n qudits
+    (the bond-dimension axis of the paper's Fig. 5a; its layer axis is layers / n)."""
+    full = d ** (n // 2)
+    return [max(ds) / full for ds in dims_per_layer]
+
+
+def chi_layer_shapes(args):
+    ds = [int(v) for v in args.chi_layers_d.split(",") if v]
+    ns = [int(v) for v in args.chi_layers_n.split(",") if v]
+    return [(d, n, args.chi_layers_factor * n) for d in ds for n in ns]
+
+
+def _curve_entry(d, n, layers, dims, secs):
+    return {"d": d, "n": n, "layers_run": len(dims), "layers": layers,
+            "scaled_layers": [round((k + 1) / n, 4) for k in range(len(dims))],
+            "scaled_max_chi": [round(v, 6) for v in scaled_max_chi(dims, n, d)],
+            "max_chi": [max(ds) for ds in dims], "seconds": round(sum(secs), 4)}
+
+
+def run_chi_layers(args):
+    """The bond-dimension-per-layer experiment of Fig. 5a on the circuit family of Fig. 4 (a random
+    Clifford on all qudits, then a T gate on qudit 0, per layer; synth.layered_t_circuit, seed 1 plus
+    the rank), run through the library one layer per launch with chi_max = d^floor(n/2) (no
+    truncation by the bond cap) and cutoff 1e-12.  value = T gates / host wall time over all curves."""
+    import torch
+    from synth import layered_t_circuit
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    curves, total_t, total_s = [], 0, 0.0
+    for d, n, layers in chi_layer_shapes(args):
+        gates, ends = layered_t_circuit(n, d, layers, 1 + rank)
+        starts = [0] + ends[:-1]
+        layer_ops = [G.ops_from_gates(gates[a:b], d) for a, b in zip(starts, ends)]
+        csize = args.cluster_qutrit if d == 3 else args.cluster_qubit
+        sim = G.Simulator(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF, cluster_size=csize or args.cluster)
+        dims, secs = bond_dims_per_layer(layer_ops, sim.run, sim.bond_dims, args.chi_layers_budget_s)
+        sim.close()
+        curves.append(_curve_entry(d, n, layers, dims, secs))
+        total_t += len(dims)
+        total_s += sum(secs)
+        progress(f"chi-layers d={d} n={n}: {len(dims)} layers in {sum(secs):.2f} s")
+    t_max = max_over_ranks(total_s)
+    line = {
+        "metric": METRIC, "value": aggregate_rate(total_t, 1, world, t_max) if t_max > 0 else None,
+        "unit": "T-gates/s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF,
+                   "timing": "host wall clock around one synchronising launch per layer"},
+        "curves": curves,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_chi_layers_reference(args):
+    """The same experiment with the oracle on the host (rank 0 only), each curve bounded by
+    --chi-layers-budget-s seconds."""
+    rank, _world, _ = dist_env()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from synth import layered_t_circuit
+    from oracle.gcamps import GCAMPS
+    curves, total_t, total_s = [], 0, 0.0
+    for d, n, layers in chi_layer_shapes(args):
+        gates, ends = layered_t_circuit(n, d, layers, 1)
+        starts = [0] + ends[:-1]
+        ref = GCAMPS(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF)
+
+        def run_layer(gs, ref=ref):
+            for gt in gs:
+                ref.apply_gate(gt)
+                if not hasattr(gt, "sp_index"):
+                    ref.disentangle()
+
+        dims, secs = bond_dims_per_layer([gates[a:b] for a, b in zip(starts, ends)], run_layer,
+                                         ref.mps.bond_dims, args.chi_layers_budget_s)
+        curves.append(_curve_entry(d, n, layers, dims, secs))
+        total_t += len(dims)
+        total_s += sum(secs)
+    value = total_t / total_s if total_s > 0 else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": args.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF},
+        "cpu_baseline": {"value": value, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"layers until {args.chi_layers_budget_s} s per curve"},
+        "e2e": {"value": value, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "curves": curves,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -379,8 +499,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
-    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient"],
-                    help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch")
+    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient", "chi-layers"],
+                    help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch; "
+                         "gradient: forward + adjoint; chi-layers: bond dimension after every layer (Fig. 5a)")
+    ap.add_argument("--chi-layers-d", default="2,3")
+    ap.add_argument("--chi-layers-n", default="6,8")
+    ap.add_argument("--chi-layers-factor", type=int, default=2, help="layers = this x n")
+    ap.add_argument("--chi-layers-budget-s", type=float, default=60.0, help="per curve; later layers are skipped")
     ap.add_argument("--batched-count", type=int, default=64)
     ap.add_argument("--batched-nmax", type=int, default=24, help="n and layers uniform in [16, this]")
     ap.add_argument("--batched-clusters", default="8,4", help="CTAs per circuit tried by the autotuner")
@@ -391,7 +516,11 @@ def main():
     ap.add_argument("--cluster-qutrit", type=int, default=16, help="CTAs per qutrit circuit (0: --cluster)")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload == "chi-layers":
+            return run_chi_layers_reference(args)
         return run_reference(args)
+    if args.workload == "chi-layers":
+        return run_chi_layers(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "gradient":

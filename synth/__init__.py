@@ -15,4 +15,5 @@ from .circuits import (  # noqa: F401
     Diag,
     param_phase_circuit,
     batched_workload,
+    layered_t_circuit,
 )

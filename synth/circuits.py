@@ -15,6 +15,9 @@ Layout (all deterministic in the seed):
 * Non-Clifford gate ``k = 0..t-1`` follows layer ``ceil((k+1) * layers / t) - 1``; its
   site is drawn uniformly right after that layer's gates, in increasing ``k``.
 
+``layered_t_circuit`` gives the layout of the paper's Fig. 4 instead: per layer a random Clifford on all
+qudits (a deep brickwork stand-in), then one T gate on qudit 0.
+
 The module only draws integers and places gates.  It never interprets a symplectic index.
 """
 from __future__ import annotations
@@ -145,6 +148,38 @@ def param_phase_circuit(n: int, d: int, layers: int, ngates: int, seed: int) -> 
             ph = (0.0, th) if d == 2 else (0.0, th, -th)
             out.append(Diag(site, ph, k))
     return out, thetas
+
+
+def layered_t_circuit(n: int, d: int, layers: int, seed: int, depth: int = 0,
+                      phases: Tuple[float, ...] = None) -> Tuple[List[Gate], List[int]]:
+    """The circuit family of the paper's Fig. 4: every layer is a random Clifford on all ``n`` qudits
+    followed by one T gate on qudit 0, so the circuit has as many T gates as layers.
+
+    The random n-qudit Clifford of a layer is ``depth`` (default ``n``) brickwork sublayers of random
+    two-qudit Cliffords drawn as in ``brickwork_circuit`` (sublayer ``s`` of the whole circuit acts on
+    the pairs ``(i, i+1)``, ``i = s (mod 2)``).  This is a stand-in: it is not the uniform distribution
+    on the n-qudit Clifford group.  Returns the gate list and, for every layer, the index one past its
+    last gate (the T gate)."""
+    if n < 2:
+        raise ValueError("need n >= 2")
+    if phases is None:
+        phases = t_gate_phases(d)
+    depth = depth or n
+    rng = SplitMix64(seed)
+    order = sp4_order(d)
+    out: List[Gate] = []
+    ends: List[int] = []
+    sub = 0
+    for _layer in range(layers):
+        for _s in range(depth):
+            for i in range(sub % 2, n - 1, 2):
+                idx = rng.uniform_int(order)
+                shift = tuple(rng.uniform_int(d) for _ in range(4))
+                out.append(Clifford2(i, i + 1, idx, shift))
+            sub += 1
+        out.append(Diag(0, tuple(phases)))
+        ends.append(len(out))
+    return out, ends
 
 
 def batched_workload(count: int, seed0: int = 0, n_range=(16, 48), layer_range=(16, 48)):

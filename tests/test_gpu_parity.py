@@ -487,3 +487,35 @@ def clifford_oracle_tableau(gates, n, d):
     for gt in gates:
         g.apply_gate(gt)
     return g.tab.exps_phase()
+
+
+@pytest.mark.parametrize("d,n,layers", [(3, 6, 12), (2, 8, 16)])
+def test_layer_by_layer_runs_match_oracle(G, d, n, layers):
+    """The circuit family of Fig. 4 (a random Clifford on all qudits, then a T gate on qudit 0, per
+    layer), run one layer per launch on one handle as the bond-dimension-per-layer experiment does:
+    the bond dimensions after every layer and all decisions equal the oracle's, and the final state is
+    exact (chi_max = d^floor(n/2) never binds).  The seeded circuits cover both regimes of Fig. 5a: a
+    product-state MPS for about n layers, then growth."""
+    from synth import layered_t_circuit
+    gates, ends = layered_t_circuit(n, d, layers, 1)
+    chi = d ** (n // 2)
+    sim = G.Simulator(n, d, chi_max=chi, cutoff=1e-12)
+    ref = GCAMPS(n, d, chi_max=chi, cutoff=1e-12)
+    a = 0
+    seen = []
+    for b in ends:
+        sim.run(G.ops_from_gates(gates[a:b], d))
+        for gt in gates[a:b]:
+            ref.apply_gate(gt)
+            if not hasattr(gt, "sp_index"):
+                ref.disentangle()
+        dims = sim.bond_dims()
+        assert dims == ref.mps.bond_dims(), b
+        seen.append(max(dims))
+        a = b
+    sim.sync()
+    assert seen[0] == 1 and max(seen) > d
+    assert sim.decisions() == ref.decisions
+    err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
+    assert err < TOL
+    sim.close()
