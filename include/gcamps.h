@@ -129,6 +129,24 @@ int gcamps_sp4_images(int d, int64_t sp_index, const int32_t* shift, int32_t* im
  * u: its d^2 x d^2 unitary, row-major, interleaved (re, im), 2 d^4 doubles (may be NULL). */
 int gcamps_candidate(int d, int k, int32_t* img, double* u);
 
+/* Named gates of Sec. 2.3 (phases in units of tau = exp(i pi / d), as everywhere in this ABI):
+ *   H    H|i> = d^{-1/2} sum_j omega^{ij} |j>:           X -> Z,               Z -> X^{d-1}
+ *   S    diag(omega^{j(j-1)/2}) (odd d), diag(1, i) (d = 2): X -> tau^{[d=2]} X Z, Z -> Z
+ *   SUM  |i, j> -> |i, i + j> (q0 the control):          X_q0 -> X_q0 X_q1,    Z_q1 -> Z_q0^{d-1} Z_q1
+ *                                                        (Z_q0 and X_q1 fixed)
+ *   X    X|j> = |j + 1>:                                 Z -> omega^{-1} Z
+ *   Z    Z|j> = omega^j |j>:                             X -> omega X               */
+#define GCAMPS_GATE_H 1
+#define GCAMPS_GATE_S 2
+#define GCAMPS_GATE_SUM 3
+#define GCAMPS_GATE_X 4
+#define GCAMPS_GATE_Z 5
+/* Host-only (no GPU needed): generator images of a named gate, in the layout of
+ * gcamps_apply_clifford (img: 6 ints for a one-qudit gate, 20 for SUM; the caller's buffer holds
+ * at least that many).  *nq (may be NULL) receives the gate's qudit count.  EINVAL for an unknown
+ * gate or unsupported d. */
+int gcamps_named_images(int d, int gate, int32_t* img, int32_t* nq);
+
 /* Create a simulator of `batch` independent circuits of n qudits (n >= 2), local dimension d,
  * bond dimension at most chi_max, all in |0...0> with C = I.  Device memory for the MPS is
  * reserved up front for bond dimension d * chi_max (the MPO growth of Sec. 2.4).
@@ -153,6 +171,9 @@ int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
  * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every
  * circuit of the handle. */
 int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img);
+/* gcamps_apply_clifford with the images of a named gate (gcamps_named_images): q1 = -1 for
+ * H, S, X, Z; for SUM q0 is the control and q1 the target.  EINVAL otherwise. */
+int gcamps_apply_named(gcamps_t* h, int gate, int q0, int q1);
 
 /* Diagonal non-Clifford gate diag(exp(i phases[j])), j = 0..d-1, on `site` (Sec. 2.3.2, Sec. 3):
  * P = C^dag Z_site C is read from the inverse tableau, the gate is expanded as

@@ -13,10 +13,12 @@ import numpy as np
 
 from . import _native as N
 from ._native import OP_DTYPE, OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE
+from ._native import GATE_H, GATE_S, GATE_SUM, GATE_X, GATE_Z
 
-__all__ = ["Simulator", "GcampsError", "sp4_images", "num_candidates", "candidate", "ops_from_gates",
+__all__ = ["Simulator", "GcampsError", "sp4_images", "named_images", "num_candidates", "candidate", "ops_from_gates",
            "score_theta_noalloc", "weyl_expectation",
-           "OP_DTYPE", "OP_CLIFFORD", "OP_NONCLIFFORD", "OP_DISENTANGLE"]
+           "OP_DTYPE", "OP_CLIFFORD", "OP_NONCLIFFORD", "OP_DISENTANGLE",
+           "GATE_H", "GATE_S", "GATE_SUM", "GATE_X", "GATE_Z"]
 
 
 class GcampsError(RuntimeError):
@@ -44,6 +46,18 @@ def sp4_images(d: int, sp_index: int, shift=(0, 0, 0, 0)) -> np.ndarray:
     if rc:
         raise GcampsError(rc, "bad sp4 index or shift")
     return img
+
+
+def named_images(d: int, gate: int) -> np.ndarray:
+    """Generator images of a named gate (GATE_H, GATE_S, GATE_SUM, GATE_X, GATE_Z) in the layout of
+    Simulator.apply_clifford: 6 int32 for a one-qudit gate, 20 for SUM."""
+    lib = N.load()
+    img = np.zeros(20, dtype=np.int32)
+    nq = C.c_int32()
+    rc = lib.gcamps_named_images(d, gate, N.ptr(img, C.c_int32), C.byref(nq))
+    if rc:
+        raise GcampsError(rc, "unknown named gate or unsupported d")
+    return img[: 6 if nq.value == 1 else 20].copy()
 
 
 def candidate(d: int, k: int):
@@ -178,6 +192,9 @@ class Simulator:
     def apply_clifford(self, q0: int, q1: int, img: Sequence[int]):
         a = np.ascontiguousarray(img, dtype=np.int32)
         self._c(self._lib.gcamps_apply_clifford(self._h, q0, q1, N.ptr(a, C.c_int32)))
+
+    def apply_named(self, gate: int, q0: int, q1: int = -1):
+        self._c(self._lib.gcamps_apply_named(self._h, gate, q0, q1))
 
     def apply_nonclifford(self, site: int, phases: Sequence[float]):
         p = np.zeros(4)

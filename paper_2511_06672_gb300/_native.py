@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libg
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE, ESNAP = 0, 1, 2, 3, 4, 5, 6, 7
 NOALLOC_MAX_SIDE = 81
 OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE = 1, 2, 3
+GATE_H, GATE_S, GATE_SUM, GATE_X, GATE_Z = 1, 2, 3, 4, 5
 
 OP_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("img", "<i4", (20,)),
                      ("pad", "<i4"), ("phases", "<f8", (4,))], align=True)
@@ -38,6 +39,7 @@ class Stats(C.Structure):
 
 EXPORTS = [
     "gcamps_default_opts", "gcamps_num_candidates", "gcamps_sp4_images", "gcamps_candidate",
+    "gcamps_named_images", "gcamps_apply_named",
     "gcamps_create",
     "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_destroy", "gcamps_num_qudits",
     "gcamps_set_cluster_size", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
@@ -66,6 +68,8 @@ def load(path: str = LIB_PATH):
         "gcamps_num_candidates": (C.c_int, [C.c_int]),
         "gcamps_sp4_images": (C.c_int, [C.c_int, C.c_int64, i32p, i32p]),
         "gcamps_candidate": (C.c_int, [C.c_int, C.c_int, i32p, dp]),
+        "gcamps_named_images": (C.c_int, [C.c_int, C.c_int, i32p, i32p]),
+        "gcamps_apply_named": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
         "gcamps_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
         "gcamps_create_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
         "gcamps_create_batch_uneven": (C.c_int, [C.c_int, i32p, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),

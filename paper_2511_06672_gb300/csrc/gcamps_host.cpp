@@ -436,6 +436,35 @@ int gcamps_num_candidates(int d) {
   return (int)tables(d).reps.size();
 }
 
+// Images of the named gates, worked out from their definitions (Sec. 2.3) with Z X = omega X Z:
+// H X H^dag = Z and H Z H^dag = X^{-1} for the DFT H; S X S^dag = omega^{j} on |j> -> |j+1>, i.e. X Z
+// (tau X Z = Y for d = 2); SUM maps X_c -> X_c X_t and Z_t -> Z_c^{-1} Z_t; X Z X^dag = omega^{-1} Z;
+// Z X Z^dag = omega X.  Phases in units of tau (omega = tau^2).
+int gcamps_named_images(int d, int gate, int32_t* img, int32_t* nq) {
+  if ((d != 2 && d != 3) || !img) return GCAMPS_EINVAL;
+  const int m1 = d - 1, two_d = 2 * d;
+  auto one = [&](int xx, int xz, int xr, int zx, int zz, int zr) {
+    const int32_t v[6] = {xx, xz, xr, zx, zz, zr};
+    std::memcpy(img, v, sizeof v);
+    if (nq) *nq = 1;
+    return GCAMPS_OK;
+  };
+  switch (gate) {
+    case GCAMPS_GATE_H: return one(0, 1, 0, m1, 0, 0);
+    case GCAMPS_GATE_S: return one(1, 1, d == 2 ? 1 : 0, 0, 1, 0);
+    case GCAMPS_GATE_X: return one(1, 0, 0, 0, 1, two_d - 2);
+    case GCAMPS_GATE_Z: return one(1, 0, 2, 0, 1, 0);
+    case GCAMPS_GATE_SUM: {
+      // images of X_c, Z_c, X_t, Z_t as (x_c, z_c, x_t, z_t, phase)
+      const int32_t v[20] = {1, 0, 1, 0, 0,   0, 1, 0, 0, 0,   0, 0, 1, 0, 0,   0, m1, 0, 1, 0};
+      std::memcpy(img, v, sizeof v);
+      if (nq) *nq = 2;
+      return GCAMPS_OK;
+    }
+    default: return GCAMPS_EINVAL;
+  }
+}
+
 int gcamps_sp4_images(int d, int64_t sp_index, const int32_t* shift, int32_t* img) {
   if ((d != 2 && d != 3) || !img) return GCAMPS_EINVAL;
   const Tables& t = tables(d);
@@ -728,6 +757,15 @@ int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img) {
   std::memcpy(op.img, img, sizeof(int32_t) * (nq == 2 ? 20 : 6));
   GC_CUDA(h, gcx::launch_single(h->e, op, h->stream));
   return GCAMPS_OK;
+}
+
+int gcamps_apply_named(gcamps_t* h, int gate, int q0, int q1) {
+  if (!h) return GCAMPS_EINVAL;
+  int32_t img[20];
+  int32_t nq = 0;
+  if (gcamps_named_images(h->e.d, gate, img, &nq)) return fail(h, GCAMPS_EINVAL, "unknown named gate");
+  if ((nq == 1) != (q1 == -1)) return fail(h, GCAMPS_EINVAL, "q1 must be -1 for one-qudit gates, a qudit for SUM");
+  return gcamps_apply_clifford(h, q0, q1, img);
 }
 
 int gcamps_apply_nonclifford(gcamps_t* h, int site, const double* phases) {

@@ -100,3 +100,29 @@ def test_create_rejects_bad_options_before_touching_the_gpu(lib):
         h = C.c_void_p()
         assert lib.gcamps_create(4, 3, 8, C.byref(o), C.byref(h)) == N.EINVAL
         assert not h.value
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_named_images_match_dense_conjugation(lib, d):
+    """gcamps_named_images vs the oracle's dense conjugation U g U^dag of the gates as defined in
+    Sec. 2.3 (H, S, SUM as matrices; X, Z the Weyl generators), snapped to tau^r W."""
+    from oracle import clifford
+    from oracle.weyl import X, Z
+    import paper_2511_06672_gb300 as G
+    dense = {G.GATE_H: (clifford.H_gate(d), 1), G.GATE_S: (clifford.S_gate(d), 1),
+             G.GATE_SUM: (clifford.SUM_gate(d), 2), G.GATE_X: (X(d), 1), G.GATE_Z: (Z(d), 1)}
+    for gate, (u, nq) in dense.items():
+        imgs = clifford.images_by_conjugation(u, nq, d)
+        if nq == 1:
+            want = []
+            for w in imgs:
+                want.extend([int(w.x[0]), int(w.z[0]), int(w.r)])
+            want = np.array(want, dtype=np.int32)
+        else:
+            want = _imgs_to_array(imgs)
+        got = G.named_images(d, gate)
+        assert np.array_equal(got, want), gate
+    with pytest.raises(G.GcampsError):
+        G.named_images(d, 6)
+    with pytest.raises(G.GcampsError):
+        G.named_images(5, G.GATE_H)

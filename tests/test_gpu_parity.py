@@ -489,6 +489,35 @@ def clifford_oracle_tableau(gates, n, d):
     return g.tab.exps_phase()
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_named_gates_match_oracle(G, d):
+    """gcamps_apply_named (H, S, SUM in either qudit order, X, Z) against the oracle's dense conjugation
+    of the same matrices: forward and inverse tableaux bit for bit."""
+    from oracle.weyl import X, Z
+    n = 4
+    sim = G.Simulator(n, d, chi_max=8)
+    ref = GCAMPS(n, d, chi_max=8)
+    one = {G.GATE_H: clifford.H_gate(d), G.GATE_S: clifford.S_gate(d), G.GATE_X: X(d), G.GATE_Z: Z(d)}
+    rng = np.random.default_rng(60 + d)
+    for _step in range(40):
+        gate = int(rng.integers(1, 6))
+        if gate == G.GATE_SUM:
+            q0, q1 = (int(v) for v in rng.choice(n, 2, replace=False))
+            sim.apply_named(gate, q0, q1)
+            ref.apply_clifford([q0, q1], clifford.images_by_conjugation(clifford.SUM_gate(d), 2, d))
+        else:
+            q = int(rng.integers(n))
+            sim.apply_named(gate, q)
+            ref.apply_clifford([q], clifford.images_by_conjugation(one[gate], 1, d))
+    sim.sync()
+    assert_same_tableaux(sim, ref)
+    with pytest.raises(G.GcampsError):
+        sim.apply_named(G.GATE_SUM, 0)
+    with pytest.raises(G.GcampsError):
+        sim.apply_named(G.GATE_H, 0, 1)
+    sim.close()
+
+
 @pytest.mark.parametrize("d,n,layers", [(3, 6, 12), (2, 8, 16)])
 def test_layer_by_layer_runs_match_oracle(G, d, n, layers):
     """The circuit family of Fig. 4 (a random Clifford on all qudits, then a T gate on qudit 0, per
