@@ -150,7 +150,9 @@ int gcamps_named_images(int d, int gate, int32_t* img, int32_t* nq);
 /* Create a simulator of `batch` independent circuits of n qudits (n >= 2), local dimension d,
  * bond dimension at most chi_max, all in |0...0> with C = I.  Device memory for the MPS is
  * reserved up front for bond dimension d * chi_max (the MPO growth of Sec. 2.4).
- * gcamps_create is gcamps_create_batch with batch = 1. */
+ * gcamps_create is gcamps_create_batch with batch = 1.  EINVAL (before any CUDA call) for bad
+ * options, or when a matrix of the engine would exceed 2^31 - 1 entries: the two-site tensor after
+ * the MPO, (d c) x (d c) with c = d min(chi_max, d^min(b, n-b)) the largest bond capacity. */
 int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 /* Batch of circuits with their own qudit counts n[c] (2 <= n[c] <= 128), for many independent

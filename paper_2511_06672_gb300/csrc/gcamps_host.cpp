@@ -382,6 +382,12 @@ int cuda_fail(gcamps_t* h, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail((h), _e, #call); \
   } while (0)
 
+// Shape limits of a handle: every matrix the engine works on (two-site tensor, Jacobi rotations,
+// scored theta' and its Gram) has at most 2^31 - 1 entries, so 32-bit element indices cannot wrap;
+// bond capacities d chi are checked first, at a size whose squares cannot overflow 64 bits.
+constexpr long long kMaxMatrixEntries = 2147483647LL;
+constexpr long long kMaxBondCap = 1LL << 20;
+
 long long sat_pow(int d, int k, long long cap) {
   long long v = 1;
   for (int i = 0; i < k; ++i) {
@@ -560,6 +566,10 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
       cap[b] = d * std::min<long long>(chi_max, sb);
       maxdim = std::max(maxdim, cap[b]);
     }
+    if (maxdim > kMaxBondCap) {   // the products below stay far from overflow
+      delete h;
+      return GCAMPS_EINVAL;
+    }
     long long* off = &h->site_off[(size_t)c * (n + 1)];
     for (int j = 0; j < nc; ++j) {
       const long long sz = cap[j] * d * cap[j + 1];
@@ -593,6 +603,10 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   const long long sside = (long long)d * std::min<long long>(chi_max, maxdim);
   e.scap = sside * sside;
   cly.total = cly.block + 2 * e.scap + sside + 64;
+  if (tcap > kMaxMatrixEntries || e.wcap > kMaxMatrixEntries || e.scap > kMaxMatrixEntries) {
+    delete h;
+    return GCAMPS_EINVAL;
+  }
   e.tab_stride = 2LL * (4LL * n * n + 2LL * n);
 
   e.sing_stride = 4 * maxm + 128;   // singular values | sort scratch / QR betas | QR diagonal

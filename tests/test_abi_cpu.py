@@ -102,6 +102,25 @@ def test_create_rejects_bad_options_before_touching_the_gpu(lib):
         assert not h.value
 
 
+def test_create_rejects_shapes_beyond_32_bit_matrix_indices(lib):
+    """A handle whose largest matrix (the two-site tensor after the MPO, or the Jacobi rotations) would
+    exceed 2^31 - 1 entries is refused on the host, before any CUDA call; shapes below the limit get
+    past the check (without a GPU they then fail at the first CUDA call instead)."""
+    import torch
+    from paper_2511_06672_gb300 import _native as N
+    for n, d, chi in ((40, 3, 1 << 16), (64, 2, 1 << 16), (128, 3, 1 << 30), (128, 2, 1 << 30), (20, 3, 6000)):
+        h = C.c_void_p()
+        assert lib.gcamps_create(n, d, chi, None, C.byref(h)) == N.EINVAL, (n, d, chi)
+        assert not h.value
+    if torch.cuda.is_available():
+        return
+    for n, d, chi in ((64, 3, 1024), (32, 3, 256), (20, 3, 5000), (40, 2, 11000)):
+        h = C.c_void_p()
+        rc = lib.gcamps_create(n, d, chi, None, C.byref(h))
+        assert rc not in (N.OK, N.EINVAL), (n, d, chi)
+        assert not h.value
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_named_images_match_dense_conjugation(lib, d):
     """gcamps_named_images vs the oracle's dense conjugation U g U^dag of the gates as defined in
