@@ -1537,9 +1537,9 @@ __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 // ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
 // One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
 // decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class
-// from an FP32 screen with a rigorous lower bound s2lo (s2_fp32), and the rounds below use s2lo;
-// round 1 evaluates S_vN of the identity and of the classes with the smallest S2 (as many as the
-// cluster evaluates at once), giving an upper bound B on the best entropy; round 2 evaluates every
+// from an FP32 screen with a rigorous lower bound s2lo (s2_fp32), and the passes below use s2lo;
+// the first pass evaluates S_vN of the identity and of the classes with the smallest S2 (as many as the
+// cluster evaluates at once), giving an upper bound B on the best entropy; the second pass evaluates every
 // other class with S2 <= B + tie_tol (usually none: they are a prefix of the S2 order).  A class left out
 // has S_vN >= S2 > best + tie_tol, so the decision equals the one from evaluating every class.
 // Cluster-wide choice of the class for one theta (shape chi_l x d x d x chi_r in global memory,
@@ -1592,7 +1592,7 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
       cluster_sync();
     } else {
       if (leader) {
-        // round 1: the identity and the classes of smallest S2 lower bound, one per FP64 pipe of the
+        // first pass: the identity and the classes of smallest S2 lower bound, one per FP64 pipe of the
         // cluster (warp-level scoring) or one per CTA (CTA-level scoring)
         const int L = (small ? 4 * C.csize : C.csize) - 1;
         for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
@@ -1618,7 +1618,7 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
       score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
       cluster_sync();
       if (leader && threadIdx.x == 0) {
-        // round 2: every class the bounds cannot exclude.  Kind 0: S2 lower bound within tie_tol of the
+        // second pass: every class the bounds cannot exclude.  Kind 0: S2 lower bound within tie_tol of the
         // best exact entropy.  Kind 2: rank bound below the best exact rank, or equal to it with the S2
         // bound within tie_tol of the best entropy among the classes of that rank.
         int rmin = 1 << 30;
