@@ -182,6 +182,89 @@ def cpu_oracle_sample(budget_s: float = 20.0):
         seed += 1
 
 
+def _oracle_whole_circuit(shape):
+    """One whole batched-workload circuit through the oracle (a pool worker): (T gates, seconds)."""
+    from synth import brickwork_circuit
+    from oracle.gcamps import GCAMPS
+    n, layers, t, seed, d, chi = shape
+    t0 = time.perf_counter()
+    g = GCAMPS(n, d, chi_max=chi, cutoff=CUTOFF)
+    tg = 0
+    for gt in brickwork_circuit(n, d, layers, t, seed):
+        g.apply_gate(gt)
+        if not hasattr(gt, "sp_index"):
+            g.disentangle()
+            tg += 1
+    return tg, time.perf_counter() - t0
+
+
+def cpu_oracle_pool_sample(shapes, d: int, chi: int, budget_s: float, procs: int):
+    """The oracle on all host cores, one process per circuit (spawned workers, one BLAS thread each):
+    circuits of ``shapes`` are started in order while fewer than ``budget_s`` seconds have passed, and
+    the ones in flight are then finished.  Returns (T gates / wall seconds, wall seconds, circuits)."""
+    import multiprocessing as mp
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    todo = [(n, layers, t, seed, d, chi) for n, layers, t, seed in shapes]
+    t_gates, done = 0, 0
+    with ctx.Pool(procs) as pool:
+        t0 = time.perf_counter()
+        pending = []
+        nxt = 0
+        while nxt < len(todo) and len(pending) < procs:
+            pending.append(pool.apply_async(_oracle_whole_circuit, (todo[nxt],)))
+            nxt += 1
+        while pending:
+            ready = [r for r in pending if r.ready()]
+            if not ready:
+                time.sleep(0.01)
+                continue
+            for r in ready:
+                pending.remove(r)
+                tg, _sec = r.get()
+                t_gates += tg
+                done += 1
+                if nxt < len(todo) and time.perf_counter() - t0 < budget_s:
+                    pending.append(pool.apply_async(_oracle_whole_circuit, (todo[nxt],)))
+                    nxt += 1
+        wall = time.perf_counter() - t0
+    return t_gates / wall, wall, done
+
+
+def run_batched_reference(args):
+    """--impl reference for the batched workload: the oracle on every host core (rank 0 only), each
+    step a bounded sample of the circuits rank 0 runs, in order."""
+    from synth import batched_workload
+    rank, _world, _ = dist_env()
+    if rank != 0:
+        return 0
+    procs = os.cpu_count() or 1
+    shapes = batched_workload(args.batched_count, seed0=0, n_range=(16, args.batched_nmax),
+                              layer_range=(16, args.batched_nmax))
+    tg_total, wall_total, circuits = 0.0, 0.0, 0
+    for i in range(args.warmup + args.steps):
+        rate, wall, done = cpu_oracle_pool_sample(shapes, 3, 128, args.ref_step_s, procs)
+        if i >= args.warmup:
+            tg_total += rate * wall
+            wall_total += wall
+            circuits += done
+    value = tg_total / wall_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_total / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"gcamps-batched-{args.batched_count}-qutrit-n16..{args.batched_nmax}"
+                               f"-L16..{args.batched_nmax}-T=n-chi128"},
+        "cpu_baseline": {"value": value, "unit": "T-gates/s", "cores": procs, "kind": "oracle",
+                         "sample": f"{circuits} whole circuits over {args.steps} steps, circuits started "
+                                   f"in order for ~{args.ref_step_s}s per step, one process per circuit"},
+        "e2e": {"value": value, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """The batched form: 256 independent qutrit circuits of uneven size (n and layers uniform in
     [16, 48], n T gates each, chi_max = 128) in one handle; every step is one reset and one engine
@@ -283,6 +366,12 @@ def run_batched(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        procs = os.cpu_count() or 1
+        rate, wall, done = cpu_oracle_pool_sample(shapes, d, chi, args.ref_step_s, procs)
+        line["cpu_baseline"] = {"value": rate, "unit": "T-gates/s", "cores": procs, "kind": "oracle",
+                                "sample": f"{done} whole circuits of this workload in order, one process per "
+                                          f"circuit, {wall:.1f}s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -518,6 +607,8 @@ def main():
     if args.impl == "reference":
         if args.workload == "chi-layers":
             return run_chi_layers_reference(args)
+        if args.workload == "batched":
+            return run_batched_reference(args)
         return run_reference(args)
     if args.workload == "chi-layers":
         return run_chi_layers(args)

@@ -47,3 +47,14 @@ def test_single_process_is_unchanged():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.rank_seeds(0) == list(range(1, bench.SEEDS_PER_D + 1))
+
+
+def test_all_core_oracle_sample_finishes_the_circuits_it_starts():
+    """The batched workload's CPU baseline: spawned workers, one circuit each; every circuit started is
+    finished and counted, and a zero budget still runs one circuit per worker."""
+    import bench
+    shapes = [(4, 3, 4, 1), (5, 3, 5, 2), (4, 2, 4, 3)]
+    rate, wall, done = bench.cpu_oracle_pool_sample(shapes, 3, 27, 60.0, 2)
+    assert done == 3 and wall > 0 and rate == pytest.approx((4 + 5 + 4) / wall)
+    _rate, _wall, done = bench.cpu_oracle_pool_sample(shapes, 3, 27, 0.0, 2)
+    assert done == 2
