@@ -609,6 +609,12 @@ def main():
             return run_chi_layers_reference(args)
         if args.workload == "batched":
             return run_batched_reference(args)
+        if args.workload == "gradient":
+            if dist_env()[0] == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle's gradient is a dense "
+                                  "state-vector adjoint; 3^24 amplitudes at n = 24 do not fit in host memory"}),
+                      flush=True)
+            return 0
         return run_reference(args)
     if args.workload == "chi-layers":
         return run_chi_layers(args)
