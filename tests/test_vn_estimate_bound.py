@@ -8,11 +8,13 @@ used by the library yet):
 
 * theta' = Q theta and its Gram in FP32: |G^ - G|_F <= eta tr G with eta as for the Renyi-2 screen,
   eta = 2 e1 + e1^2 + (2M + 4) u (1 + e1)^2, e1 = d (d^2 + 6) u, u = 2^-24;
+* scaling G^ to unit trace before the reduction (which keeps every square inside FP32's range) adds
+  one rounding per entry, at most u tr G in Frobenius norm;
 * an FP32 Hermitian eigensolver is backward stable: its eigenvalues are those of G^ + E with
   |E|_F <= 16 m u |G^|_F, and |G^|_F <= (1 + eta) tr G; a bisection finish adds at most 9 u tr G per
   eigenvalue;
 * Hoffman-Wielandt and Cauchy-Schwarz: sum_i |lambda^_i - lambda_i| <= sqrt(m) |G^ + E - G|_F, so
-  the l1 distance of the spectra is at most D = (sqrt(m) (eta + 16 m u (1 + eta)) + 9 m u) tr G;
+  the l1 distance of the spectra is at most D = (sqrt(m) (eta + u + 16 m u (1 + eta)) + 9 m u) tr G;
 * normalising by the estimated trace (and clipping negative estimates) at most doubles the l1
   distance of the normalised spectra, so their trace distance is T <= D / tr G;
 * Fannes-Audenaert: |S^ - S| <= T ln(m - 1) + H2(T); the bound used is twice that with ln m
@@ -40,7 +42,7 @@ def _dv(d, rows, cols):
     m, M = min(rows, cols), max(rows, cols)
     e1 = d * (d * d + 6) * U
     eta = 2 * e1 + e1 * e1 + (2 * M + 4) * U * (1 + e1) ** 2
-    t = np.sqrt(m) * (eta + 16 * m * U * (1 + eta)) + 9 * m * U
+    t = np.sqrt(m) * (eta + U + 16 * m * U * (1 + eta)) + 9 * m * U
     assert t <= 0.5
     return 2 * (t * np.log(m) + _h2(t))
 
@@ -48,6 +50,7 @@ def _dv(d, rows, cols):
 def _fp32_entropy(x):
     x32 = x.astype(np.complex64)
     g = x32 @ x32.conj().T if x.shape[0] <= x.shape[1] else x32.conj().T @ x32
+    g = (g * np.float32(1.0 / np.trace(g).real)).astype(np.complex64)
     lam = np.clip(np.linalg.eigvalsh(g).astype(np.float64), 0.0, None)
     p = lam / lam.sum()
     p = p[p > 0]
