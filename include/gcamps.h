@@ -120,10 +120,12 @@ int gcamps_num_candidates(int d);
  * (column k = exponents of the image of generator k in coordinates (x_q0, z_q0, x_q1, z_q1)),
  * U_S maps each generator to the standard-phase Weyl operator of its column (phase tau^0 for
  * odd d, tau^{x_q0 z_q0 + x_q1 z_q1} for d = 2), and W(shift) = X^s0 Z^s1 (x) X^s2 Z^s3 acts after
- * it.  This is how the seeded benchmark circuits name their gates.  EINVAL on bad arguments. */
+ * it.  This is how the seeded benchmark circuits name their gates (the random two-qudit Cliffords of
+ * the Sec. 4 benchmarks; Sp(4, F_d) as in Sec. 3.1).  EINVAL on bad arguments. */
 int gcamps_sp4_images(int d, int64_t sp_index, const int32_t* shift, int32_t* img);
 
-/* Host-only (no GPU needed): class k (0 <= k < gcamps_num_candidates(d)) of the disentangler set.
+/* Host-only (no GPU needed): class k (0 <= k < gcamps_num_candidates(d)) of the disentangler set
+ * (the 20 / 90 entangling classes of Sec. 3, built as in Sec. 3.1).
  * img[20]: generator images of its representative (class 0 = identity; the others are the
  * lexicographically smallest symplectic matrix of their class {(L_0 (+) L_1) S}, standard phases);
  * u: its d^2 x d^2 unitary, row-major, interleaved (re, im), 2 d^4 doubles (may be NULL). */
@@ -158,23 +160,27 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
 /* Batch of circuits with their own qudit counts n[c] (2 <= n[c] <= 128), for many independent
  * circuits of uneven size in one engine launch (gcamps_run with per-circuit op ranges).  Memory is
  * reserved per circuit for its own n[c]; calls that apply to every circuit (apply_*, disentangle)
- * require sites below the smallest n[c]; readouts use the circuit's own n[c]. */
+ * require sites below the smallest n[c]; readouts use the circuit's own n[c].  No counterpart in the
+ * paper (it runs one circuit at a time, Sec. 4.1.1). */
 int gcamps_create_batch_uneven(int batch, const int32_t* n, int d, int chi_max, const gcamps_opts* o,
                                gcamps_t** out);
+/* Waits for the handle's work, then frees it, its device memory and the stream it created (not a
+ * caller's stream); NULL is ignored. */
 void gcamps_destroy(gcamps_t* h);
-/* Qudits of circuit `circuit` (-1 for a bad handle or index). */
+/* Qudits of circuit `circuit` (-1 for a bad handle or index).  No counterpart in the paper. */
 int gcamps_num_qudits(gcamps_t* h, int circuit);
 /* CTAs per circuit for the following launches: a power of two up to the cluster size the handle was
  * created with (its per-CTA scratch is laid out for that many).  Synchronises the handle's stream.
- * Used to pick the fastest cluster size for a workload by measurement. */
+ * Used to pick the fastest cluster size for a workload by measurement.  No counterpart in the paper
+ * (a launch shape of this library).  EINVAL for other sizes. */
 int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
 
 /* C <- G C for a one- or two-qudit Clifford G (Sec. 3, top loop of Fig. 3): the tableau rows
  * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every
  * circuit of the handle. */
 int gcamps_apply_clifford(gcamps_t* h, int q0, int q1, const int32_t* img);
-/* gcamps_apply_clifford with the images of a named gate (gcamps_named_images): q1 = -1 for
- * H, S, X, Z; for SUM q0 is the control and q1 the target.  EINVAL otherwise. */
+/* gcamps_apply_clifford with the images of a named gate of Sec. 2.3 (gcamps_named_images): q1 = -1
+ * for H, S, X, Z; for SUM q0 is the control and q1 the target.  EINVAL otherwise. */
 int gcamps_apply_named(gcamps_t* h, int gate, int q0, int q1);
 
 /* Diagonal non-Clifford gate diag(exp(i phases[j])), j = 0..d-1, on `site` (Sec. 2.3.2, Sec. 3):
@@ -191,11 +197,13 @@ int gcamps_apply_nonclifford(gcamps_t* h, int site, const double* phases);
  * Applied to every circuit of the handle. */
 int gcamps_disentangle(gcamps_t* h, gcamps_stats* st);
 
-/* Run a gate list on every circuit of the handle.  ops: host array; circuit c runs
- * ops[begin[c] .. begin[c+1]) (begin has batch+1 entries; NULL begin = all ops on every
- * circuit).  One kernel launch for the whole list; asynchronous. */
+/* Run a gate list on every circuit of the handle: both loops of Fig. 3 (Sec. 3) for every op in
+ * order.  ops: host array; circuit c runs ops[begin[c] .. begin[c+1]) (begin has batch+1 entries;
+ * NULL begin = all ops on every circuit).  One kernel launch for the whole list; asynchronous.
+ * EINVAL (nothing enqueued) for a bad op or bad offsets. */
 int gcamps_run(gcamps_t* h, const gcamps_op* ops, int nops, const int32_t* begin);
-/* Same, with `ops_dev` and `begin_dev` already in device memory (no host-to-device copy). */
+/* Same, with `ops_dev` and `begin_dev` already in device memory (no host-to-device copy; the ops
+ * are not validated, so they must have passed through gcamps_run's checks before). */
 int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begin_dev);
 
 /* <psi| W |psi> for W = (x)_j X_j^{x_j} Z_j^{z_j} (phase 1), as C^dag W C is a product of inverse
@@ -220,41 +228,43 @@ int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t
 int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* value,
                            double* grad, int32_t cap_gates, int32_t* ngates);
 
-/* Dense C|MPS> (d^n amplitudes, d^n <= 2^20) up to one global phase (a Clifford given by its
+/* Dense psi = C|MPS> (Sec. 3; d^n amplitudes, d^n <= 2^20) up to one global phase (a Clifford given by its
  * images has no defined phase): C|y> = prod_j D_j^{y_j} C|0>, with C|0> the common +1
  * eigenvector of the stabilizer rows.  re/im: d^n doubles each. */
 int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im);
-/* One amplitude <s|C|MPS> with the same global-phase convention (d^n <= 2^20). */
+/* One amplitude <s|C|MPS> (Sec. 3) with the same global-phase convention (d^n <= 2^20). */
 int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im);
 
-/* Tableau of C: exps[2n][2n] (row-major; rows 0..n-1 = C Z_j C^dag, rows n..2n-1 = C X_j C^dag;
+/* Tableau of C (Sec. 2.2, Sec. 2.3): exps[2n][2n] (row-major; rows 0..n-1 = C Z_j C^dag, rows n..2n-1 = C X_j C^dag;
  * columns x_0..x_{n-1} | z_0..z_{n-1}) and phase[2n] (mod 2d, units of tau). */
 int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
-/* Inverse tableau: rows C^dag Z_j C (0..n-1) and C^dag X_j C (n..2n-1), same layout. */
+/* Inverse tableau: rows C^dag Z_j C (0..n-1) and C^dag X_j C (n..2n-1), same layout (the strings
+ * that the Gaussian elimination of Sec. 2.3.1 produces, kept up to date instead). */
 int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
-/* Bond dimensions chi[0..n-2] (bond j joins qudits j and j+1). */
+/* Bond dimensions chi[0..n-2] of the MPS (Sec. 2.4; bond j joins qudits j and j+1). */
 int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi);
-/* Schmidt values of bond `bond` (count <= chi of that bond), sorted descending. */
+/* Schmidt values of bond `bond` (Sec. 2.4; count <= chi of that bond), sorted descending. */
 int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count);
-/* Tensor of MPS site j: dims[0..2] = (chi_l, d, chi_r); if t is not NULL it receives the
+/* Tensor of MPS site j (Sec. 2.4, Eq. mps): dims[0..2] = (chi_l, d, chi_r); if t is not NULL it receives the
  * chi_l d chi_r complex entries (interleaved re, im; row-major over (a, s, b)); cap = capacity of t
  * in complex entries (EINVAL if too small). */
 int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, int32_t* dims);
-/* Weyl string P = C^dag Z_k C of the last non-Clifford gate: x[n], z[n], r. */
+/* Weyl string P = C^dag Z_k C of the last non-Clifford gate (Sec. 2.3.1, Sec. 3): x[n], z[n], r. */
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
+/* Counters of circuit `circuit` (gcamps_stats; no counterpart in the paper). */
 int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
-/* Scores of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
+/* Scores (Sec. 3) of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
  * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact
  * one with eta < 3 (d^3 + 6 d + max side) 2^-24), vn[k] (von Neumann entropy, valid where
  * evaluated[k] = 1 except for classes scored by Renyi-2 alone under score_kind 1, which read NaN;
  * the bounds excluded the others);
  * K = gcamps_num_candidates(d) entries each; any pointer may be NULL. */
 int gcamps_get_last_scores(gcamps_t* h, int circuit, double* s2, double* vn, uint8_t* evaluated);
-/* Two-site tensor scored at the last bond visit: shape[0..1] = (chi_l, chi_r); theta receives the
+/* Two-site tensor theta scored at the last bond visit (Sec. 3): shape[0..1] = (chi_l, chi_r); theta receives the
  * chi_l d d chi_r complex entries (interleaved re, im) when that count is at most 729 (larger
  * tensors are not kept). */
 int gcamps_get_last_theta(gcamps_t* h, int circuit, double* theta, int32_t* shape);
-/* Disentangler decisions of the circuit since the last reset: (bond, class index) per bond
+/* Disentangler decisions (Sec. 3, each folded as C~ = C Q^dag) of the circuit since the last reset: (bond, class index) per bond
  * visit, in visit order; class 0 = nothing applied.  *count receives the total number
  * recorded; at most cap pairs are copied. */
 int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, int32_t* count);
@@ -303,11 +313,15 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
 int gcamps_score_theta_noalloc(int d, int chi_l, int chi_r, const double* theta_dev, double* s2_dev,
                                double* vn_dev, int32_t* choice_dev, double tie_tol, void* cuda_stream);
 
-/* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded. */
+/* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded.  No
+ * counterpart in the paper. */
 int gcamps_sync(gcamps_t* h);
-/* Back to |0...0>, C = I, counters and decisions cleared, for every circuit (enqueued on the
- * handle's stream; asynchronous). */
+/* Back to |0...0>, C = I (the initial state of Sec. 2.2), counters and decisions cleared, for every
+ * circuit (enqueued on the handle's stream; asynchronous). */
 int gcamps_reset(gcamps_t* h);
+/* Message of the handle's most recent failed call ("" if none has failed, "null handle" for NULL);
+ * owned by the handle, valid until its next failing call or gcamps_destroy.  No counterpart in the
+ * paper. */
 const char* gcamps_last_error(gcamps_t* h);
 
 #ifdef __cplusplus
