@@ -156,6 +156,7 @@ int gcamps_named_images(int d, int gate, int32_t* img, int32_t* nq);
  * options, or when a matrix of the engine would exceed 2^31 - 1 entries: the two-site tensor after
  * the MPO, (d c) x (d c) with c = d min(chi_max, d^min(b, n-b)) the largest bond capacity. */
 int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
+/* `batch` independent circuits of the same n (Sec. 2.4 layout each, as above). */
 int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 /* Batch of circuits with their own qudit counts n[c] (2 <= n[c] <= 128), for many independent
  * circuits of uneven size in one engine launch (gcamps_run with per-circuit op ranges).  Memory is
@@ -165,7 +166,7 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
 int gcamps_create_batch_uneven(int batch, const int32_t* n, int d, int chi_max, const gcamps_opts* o,
                                gcamps_t** out);
 /* Waits for the handle's work, then frees it, its device memory and the stream it created (not a
- * caller's stream); NULL is ignored. */
+ * caller's stream); NULL is ignored.  No counterpart in the paper. */
 void gcamps_destroy(gcamps_t* h);
 /* Qudits of circuit `circuit` (-1 for a bad handle or index).  No counterpart in the paper. */
 int gcamps_num_qudits(gcamps_t* h, int circuit);
@@ -202,7 +203,7 @@ int gcamps_disentangle(gcamps_t* h, gcamps_stats* st);
  * NULL begin = all ops on every circuit).  One kernel launch for the whole list; asynchronous.
  * EINVAL (nothing enqueued) for a bad op or bad offsets. */
 int gcamps_run(gcamps_t* h, const gcamps_op* ops, int nops, const int32_t* begin);
-/* Same, with `ops_dev` and `begin_dev` already in device memory (no host-to-device copy; the ops
+/* gcamps_run (Fig. 3, Sec. 3) with `ops_dev` and `begin_dev` already in device memory (no host-to-device copy; the ops
  * are not validated, so they must have passed through gcamps_run's checks before). */
 int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begin_dev);
 

@@ -40,6 +40,21 @@ def test_exports_match_header(lib):
     assert sorted(EXPORTS) == names
 
 
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's comment names the passage of the paper it implements (Sec., Eq., Table, Fig.)
+    or says that the paper has no counterpart."""
+    with open(os.path.join(ROOT, "include", "gcamps.h")) as fh:
+        src = fh.read()
+    decl = re.compile(r"^(?:int|void|const char\*|int64_t)\s+\**(gcamps_[a-z0-9_]+)\s*\([^;]*\);", re.M)
+    prev, missing = 0, []
+    for m in decl.finditer(src):
+        block = src[prev:m.start()]
+        prev = m.end()
+        if not any(t in block for t in ("Sec.", "Eq.", "Table", "Fig.", "counterpart")):
+            missing.append(m.group(1))
+    assert not missing
+
+
 def test_num_candidates(lib):
     assert lib.gcamps_num_candidates(2) == 20
     assert lib.gcamps_num_candidates(3) == 90
