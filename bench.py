@@ -83,6 +83,17 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, device=None) -> float:
+    """Sum of a per-rank count over all ranks (the value itself for one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def aggregate_rate(units_per_rank_step: float, steps: int, world: int, max_time_s: float) -> float:
     """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
     return units_per_rank_step * steps * world / max_time_s
@@ -265,6 +276,23 @@ def run_batched_reference(args):
     return 0
 
 
+def init_ranks():
+    """Process group for N > 1 (NCCL with a GPU, else gloo); returns (rank, world, local)."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def finish_ranks():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
 def run_batched(args):
     """The batched form: 256 independent qutrit circuits of uneven size (n and layers uniform in
     [16, 48], n T gates each, chi_max = 128) in one handle; every step is one reset and one engine
@@ -389,7 +417,7 @@ def run_gradient(args):
     import numpy as np
     import torch
     from synth import param_phase_circuit
-    rank, world, local = dist_env()
+    rank, world, local = init_ranks()
     torch.cuda.set_device(local)
     from paper_2511_06672_gb300.build import build_library
     build_library()
@@ -421,10 +449,11 @@ def run_gradient(args):
         if not exact:
             break
     st = sim.stats()
-    total = sum(fwd) + sum(bwd)
+    total = max_over_ranks(sum(fwd) + sum(bwd), device=f"cuda:{local}")
     line = {
-        "metric": "gradients/s", "value": len(fwd) / total if exact and total > 0 else None, "unit": "gradients/s",
-        "n_gpus": 1, "steps": len(fwd), "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(fwd)),
+        "metric": "gradients/s", "value": aggregate_rate(1, len(fwd), world, total) if exact and total > 0 else None,
+        "unit": "gradients/s",
+        "n_gpus": world, "steps": len(fwd), "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(fwd)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "gcamps-gradient-qutrit-n24-L20-48params-chi256", "observable": "Re<Z_0 Z_12>",
                    "timing": "host wall clock around synchronising calls"},
@@ -432,8 +461,10 @@ def run_gradient(args):
         "value_re": val, "exact": exact, "error": err, "max_chi": st["max_chi"],
         "forward_discarded_weight": st["discarded_weight"],
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     sim.close()
+    finish_ranks()
     return 0
 
 
@@ -480,7 +511,7 @@ def run_chi_layers(args):
     truncation by the bond cap) and cutoff 1e-12.  value = T gates / host wall time over all curves."""
     import torch
     from synth import layered_t_circuit
-    rank, world, local = dist_env()
+    rank, world, local = init_ranks()
     torch.cuda.set_device(local)
     from paper_2511_06672_gb300.build import build_library
     build_library()
@@ -498,9 +529,10 @@ def run_chi_layers(args):
         total_t += len(dims)
         total_s += sum(secs)
         progress(f"chi-layers d={d} n={n}: {len(dims)} layers in {sum(secs):.2f} s")
-    t_max = max_over_ranks(total_s)
+    t_max = max_over_ranks(total_s, device=f"cuda:{local}")
+    units = sum_over_ranks(total_t, device=f"cuda:{local}")   # ranks may stop at different layers
     line = {
-        "metric": METRIC, "value": aggregate_rate(total_t, 1, world, t_max) if t_max > 0 else None,
+        "metric": METRIC, "value": units / t_max if t_max > 0 else None,
         "unit": "T-gates/s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF,
@@ -509,6 +541,7 @@ def run_chi_layers(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    finish_ranks()
     return 0
 
 

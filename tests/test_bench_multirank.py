@@ -19,13 +19,16 @@ def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       LOCAL_RANK=str(rank))
     import bench
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.init_ranks()                                 # gloo here: no GPU
+    assert dist.is_initialized() and dist.get_backend() == "gloo"
     try:
         r, w, local = bench.dist_env()
         t = bench.max_over_ranks(1.5 + rank)          # rank 0 took 1.5 s, rank 1 took 2.5 s
-        out[rank] = (r, w, local, t, tuple(bench.rank_seeds(r)))
+        units = bench.sum_over_ranks(3.0 + rank)      # rank 0 did 3 units, rank 1 did 4
+        out[rank] = (r, w, local, t, tuple(bench.rank_seeds(r)), units)
     finally:
-        dist.destroy_process_group()
+        bench.finish_ranks()
+        assert not dist.is_initialized()
 
 
 def test_two_gloo_ranks_reduce_the_step_time_and_split_the_seeds():
@@ -35,9 +38,10 @@ def test_two_gloo_ranks_reduce_the_step_time_and_split_the_seeds():
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
     assert sorted(res) == [0, 1]
-    for rank, (r, w, local, t, seeds) in res.items():
+    for rank, (r, w, local, t, seeds, units) in res.items():
         assert (r, w, local) == (rank, world, rank)
         assert t == pytest.approx(2.5)                  # max over ranks
+        assert units == pytest.approx(7.0)              # sum over ranks
     assert not set(res[0][4]) & set(res[1][4])          # each rank its own circuits
     import bench
     assert bench.aggregate_rate(512, 5, world, 2.5) == pytest.approx(512 * 5 * 2 / 2.5)
@@ -46,6 +50,7 @@ def test_two_gloo_ranks_reduce_the_step_time_and_split_the_seeds():
 def test_single_process_is_unchanged():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
+    assert bench.sum_over_ranks(3.25) == 3.25
     assert bench.rank_seeds(0) == list(range(1, bench.SEEDS_PER_D + 1))
 
 
