@@ -768,6 +768,8 @@ def main():
     progress(f"timed steps: {[round(t, 3) for t in times]}")
     # end to end: host gate lists, copies and readback inside the timed region
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     e2e_times = []
     h2d = sum(ops_host[d][0].nbytes + ops_host[d][1].nbytes for d in (2, 3))
     d2h = 0
@@ -782,7 +784,8 @@ def main():
                 res.append(sims[d].bond_dims(c))
         e2e_times.append(time.perf_counter() - t0)
         d2h = sum(len(r) * 4 for r in res)
-    e2e_value = tg_per_step * world / (sum(e2e_times) / len(e2e_times))
+    e2e_total = max_over_ranks(sum(e2e_times), device=f"cuda:{local}")   # slowest rank, as for value
+    e2e_value = aggregate_rate(tg_per_step, len(e2e_times), world, e2e_total)
 
     line = {
         "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": world, "steps": args.steps,
