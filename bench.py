@@ -522,7 +522,8 @@ def run_chi_layers(args):
         starts = [0] + ends[:-1]
         layer_ops = [G.ops_from_gates(gates[a:b], d) for a, b in zip(starts, ends)]
         csize = args.cluster_qutrit if d == 3 else args.cluster_qubit
-        sim = G.Simulator(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF, cluster_size=csize or args.cluster)
+        sim = G.Simulator(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF, cluster_size=csize or args.cluster,
+                          score_kind=args.chi_layers_score_kind)
         dims, secs = bond_dims_per_layer(layer_ops, sim.run, sim.bond_dims, args.chi_layers_budget_s)
         sim.close()
         curves.append(_curve_entry(d, n, layers, dims, secs))
@@ -536,6 +537,7 @@ def run_chi_layers(args):
         "unit": "T-gates/s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF,
+                   "score_kind": args.chi_layers_score_kind,
                    "timing": "host wall clock around one synchronising launch per layer"},
         "curves": curves,
     }
@@ -558,7 +560,7 @@ def run_chi_layers_reference(args):
     for d, n, layers in chi_layer_shapes(args):
         gates, ends = layered_t_circuit(n, d, layers, 1)
         starts = [0] + ends[:-1]
-        ref = GCAMPS(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF)
+        ref = GCAMPS(n, d, chi_max=d ** (n // 2), cutoff=CUTOFF, score_kind=args.chi_layers_score_kind)
 
         def run_layer(gs, ref=ref):
             for gt in gs:
@@ -576,7 +578,8 @@ def run_chi_layers_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": args.gpus,
         "steps": 1, "warmup": 0, "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF},
+        "config": {"workload": "gcamps-fig4-layers-T-on-qudit-0", "chi_max": "d^floor(n/2)", "cutoff": CUTOFF,
+                   "score_kind": args.chi_layers_score_kind},
         "cpu_baseline": {"value": value, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
                          "sample": f"layers until {args.chi_layers_budget_s} s per curve"},
         "e2e": {"value": value, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -628,6 +631,8 @@ def main():
     ap.add_argument("--chi-layers-n", default="6,8")
     ap.add_argument("--chi-layers-factor", type=int, default=2, help="layers = this x n")
     ap.add_argument("--chi-layers-budget-s", type=float, default=60.0, help="per curve; later layers are skipped")
+    ap.add_argument("--chi-layers-score-kind", type=int, default=0, choices=[0, 1, 2],
+                    help="disentangler score: 0 von Neumann, 1 Renyi-2, 2 weight rank (bond-dimension criterion)")
     ap.add_argument("--batched-count", type=int, default=64)
     ap.add_argument("--batched-nmax", type=int, default=24, help="n and layers uniform in [16, this]")
     ap.add_argument("--batched-clusters", default="8,4", help="CTAs per circuit tried by the autotuner")

@@ -93,11 +93,13 @@ def test_reference_arm_prints_the_curves():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
-                          "chi-layers", "--chi-layers-d", "2,3", "--chi-layers-n", "4", "--chi-layers-factor", "1"],
+                          "chi-layers", "--chi-layers-d", "2,3", "--chi-layers-n", "4", "--chi-layers-factor", "1",
+                          "--chi-layers-score-kind", "2"],
                          capture_output=True, text=True, timeout=300, cwd=root)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "T-gates/s" and line["value"] > 0
+    assert line["config"]["score_kind"] == 2
     assert [(c["d"], c["n"], c["layers_run"]) for c in line["curves"]] == [(2, 4, 4), (3, 4, 4)]
     for c in line["curves"]:
         assert len(c["scaled_max_chi"]) == len(c["max_chi"]) == 4
