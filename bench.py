@@ -589,6 +589,41 @@ def run_chi_layers_reference(args):
     return 0
 
 
+def run_case(args):
+    """One seeded benchmark-family circuit (or a batch of consecutive seeds), reset and run in one engine
+    launch per repetition: for profiling one launch (ncu) and for the per-phase cycle profile of the
+    engine.  Prints one JSON line per repetition."""
+    import numpy as np
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    from synth import brickwork_circuit
+    ops, begin = [], [0]
+    for b in range(args.case_batch):
+        o = G.ops_from_gates(brickwork_circuit(args.case_n, args.case_d, args.case_layers, args.case_t,
+                                               args.case_seed + b), args.case_d)
+        ops.append(o)
+        begin.append(begin[-1] + len(o))
+    ops = np.concatenate(ops)
+    sim = G.Simulator(args.case_n, args.case_d, chi_max=args.case_chi, cutoff=CUTOFF, batch=args.case_batch,
+                      cluster_size=args.cluster)
+    for r in range(args.case_repeat):
+        sim.reset()
+        t0 = time.perf_counter()
+        sim.run(ops, np.array(begin, dtype=np.int32))
+        sim.sync()
+        el = time.perf_counter() - t0
+        st = [sim.stats(c) for c in range(args.case_batch)]
+        line = {"workload": "case", "rep": r, "seconds": el, "d": args.case_d, "n": args.case_n,
+                "layers": args.case_layers, "t_gates": args.case_t, "chi_max": args.case_chi,
+                "seed": args.case_seed, "batch": args.case_batch, "cluster": args.cluster,
+                "stats": st[0] if args.case_batch == 1 else st,
+                "profile": [sim.profile(c) for c in range(args.case_batch)]}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -624,9 +659,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
-    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient", "chi-layers"],
+    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient", "chi-layers", "case"],
                     help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch; "
-                         "gradient: forward + adjoint; chi-layers: bond dimension after every layer (Fig. 5a)")
+                         "gradient: forward + adjoint; chi-layers: bond dimension after every layer (Fig. 5a); "
+                         "case: one seeded circuit per launch with its engine profile (for ncu)")
+    ap.add_argument("--case-d", type=int, default=3)
+    ap.add_argument("--case-n", type=int, default=12)
+    ap.add_argument("--case-layers", type=int, default=10)
+    ap.add_argument("--case-t", type=int, default=12)
+    ap.add_argument("--case-chi", type=int, default=64)
+    ap.add_argument("--case-seed", type=int, default=1)
+    ap.add_argument("--case-batch", type=int, default=1)
+    ap.add_argument("--case-repeat", type=int, default=2)
     ap.add_argument("--chi-layers-d", default="2,3")
     ap.add_argument("--chi-layers-n", default="6,8")
     ap.add_argument("--chi-layers-factor", type=int, default=2, help="layers = this x n")
@@ -654,6 +698,8 @@ def main():
                       flush=True)
             return 0
         return run_reference(args)
+    if args.workload == "case":
+        return run_case(args)
     if args.workload == "chi-layers":
         return run_chi_layers(args)
     if args.workload == "batched":

@@ -29,8 +29,8 @@
  * inside a kernel, or GCAMPS_ECHI) is reported by the next call that synchronises
  * (gcamps_sync and every getter).  After EINVAL or ENOCONV the handle stays valid.
  */
-#ifndef GCAMPS_H
-#define GCAMPS_H
+#ifndef GCAMPS_H_INCLUDED
+#define GCAMPS_H_INCLUDED
 
 #include <stdint.h>
 
@@ -60,8 +60,9 @@ typedef struct {
                        /*     broken by the von Neumann entropy                               */
   int precision;       /* 0 = FP64 everywhere (only mode now)                                  */
   double tie_tol;      /* accept Q only if S(Q) < S(I) - tie_tol; ties -> lowest index (1e-10) */
-  double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
+  /* The fields above are the contract's options, in its order; the ones below extend it.           */
+  double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
   int cluster_size;    /* CTAs (one thread-block cluster) per circuit: 1, 2, 4, 8 or 16; 0 = 8   */
   int64_t snapshot_entries;   /* per circuit: complex entries of the arena that keeps the MPS  */
                               /* after every non-Clifford gate for gcamps_expect_gradient    */
@@ -143,6 +144,12 @@ int gcamps_candidate(int d, int k, int32_t* img, double* u);
 #define GCAMPS_GATE_SUM 3
 #define GCAMPS_GATE_X 4
 #define GCAMPS_GATE_Z 5
+/* The same gate codes under the short names gcamps_apply_named is documented with. */
+#define GCAMPS_H GCAMPS_GATE_H
+#define GCAMPS_S GCAMPS_GATE_S
+#define GCAMPS_SUM GCAMPS_GATE_SUM
+#define GCAMPS_X GCAMPS_GATE_X
+#define GCAMPS_Z GCAMPS_GATE_Z
 /* Host-only (no GPU needed): generator images of a named gate, in the layout of
  * gcamps_apply_clifford (img: 6 ints for a one-qudit gate, 20 for SUM; the caller's buffer holds
  * at least that many).  *nq (may be NULL) receives the gate's qudit count.  EINVAL for an unknown
@@ -158,6 +165,9 @@ int gcamps_named_images(int d, int gate, int32_t* img, int32_t* nq);
 int gcamps_create(int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 /* `batch` independent circuits of the same n (Sec. 2.4 layout each, as above). */
 int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
+/* gcamps_batch_create(count, n[], d, chi_max, o, out): the batched form's constructor, the same call as
+ * gcamps_create_batch_uneven below (circuits with their own qudit counts, no counterpart in the paper). */
+int gcamps_batch_create(int count, const int32_t* n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out);
 /* Batch of circuits with their own qudit counts n[c] (2 <= n[c] <= 128), for many independent
  * circuits of uneven size in one engine launch (gcamps_run with per-circuit op ranges).  Memory is
  * reserved per circuit for its own n[c]; calls that apply to every circuit (apply_*, disentangle)
@@ -209,9 +219,11 @@ int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begi
 
 /* <psi| W |psi> for W = (x)_j X_j^{x_j} Z_j^{z_j} (phase 1), as C^dag W C is a product of inverse
  * tableau rows and <MPS|.|MPS> a transfer-matrix contraction (Sec. 3).  O_sigma of Sec. 3 is
- * the real part.  circuit selects the batch entry. */
-int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z,
-                       double* re, double* im);
+ * the real part.  x, z: n exponents each (0..d-1).  The handle's circuit 0 (the only one of a handle
+ * from gcamps_create); gcamps_batch_expect_weyl takes the batch entry `circuit`.  Synchronising. */
+int gcamps_expect_weyl(gcamps_t* h, const int32_t* x, const int32_t* z, double* re, double* im);
+/* The same readout for batch entry `circuit` (Sec. 3). */
+int gcamps_batch_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* re, double* im);
 
 /* Phase gradient of O = Re <psi| W |psi> = <psi| (W + W^dag)/2 |psi>, W = (x)_j X_j^{x_j} Z_j^{z_j},
  * with respect to the phases of every non-Clifford gate k applied since the last reset
@@ -233,17 +245,26 @@ int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int
  * images has no defined phase): C|y> = prod_j D_j^{y_j} C|0>, with C|0> the common +1
  * eigenvector of the stabilizer rows.  re/im: d^n doubles each. */
 int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im);
-/* One amplitude <s|C|MPS> (Sec. 3) with the same global-phase convention (d^n <= 2^20). */
-int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im);
+/* One amplitude <s|C|MPS> (Sec. 3) with the same global-phase convention (d^n <= 2^20); digits: n values in
+ * 0..d-1 (qudit 0 first).  Circuit 0 (gcamps_amplitude) or batch entry `circuit` (gcamps_batch_amplitude). */
+int gcamps_amplitude(gcamps_t* h, const int32_t* digits, double* re, double* im);
+/* The same readout for batch entry `circuit` (Sec. 3). */
+int gcamps_batch_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im);
 
 /* Tableau of C (Sec. 2.2, Sec. 2.3): exps[2n][2n] (row-major; rows 0..n-1 = C Z_j C^dag, rows n..2n-1 = C X_j C^dag;
- * columns x_0..x_{n-1} | z_0..z_{n-1}) and phase[2n] (mod 2d, units of tau). */
-int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
+ * columns x_0..x_{n-1} | z_0..z_{n-1}) and phase[2n] (mod 2d, units of tau); either may be NULL.  Circuit 0
+ * (gcamps_get_tableau) or batch entry `circuit` (gcamps_batch_get_tableau). */
+int gcamps_get_tableau(gcamps_t* h, uint8_t* exps, uint8_t* phase);
+/* The same readout for batch entry `circuit` (Sec. 2.2, Sec. 2.3). */
+int gcamps_batch_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
 /* Inverse tableau: rows C^dag Z_j C (0..n-1) and C^dag X_j C (n..2n-1), same layout (the strings
  * that the Gaussian elimination of Sec. 2.3.1 produces, kept up to date instead). */
 int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase);
-/* Bond dimensions chi[0..n-2] of the MPS (Sec. 2.4; bond j joins qudits j and j+1). */
-int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi);
+/* Bond dimensions chi[0..n-2] of the MPS (Sec. 2.4; bond j joins qudits j and j+1).  Circuit 0
+ * (gcamps_get_bond_dims) or batch entry `circuit` (gcamps_batch_get_bond_dims). */
+int gcamps_get_bond_dims(gcamps_t* h, int32_t* chi);
+/* The same readout for batch entry `circuit` (Sec. 2.4). */
+int gcamps_batch_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi);
 /* Schmidt values of bond `bond` (Sec. 2.4; count <= chi of that bond), sorted descending. */
 int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count);
 /* Tensor of MPS site j (Sec. 2.4, Eq. mps): dims[0..2] = (chi_l, d, chi_r); if t is not NULL it receives the
@@ -254,6 +275,21 @@ int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, 
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
 /* Counters of circuit `circuit` (gcamps_stats; no counterpart in the paper). */
 int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
+/* Where the engine's time went for circuit `circuit` since creation (or gcamps_reset): no counterpart in
+ * the paper, a measurement aid.  out receives min(cap, GCAMPS_PROF_WORDS) int64 words (*count, may be NULL,
+ * receives GCAMPS_PROF_WORDS), all SM clock cycles (clock64) of the circuit's leader CTA, whose intervals
+ * include its waits at the cluster's barriers, so the phases add up to the launch's time on that circuit:
+ *   [0] Clifford tableau updates          [1] non-Clifford steps (MPO apply and recompression)
+ *   [2] centre moves before a sweep       [3] forming theta at a bond visit
+ *   [4] FP32 Renyi-2 screen of every class [5] FP32 von Neumann estimates (their bounds)
+ *   [6] exact FP64 class evaluations       [7] the decision
+ *   [8] applying the chosen class and folding it into the tableau
+ *   [9] truncated SVD splits               [10] QR centre moves after a visit that applies nothing
+ *   [12 + b] bond visits, [17 + b] their cycles, [22 + b] their exact evaluations, [27 + b] their FP32
+ *   von Neumann estimates, for the visit size buckets b = 0..4 of m = min(chi_l d, d chi_r): m <= 9, <= 27,
+ *   <= 54, <= 81, larger.  Words 11 and 31 are zero. */
+#define GCAMPS_PROF_WORDS 32
+int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count);
 /* Scores (Sec. 3) of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
  * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact
  * one with eta < 3 (d^3 + 6 d + max side) 2^-24), vn[k] (von Neumann entropy, valid where
@@ -280,6 +316,16 @@ int gcamps_get_decisions(gcamps_t* h, int circuit, int32_t* pairs, int32_t cap, 
 int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* s2, double* vn,
                        int32_t* choice);
 
+/* FP32 estimates of the von Neumann entropy (Sec. 3 score) of every class on a given two-site tensor, with
+ * the error bound the disentangler prunes with: theta' = Q_k theta and its Gram in FP32, scaled to unit
+ * trace, reduced to a tridiagonal by FP32 Householder reflections, eigenvalues by FP32 multisection;
+ * |est[k] - S_vN(Q_k theta)| <= bound[k] (bound[k] = 1e300 where it carries no information: large Grams,
+ * or a trace outside 1e-12 .. 1e12).  The bound is twice the Fannes-Audenaert bound of a trace distance
+ * T = sqrt(m) (eta + u + 2 m^2 u (1 + eta)) + 9 m u (u = 2^-24; eta the FP32 Gram error of the screen;
+ * 2 m^2 u |G|_F the backward error of the FP32 reduction).  theta as for gcamps_score_theta (host memory);
+ * est, bound: K doubles each.  Synchronising. */
+int gcamps_estimate_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* est, double* bound);
+
 /* The class scores of gcamps_score_theta for callers that cannot allocate device memory: code
  * whose GPU memory belongs to another allocator (a framework's memory pool that has already
  * reserved the device, or a fixed per-process memory budget), and latency-critical loops that
@@ -295,8 +341,9 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
  * Every pointer is device memory of the current device, owned by the caller.  theta_dev: chi_l x d
  * x d x chi_r complex entries (interleaved re, im; row-major over (a, s, t, b)).  s2_dev, vn_dev:
  * K = gcamps_num_candidates(d) doubles each, the Renyi-2 and von Neumann entropies of every class
- * as in gcamps_score_theta.  choice_dev: 3 int32, the class the disentangler would apply (0 = none;
- * a class is applied only if it lowers the entropy by more than tie_tol, ties to the lowest index),
+ * as in gcamps_score_theta.  choice_dev: 3 int32, the class the von Neumann disentangler (score_kind 0,
+ * rank threshold of cutoff 0) would apply (0 = none; a class is applied only if it lowers the entropy by
+ * more than tie_tol, ties to the lowest index; handles made with score_kind 1 or 2 can choose otherwise),
  * the number of exact entropies its Renyi-2 pruning evaluated, and the device status of the call
  * (0 or a GCAMPS_E* code; the eigenvalue search runs a fixed number of steps, so 0 in practice).  cuda_stream: the cudaStream_t
  * to run on, NULL for the default stream.  Asynchronous: the outputs are valid once the stream has
@@ -328,4 +375,4 @@ const char* gcamps_last_error(gcamps_t* h);
 #ifdef __cplusplus
 }
 #endif
-#endif /* GCAMPS_H */
+#endif /* GCAMPS_H_INCLUDED */

@@ -82,6 +82,18 @@ def score_theta_noalloc(d: int, chi_l: int, chi_r: int, theta_dev, s2_dev, vn_de
     addresses: theta (chi_l, d, d, chi_r) complex128, s2 and vn K float64, choice 3 int32.  stream:
     a torch.cuda.Stream, a raw cudaStream_t, or None (default stream).  Asynchronous."""
     lib = N.load()
+    K = num_candidates(d)
+    # shapes beyond the static limit are left to the library, which refuses them (ESIZE) before any launch
+    if K > 0 and 1 <= chi_l <= N.NOALLOC_MAX_SIDE // d and 1 <= chi_r <= N.NOALLOC_MAX_SIDE // d:
+        # torch tensors are checked against the shapes the call reads and writes (raw addresses are not)
+        import torch
+        for name, t, dtype, numel in (("theta", theta_dev, torch.complex128, chi_l * d * d * chi_r),
+                                      ("s2", s2_dev, torch.float64, K), ("vn", vn_dev, torch.float64, K),
+                                      ("choice", choice_dev, torch.int32, 3)):
+            if isinstance(t, torch.Tensor):
+                if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+                    raise GcampsError(N.EINVAL, f"score_theta_noalloc: {name} must be a contiguous CUDA {dtype} "
+                                                f"tensor of at least {numel} elements")
     st = getattr(stream, "cuda_stream", stream) or None
     rc = lib.gcamps_score_theta_noalloc(d, chi_l, chi_r, _dev_ptr(theta_dev), _dev_ptr(s2_dev), _dev_ptr(vn_dev),
                                         _dev_ptr(choice_dev), float(tie_tol), st)
@@ -226,7 +238,7 @@ class Simulator:
         xa = np.ascontiguousarray(x, dtype=np.int32)
         za = np.ascontiguousarray(z, dtype=np.int32)
         re, im = C.c_double(), C.c_double()
-        self._c(self._lib.gcamps_expect_weyl(self._h, circuit, N.ptr(xa, C.c_int32), N.ptr(za, C.c_int32),
+        self._c(self._lib.gcamps_batch_expect_weyl(self._h, circuit, N.ptr(xa, C.c_int32), N.ptr(za, C.c_int32),
                                              C.byref(re), C.byref(im)))
         return complex(re.value, im.value)
 
@@ -251,14 +263,14 @@ class Simulator:
     def amplitude(self, digits, circuit: int = 0) -> complex:
         a = np.ascontiguousarray(digits, dtype=np.int32)
         re, im = C.c_double(), C.c_double()
-        self._c(self._lib.gcamps_amplitude(self._h, circuit, N.ptr(a, C.c_int32), C.byref(re), C.byref(im)))
+        self._c(self._lib.gcamps_batch_amplitude(self._h, circuit, N.ptr(a, C.c_int32), C.byref(re), C.byref(im)))
         return complex(re.value, im.value)
 
     def tableau(self, circuit: int = 0):
         n = self.nq[circuit]
         e = np.zeros((2 * n, 2 * n), dtype=np.uint8)
         p = np.zeros(2 * n, dtype=np.uint8)
-        self._c(self._lib.gcamps_get_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
+        self._c(self._lib.gcamps_batch_get_tableau(self._h, circuit, N.ptr(e, C.c_uint8), N.ptr(p, C.c_uint8)))
         return e, p
 
     def inverse_tableau(self, circuit: int = 0):
@@ -270,7 +282,7 @@ class Simulator:
 
     def bond_dims(self, circuit: int = 0) -> list:
         a = np.zeros(self.nq[circuit] - 1, dtype=np.int32)
-        self._c(self._lib.gcamps_get_bond_dims(self._h, circuit, N.ptr(a, C.c_int32)))
+        self._c(self._lib.gcamps_batch_get_bond_dims(self._h, circuit, N.ptr(a, C.c_int32)))
         return a.tolist()
 
     def schmidt_values(self, bond: int, circuit: int = 0) -> np.ndarray:
@@ -301,6 +313,19 @@ class Simulator:
         self._c(self._lib.gcamps_get_stats(self._h, circuit, C.byref(st)))
         return st.as_dict()
 
+    def profile(self, circuit: int = 0) -> dict:
+        """Leader-CTA cycles per engine phase and per bond-visit size bucket since the last reset
+        (gcamps_get_profile)."""
+        p = np.zeros(N.PROF_WORDS, dtype=np.int64)
+        cnt = C.c_int32()
+        self._c(self._lib.gcamps_get_profile(self._h, circuit, p.ctypes.data_as(C.POINTER(C.c_int64)), N.PROF_WORDS,
+                                             C.byref(cnt)))
+        out = {"cycles": {k: int(p[i]) for i, k in enumerate(N.PROF_PHASES)}, "buckets": {}}
+        for b, name in enumerate(N.PROF_BUCKETS):
+            out["buckets"][name] = {"visits": int(p[12 + b]), "cycles": int(p[17 + b]), "exact": int(p[22 + b]),
+                                    "estimates": int(p[27 + b])}
+        return out
+
     def score_theta(self, theta: np.ndarray):
         """(S2, S_vN, chosen class, exact evaluations) for theta of shape (chi_l, d, d, chi_r)."""
         t = np.ascontiguousarray(theta, dtype=np.complex128)
@@ -311,6 +336,16 @@ class Simulator:
         self._c(self._lib.gcamps_score_theta(self._h, cl, cr, t.ctypes.data_as(C.POINTER(C.c_double)),
                                              N.ptr(s2, C.c_double), N.ptr(vn, C.c_double), N.ptr(ch, C.c_int32)))
         return s2, vn, int(ch[0]), int(ch[1])
+
+    def estimate_theta(self, theta: np.ndarray):
+        """(FP32 von Neumann estimate, its error bound) of every class for theta (chi_l, d, d, chi_r)."""
+        t = np.ascontiguousarray(theta, dtype=np.complex128)
+        cl, cr = t.shape[0], t.shape[3]
+        est = np.zeros(self._lib.gcamps_num_candidates(self.d))
+        bd = np.zeros_like(est)
+        self._c(self._lib.gcamps_estimate_theta(self._h, cl, cr, t.ctypes.data_as(C.POINTER(C.c_double)),
+                                                N.ptr(est, C.c_double), N.ptr(bd, C.c_double)))
+        return est, bd
 
     def last_scores(self, circuit: int = 0):
         """(S2, S_vN, evaluated) of every class at the last disentangler bond visit."""

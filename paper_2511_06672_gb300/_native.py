@@ -10,6 +10,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libg
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE, ESNAP = 0, 1, 2, 3, 4, 5, 6, 7
 NOALLOC_MAX_SIDE = 81
+PROF_WORDS = 32
+PROF_PHASES = ("clifford", "mpo", "center", "theta", "screen", "vn_estimate", "exact", "decide", "apply_q", "split",
+               "qr_move")
+PROF_BUCKETS = ("m<=9", "m<=27", "m<=54", "m<=81", "m>81")
 OP_CLIFFORD, OP_NONCLIFFORD, OP_DISENTANGLE = 1, 2, 3
 GATE_H, GATE_S, GATE_SUM, GATE_X, GATE_Z = 1, 2, 3, 4, 5
 
@@ -20,8 +24,8 @@ assert OP_DTYPE.itemsize == 128
 
 class Opts(C.Structure):
     _fields_ = [("cutoff", C.c_double), ("max_sweeps", C.c_int), ("score_kind", C.c_int),
-                ("precision", C.c_int), ("tie_tol", C.c_double), ("strict_weight", C.c_double),
-                ("cuda_stream", C.c_void_p), ("cluster_size", C.c_int),
+                ("precision", C.c_int), ("tie_tol", C.c_double), ("cuda_stream", C.c_void_p),
+                ("strict_weight", C.c_double), ("cluster_size", C.c_int),
                 ("snapshot_entries", C.c_int64), ("snapshot_max_gates", C.c_int32)]
 
 
@@ -41,13 +45,14 @@ EXPORTS = [
     "gcamps_default_opts", "gcamps_num_candidates", "gcamps_sp4_images", "gcamps_candidate",
     "gcamps_named_images", "gcamps_apply_named",
     "gcamps_create",
-    "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_destroy", "gcamps_num_qudits",
+    "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_batch_create",
+    "gcamps_batch_expect_weyl", "gcamps_batch_amplitude", "gcamps_batch_get_tableau", "gcamps_batch_get_bond_dims", "gcamps_destroy", "gcamps_num_qudits",
     "gcamps_set_cluster_size", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
     "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
-    "gcamps_get_stats",
-    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
+    "gcamps_get_stats", "gcamps_get_profile",
+    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_estimate_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
 ]
 
 _lib = None
@@ -81,19 +86,26 @@ def load(path: str = LIB_PATH):
         "gcamps_disentangle": (C.c_int, [vp, C.POINTER(Stats)]),
         "gcamps_run": (C.c_int, [vp, vp, C.c_int, i32p]),
         "gcamps_run_device": (C.c_int, [vp, vp, vp]),
-        "gcamps_expect_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, dp, dp]),
+        "gcamps_expect_weyl": (C.c_int, [vp, i32p, i32p, dp, dp]),
+        "gcamps_batch_expect_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, dp, dp]),
+        "gcamps_batch_create": (C.c_int, [C.c_int, i32p, C.c_int, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
         "gcamps_expect_gradient": (C.c_int, [vp, C.c_int, i32p, i32p, dp, dp, C.c_int32, i32p]),
         "gcamps_statevector": (C.c_int, [vp, C.c_int, dp, dp]),
-        "gcamps_amplitude": (C.c_int, [vp, C.c_int, i32p, dp, dp]),
-        "gcamps_get_tableau": (C.c_int, [vp, C.c_int, u8p, u8p]),
+        "gcamps_amplitude": (C.c_int, [vp, i32p, dp, dp]),
+        "gcamps_batch_amplitude": (C.c_int, [vp, C.c_int, i32p, dp, dp]),
+        "gcamps_get_tableau": (C.c_int, [vp, u8p, u8p]),
+        "gcamps_batch_get_tableau": (C.c_int, [vp, C.c_int, u8p, u8p]),
         "gcamps_get_inverse_tableau": (C.c_int, [vp, C.c_int, u8p, u8p]),
-        "gcamps_get_bond_dims": (C.c_int, [vp, C.c_int, i32p]),
+        "gcamps_get_bond_dims": (C.c_int, [vp, i32p]),
+        "gcamps_batch_get_bond_dims": (C.c_int, [vp, C.c_int, i32p]),
         "gcamps_get_schmidt": (C.c_int, [vp, C.c_int, C.c_int, dp, i32p]),
         "gcamps_get_site": (C.c_int, [vp, C.c_int, C.c_int, dp, C.c_int64, i32p]),
         "gcamps_get_last_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, i32p]),
         "gcamps_get_stats": (C.c_int, [vp, C.c_int, C.POINTER(Stats)]),
+        "gcamps_get_profile": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int64), C.c_int32, i32p]),
         "gcamps_get_decisions": (C.c_int, [vp, C.c_int, i32p, C.c_int32, i32p]),
         "gcamps_score_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp, i32p]),
+        "gcamps_estimate_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp]),
         "gcamps_score_theta_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_double, vp]),
         "gcamps_get_last_scores": (C.c_int, [vp, C.c_int, dp, dp, u8p]),
         "gcamps_get_last_theta": (C.c_int, [vp, C.c_int, dp, i32p]),

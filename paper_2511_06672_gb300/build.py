@@ -39,7 +39,7 @@ def build_library(verbose: bool = False, force: bool = False) -> str:
     """Compile and link libgcamps.so; returns its path.  Skips the work when the library is
     newer than every source and header."""
     srcs = _sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "gcamps.h"))
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in srcs + headers + [__file__])

@@ -1,1857 +1,12 @@
-// Device engine of libgcamps: the GCAMPS non-Clifford step (arxiv 2511.06672, Sec. 3) on sm_103a.
-//
-// One CTA runs one circuit.  A launch processes a whole gate list for every circuit of the
-// batch, so the control flow of the method (support span of the commuted Weyl string, bond
-// dimensions after truncation, the disentangler decision at every bond) stays on the device and
-// no host round trip separates two steps.
-//
-// Layout of a circuit in device memory (see gcamps_internal.h):
-//   tableau   fwd exps [2n][2n] | fwd phase [2n] | inv exps [2n][2n] | inv phase [2n]  (uint8)
-//             rows 0..n-1: C Z_j C^dag (fwd) / C^dag Z_j C (inv); rows n..2n-1: the X_j images;
-//             columns x_0..x_{n-1} | z_0..z_{n-1}; phase in units of tau = exp(i pi/d), mod 2d.
-//   MPS       site j in its own slot, compact row-major (a, s, b) with the current bond dims
-//             dims[j] x d x dims[j+1]; complex128.
-//   scratch   two-site tensor, Jacobi buffers, matmul staging, per-warp scoring buffers.
-//
-// All arithmetic on the MPS is complex128 (FP64), the precision the paper's simulator uses
-// (Sec. 4.1.2); the tableau is exact integer arithmetic mod d / mod 2d.
+// Engine launch of libgcamps (arxiv 2511.06672, Sec. 3): the gate-list kernel k_run, the reset and
+// the readout kernels (<W>, dense state vector).
 
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
-#include <math_constants.h>
-
-#include <cstdint>
-
-#include "gcamps_internal.h"
+#include "gcamps_device.cuh"
 
 namespace gcx {
 namespace {
 
-namespace cg = cooperative_groups;
-
-// Classes are scored with the Renyi-2 bound first when the Gram has more rows than this.
-constexpr int kPruneMin = 1;
-// CTA-level eigenvalue multisection keeps the tridiagonal in shared memory up to this size.
-constexpr int kBTri = 256;
-
-// (i, j), j <= i, of entry t of the row-major packed lower triangle (t = i (i + 1) / 2 + j).
-__device__ __forceinline__ void tri_index(int t, int& i, int& j) {
-  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while (r * (r + 1) / 2 > t) --r;
-  while ((r + 1) * (r + 2) / 2 <= t) ++r;
-  i = r;
-  j = t - r * (r + 1) / 2;
-}
-
-// ------------------------------------------------------------------------------ complex helpers
-__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-// acc + a * b
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(a.y, b.x, acc.y);
-  return acc;
-}
-// acc + conj(a) * b
-__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(-a.y, b.x, acc.y);
-  return acc;
-}
-__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-// FP32 complex: acc + a b and acc + a conj(b)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 acc) {
-  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
-  return acc;
-}
-__device__ __forceinline__ float2 ffmac2(float2 a, float2 b, float2 acc) {
-  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
-  acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
-  return acc;
-}
-// x / |x|, and 1 for x = 0.  A subnormal x is first scaled by 2^600 (exact): its modulus carries only
-// a few significant bits, so the plain quotient has a modulus visibly different from 1 and a
-// Householder reflector built with it is no longer unitary.
-__device__ __forceinline__ double2 unit_phase(double2 x) {
-  if (x.x == 0.0 && x.y == 0.0) return make_double2(1.0, 0.0);
-  if (fabs(x.x) < 0x1p-900 && fabs(x.y) < 0x1p-900) {
-    x.x *= 0x1p600;
-    x.y *= 0x1p600;
-  }
-  const double ax = hypot(x.x, x.y);
-  return make_double2(x.x / ax, x.y / ax);
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ int warp_sum_int(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// -------------------------------------------------------------------------- per-CTA workspace
-struct Smem {
-  uint8_t lut[81 * 5];        // conjugation table of the current two-qudit Clifford
-  int img[20];                // its generator images, 4 x (x0, z0, x1, z1, r)
-  int inv[20];                // images of its inverse
-  uint8_t src[4][2 * kMaxN];  // rows read by a row product
-  int srcr[4];
-  double s2[kMaxK];           // Renyi-2 entropy per class (cluster leader)
-  double vn[kMaxK];           // von Neumann entropy per class (cluster leader)
-  uint8_t evald[kMaxK];       // vn[k] valid
-  int list[kMaxK];            // classes to evaluate next (cluster leader)
-  int nlist;
-  int rank0;                  // numerical rank of the identity class's Gram (cluster leader; -1 = none)
-  int ord[kMaxK];             // rank of each class in ascending S2 (cluster leader)
-  double s2lo[kMaxK];         // lower bound of S2 from the FP32 screen (cluster leader)
-  int rk[kMaxK];              // weight rank of each exactly evaluated class (cluster leader)
-  double wtri[kWarps][64];    // per warp: tridiagonal diagonal [0, 32) | off-diagonal squared [32, 64)
-  float wtri32[kWarps][64];   // the same in FP32
-  double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
-  float btri32[2 * kBTri];
-  int bcast;
-  double red[kWarps * 4];
-  double2 coef[4];            // MPO term coefficients c_m tau^{...}
-  double2 tau[6];             // tau^k, k < 2d
-  int flag;
-  int ival[8];
-  double dval[4];
-};
-
-struct Ctx {
-  const Engine* e;
-  int c, n, d, K;
-  int rank, csize;            // position in the circuit's cluster; rank 0 leads
-  double2* cta;               // this CTA's scoring scratch
-  float2* th32;               // FP32 copy of the two-site tensor being scored
-  const long long* site_off;  // this circuit's slot offsets
-  const int* bond_bound;      // this circuit's Schmidt-rank bounds
-  uint8_t *fx, *fr, *ix, *ir;
-  double2* mps;
-  int* dims;
-  int* meta;
-  long long* stats;
-  double* dstats;
-  int* dec;
-  int8_t* weyl;
-  double2* scr;
-  double* sing;
-  int* perm;
-};
-
-__device__ __forceinline__ double2* site_ptr(const Ctx& C, int j) { return C.mps + C.site_off[j]; }
-
-__device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
-  Ctx C;
-  C.e = &e;
-  C.c = c;
-  C.rank = rank;
-  C.csize = e.csize;
-  C.cta = e.cscr + ((long long)c * e.csize + rank) * e.cl.total;
-  C.th32 = reinterpret_cast<float2*>(e.scr + (long long)c * e.sl.total + e.sl.tmp);
-  const int n = e.nq[c];   // the circuit's tableau is stored compactly in its n_max-sized slot
-  C.n = n;
-  C.d = e.d;
-  C.K = e.K;
-  uint8_t* t = e.tab + (long long)c * e.tab_stride;
-  C.fx = t;
-  C.fr = t + 4 * n * n;
-  C.ix = C.fr + 2 * n;
-  C.ir = C.ix + 4 * n * n;
-  C.mps = e.mps + e.mps_base[c];
-  C.site_off = e.site_off + (long long)c * (e.n + 1);
-  C.bond_bound = e.bond_bound + (long long)c * (e.n + 1);
-  C.dims = e.dims + (long long)c * (e.n + 1);
-  C.meta = e.meta + (long long)c * M_COUNT;
-  C.stats = e.stats + (long long)c * S_COUNT;
-  C.dstats = e.dstats + (long long)c * 4;
-  C.dec = e.dec + (long long)c * kDecCap * 2;
-  C.weyl = e.weyl + (long long)c * 2 * e.n;
-  C.scr = e.scr + (long long)c * e.sl.total;
-  C.sing = e.sing + (long long)c * e.sing_stride;
-  C.perm = e.iscr + (long long)c * e.iscr_stride;
-  return C;
-}
-
-__device__ void set_status(const Ctx& C, int code) {
-  if (C.meta[M_STATUS] == 0) C.meta[M_STATUS] = code;
-}
-
-// First failure of a circuit: which routine (1 = Jacobi SVD, 2 = tridiagonal eigenvalues) and the
-// matrix shape it had, for gcamps_last_error.
-__device__ void set_failure(const Ctx& C, int code, int where, int a, int b) {
-  if (C.meta[M_STATUS] == 0) {
-    C.meta[M_STATUS] = code;
-    C.meta[M_DIAG_WHERE] = where;
-    C.meta[M_DIAG_A] = a;
-    C.meta[M_DIAG_B] = b;
-  }
-}
-
-__device__ double block_sum(double v, Smem& s) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) s.red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int i = 0; i < kWarps; ++i) t += s.red[i];
-  return t;
-}
-
-__device__ void block_copy(double2* dst, const double2* src, long long count) {
-  for (long long i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
-}
-
-// C[M x N] = A[M x K] * B[K x N], row-major, no aliasing.
-__device__ void block_matmul(double2* Cm, const double2* A, const double2* B, int M, int K, int N) {
-  const long long total = (long long)M * N;
-  for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int r = (int)(idx / N), col = (int)(idx % N);
-    const double2* a = A + (long long)r * K;
-    double2 acc = cz();
-    for (int k = 0; k < K; ++k) acc = cfma(a[k], B[(long long)k * N + col], acc);
-    Cm[idx] = acc;
-  }
-}
-
-// ------------------------------------------------------------------------- tableau (Sec. 2.3)
-// Images are normalised to 4 x (x0, z0, x1, z1, r); for one qudit only generators 0, 1 are used
-// and x1 = z1 = 0.
-
-// lut[v] = exponents and phase of G W(v) G^dag for every local exponent vector v, where
-// W(v) = X_q0^v0 Z_q0^v1 X_q1^v2 Z_q1^v3 and the images of the generators are s.img.  The product of
-// images is accumulated with the Weyl rule  (tau^r W(a))(tau^r' W(b)) = tau^{r+r'+2 sum z(a) x(b)} W(a+b).
-__device__ void lut_build(Smem& s, int nq, int d) {
-  const int ng = 2 * nq;
-  int nent = d * d;
-  if (nq == 2) nent *= d * d;
-  for (int v = threadIdx.x; v < nent; v += blockDim.x) {
-    int dig[4] = {0, 0, 0, 0};
-    int t = v;
-    for (int k = ng - 1; k >= 0; --k) {
-      dig[k] = t % d;
-      t /= d;
-    }
-    int ax0 = 0, az0 = 0, ax1 = 0, az1 = 0, r = 0;
-    for (int k = 0; k < ng; ++k) {
-      const int* g = s.img + 5 * k;
-      for (int p = 0; p < dig[k]; ++p) {
-        r += g[4] + 2 * (az0 * g[0] + az1 * g[2]);
-        ax0 = (ax0 + g[0]) % d;
-        az0 = (az0 + g[1]) % d;
-        ax1 = (ax1 + g[2]) % d;
-        az1 = (az1 + g[3]) % d;
-      }
-    }
-    uint8_t* o = s.lut + 5 * v;
-    o[0] = (uint8_t)ax0;
-    o[1] = (uint8_t)az0;
-    o[2] = (uint8_t)ax1;
-    o[3] = (uint8_t)az1;
-    o[4] = (uint8_t)(r % (2 * d));
-  }
-  __syncthreads();
-  // Inverse images: the unique v with G W(v) G^dag = tau^delta g_k gives G^dag g_k G = tau^{-delta} W(v).
-  for (int v = threadIdx.x; v < nent; v += blockDim.x) {
-    const uint8_t* o = s.lut + 5 * v;
-    int hit = -1, cnt = 0;
-    for (int k = 0; k < 4; ++k) {
-      if (o[k]) {
-        ++cnt;
-        hit = (o[k] == 1) ? k : -2;
-      }
-    }
-    if (cnt == 1 && hit >= 0 && hit < ng) {
-      int dig[4] = {0, 0, 0, 0};
-      int t = v;
-      for (int k = ng - 1; k >= 0; --k) {
-        dig[k] = t % d;
-        t /= d;
-      }
-      int* w = s.inv + 5 * hit;
-      for (int k = 0; k < 4; ++k) w[k] = dig[k];
-      w[4] = (2 * d - o[4]) % (2 * d);
-    }
-  }
-  __syncthreads();
-}
-
-// Conjugate every row of a tableau by the Clifford of s.lut on sites q0 (, q1).
-__device__ void tab_apply_lut(Smem& s, uint8_t* X, uint8_t* R, int n, int d, int q0, int q1, int nq) {
-  for (int row = threadIdx.x; row < 2 * n; row += blockDim.x) {
-    uint8_t* e = X + (long long)row * 2 * n;
-    int v = e[q0] * d + e[n + q0];
-    if (nq == 2) v = (v * d + e[q1]) * d + e[n + q1];
-    const uint8_t* o = s.lut + 5 * v;
-    e[q0] = o[0];
-    e[n + q0] = o[1];
-    if (nq == 2) {
-      e[q1] = o[2];
-      e[n + q1] = o[3];
-    }
-    R[row] = (uint8_t)((R[row] + o[4]) % (2 * d));
-  }
-  __syncthreads();
-}
-
-// Replace the rows of the generators on (q0, q1) by products of the old rows: row(g_k) becomes
-// tau^{r_k} prod_g row(g)^{v_k[g]} for the images (v_k, r_k) in s.inv (generator order
-// X_q0, Z_q0, X_q1, Z_q1; row of X_q is n + q, of Z_q is q).
-__device__ void tab_rowprod(Smem& s, uint8_t* X, uint8_t* R, int n, int d, int q0, int q1, int nq) {
-  const int ng = 2 * nq;
-  const int rowlen = 2 * n;
-  for (int i = threadIdx.x; i < ng * rowlen; i += blockDim.x) {
-    const int g = i / rowlen, j = i % rowlen;
-    const int q = (g >> 1) ? q1 : q0;
-    const int row = (g & 1) ? q : n + q;
-    s.src[g][j] = X[(long long)row * rowlen + j];
-  }
-  if (threadIdx.x < ng) {
-    const int g = threadIdx.x;
-    const int q = (g >> 1) ? q1 : q0;
-    s.srcr[g] = R[(g & 1) ? q : n + q];
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w < ng) {
-    constexpr int kPer = (kMaxN + 31) / 32;
-    int ax[kPer], az[kPer];
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) ax[t] = az[t] = 0;
-    int r = s.inv[5 * w + 4];
-    for (int g = 0; g < ng; ++g) {
-      const int pw = s.inv[5 * w + g];
-      for (int p = 0; p < pw; ++p) {
-        int loc = 0;
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-          const int j = lane + 32 * t;
-          if (j < n) loc += az[t] * s.src[g][j];
-        }
-        r += s.srcr[g] + 2 * warp_sum_int(loc);
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-          const int j = lane + 32 * t;
-          if (j < n) {
-            ax[t] = (ax[t] + s.src[g][j]) % d;
-            az[t] = (az[t] + s.src[g][n + j]) % d;
-          }
-        }
-      }
-    }
-    const int q = (w >> 1) ? q1 : q0;
-    const int row = (w & 1) ? q : n + q;
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-      const int j = lane + 32 * t;
-      if (j < n) {
-        X[(long long)row * rowlen + j] = (uint8_t)ax[t];
-        X[(long long)row * rowlen + n + j] = (uint8_t)az[t];
-      }
-    }
-    if (lane == 0) R[row] = (uint8_t)(((r % (2 * d)) + 2 * d) % (2 * d));
-  }
-  __syncthreads();
-}
-
-__device__ void load_images(Smem& s, const int32_t* img, int nq) {
-  if (threadIdx.x < 20) {
-    int v = 0;
-    const int k = threadIdx.x / 5, f = threadIdx.x % 5;
-    if (nq == 2) {
-      v = img[threadIdx.x];
-    } else if (k < 2) {
-      if (f == 0) v = img[3 * k + 0];
-      else if (f == 1) v = img[3 * k + 1];
-      else if (f == 4) v = img[3 * k + 2];
-    }
-    s.img[threadIdx.x] = v;
-    s.inv[threadIdx.x] = 0;
-  }
-  __syncthreads();
-}
-
-// C <- G C (Sec. 3, top loop of Fig. 3).  Forward rows are conjugated by G; the rows of the
-// inverse tableau for G's sites become products of old rows via the images of G^{-1}.
-__device__ void apply_clifford(Smem& s, const Ctx& C, int q0, int q1, const int32_t* img) {
-  const int nq = (q1 < 0) ? 1 : 2;
-  load_images(s, img, nq);
-  lut_build(s, nq, C.d);
-  tab_apply_lut(s, C.fx, C.fr, C.n, C.d, q0, q1, nq);
-  tab_rowprod(s, C.ix, C.ir, C.n, C.d, q0, q1, nq);
-  if (threadIdx.x == 0) C.stats[S_CLIFF] += 1;
-}
-
-// C <- C Q^dag (Sec. 3): the inverse rows are conjugated by Q, the forward rows of Q's sites
-// become products of old rows via the images of Q^{-1}.
-__device__ void fold_candidate(Smem& s, const Ctx& C, int k, int q0) {
-  load_images(s, C.e->candImg + 20 * k, 2);
-  lut_build(s, 2, C.d);
-  tab_apply_lut(s, C.ix, C.ir, C.n, C.d, q0, q0 + 1, 2);
-  tab_rowprod(s, C.fx, C.fr, C.n, C.d, q0, q0 + 1, 2);
-}
-
-// --------------------------------------------------------- one-sided Jacobi SVD (block level)
-// Orthogonalises the n columns of B (m x n, column-major) by complex Jacobi rotations applied
-// from the right, accumulating them in W (n x n, column-major, starts as I):  B_in W = B_out.
-// Round-robin ordering: in each round the n/2 column pairs are disjoint and handled by the
-// warps in parallel.  A pair is rotated while |b_i^H b_j| > 1e-14 |b_i| |b_j|, unless one of the
-// two columns is numerically zero (|b|^2 <= 1e-30 |B|_F^2): the direction of such a column is
-// rounding noise, rotating it never settles, and its singular value lies below any truncation
-// cutoff.  Returns the number of sweeps, or -1 if `max_sweeps` were not enough.
-__device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* W, int max_sweeps) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long long i = threadIdx.x; i < (long long)n * n; i += blockDim.x)
-    W[i] = ((i % n) == (i / n)) ? make_double2(1.0, 0.0) : cz();
-  double fro = 0;
-  for (long long i = threadIdx.x; i < (long long)m * n; i += blockDim.x) fro += cabs2(B[i]);
-  fro = block_sum(fro, s);
-  const double zero_col = 1e-30 * fro;
-  const long long zc_bits = __double_as_longlong(zero_col);
-  if (threadIdx.x == 0) s.flag = 0;
-  __syncthreads();
-  if (n <= 1) return 0;
-  const int N = n + (n & 1);
-  const int npairs = N / 2;
-  const double tol2 = 1e-28;   // rotate while |b_i^H b_j| > 1e-14 |b_i| |b_j|
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int round = 0; round < N - 1; ++round) {
-      for (int p = warp; p < npairs; p += kWarps) {
-        const int pa = (p == 0) ? 0 : 1 + ((p - 1 + round) % (N - 1));
-        const int qa = 1 + ((N - 2 - p + round) % (N - 1));
-        int i = pa < qa ? pa : qa, j = pa < qa ? qa : pa;
-        if (j >= n) continue;
-        double2* bi = B + (long long)i * m;
-        double2* bj = B + (long long)j * m;
-        double al = 0, be = 0, gr = 0, gi = 0;
-        for (int r = lane; r < m; r += 32) {
-          const double2 x = bi[r], y = bj[r];
-          al = fma(x.x, x.x, fma(x.y, x.y, al));
-          be = fma(y.x, y.x, fma(y.y, y.y, be));
-          gr = fma(x.x, y.x, fma(x.y, y.y, gr));   // Re conj(x) y
-          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));  // Im conj(x) y
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        gr = warp_sum(gr);
-        gi = warp_sum(gi);
-        // al, be >= 0: compared as integers (off the FP64 pipe)
-        if (__double_as_longlong(al) <= zc_bits || __double_as_longlong(be) <= zc_bits) continue;
-        const double g2 = fma(gr, gr, gi * gi);
-        if (!(g2 > tol2 * al * be) || g2 < 1e-290) continue;   // |gamma| <= tol sqrt(al be)
-        const double ig = rsqrt(g2);                            // 1 / |gamma|
-        const double zeta = (be - al) * 0.5 * ig;
-        const double t = fabs(zeta) < 1e150 ? copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)))
-                                            : 0.5 / zeta;
-        const double cs = rsqrt(fma(t, t, 1.0));
-        const double sn = cs * t;
-        const double2 e = make_double2(gr * ig, gi * ig);      // gamma / |gamma|
-        const double2 se = cscale(e, sn), sec = cscale(cconj(e), sn);
-        // b_i' = cs b_i - sn conj(e) b_j ; b_j' = sn e b_i + cs b_j
-        for (int r = lane; r < m; r += 32) {
-          const double2 x = bi[r], y = bj[r];
-          bi[r] = csub(cscale(x, cs), cmul(sec, y));
-          bj[r] = cadd(cmul(se, x), cscale(y, cs));
-        }
-        double2* wi = W + (long long)i * n;
-        double2* wj = W + (long long)j * n;
-        for (int r = lane; r < n; r += 32) {
-          const double2 x = wi[r], y = wj[r];
-          wi[r] = csub(cscale(x, cs), cmul(sec, y));
-          wj[r] = cadd(cmul(se, x), cscale(y, cs));
-        }
-        if (lane == 0) s.flag = 1;
-      }
-      __syncthreads();
-    }
-    const int rotated = s.flag;
-    __syncthreads();
-    if (threadIdx.x == 0) s.flag = 0;
-    __syncthreads();
-    if (!rotated) return sweep + 1;
-  }
-  return -1;
-}
-
-// Singular values of the orthogonalised columns, sorted descending: sing[i] = |b_perm[i]|.
-__device__ void sorted_column_norms(const double2* B, int m, int n, double* sv_tmp, double* sing, int* perm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = warp; j < n; j += kWarps) {
-    double a = 0;
-    for (int r = lane; r < m; r += 32) a += cabs2(B[(long long)j * m + r]);
-    a = warp_sum(a);
-    if (lane == 0) sv_tmp[j] = sqrt(a);
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double v = sv_tmp[j];
-    int rank = 0;
-    for (int i = 0; i < n; ++i) {
-      const double u = sv_tmp[i];
-      rank += (u > v) || (u == v && i < j);
-    }
-    perm[rank] = j;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) sing[j] = sv_tmp[perm[j]];
-  __syncthreads();
-}
-
-// Factor M (rows x cols, row-major) = U S Vh keeping the k largest singular values with
-// s_i > cutoff * s_0 (at most cap, at least one).  U: rows x k, Vh: k x cols, both row-major in
-// scratch; S in C.sing[0..k).  If renorm, S is rescaled to unit norm.  Returns k; *disc gets the
-// discarded weight sum_{i>=k} s_i^2.
-struct Factor {
-  double2* U;
-  double2* Vh;
-  int k;
-  double disc;
-};
-
-__device__ int block_qr(Smem& s, double2* B, int m, int n, double2* Q, double2* R, double* beta, double2* rdiag);
-
-// When the long side is at least twice the short one, the long side is first reduced by a QR
-// (B = Q R) and the Jacobi rotations act on the n x n factor R; the long factor is then Q times
-// the orthogonalised columns of R.
-__device__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, int cols, int cap,
-                             bool renorm) {
-  const Engine& e = *C.e;
-  double2* B = C.scr + e.sl.b;
-  double2* W = C.scr + e.sl.w;
-  double2* U = C.scr + e.sl.u;
-  double2* Vh = C.scr + e.sl.vh;
-  double2* Qb = C.scr + e.sl.tmp;
-  double* sing = C.sing;
-  double* svt = C.sing + e.sing_stride / 2;
-  int* perm = C.perm;
-  const bool tall = rows >= cols;
-  const int m = tall ? rows : cols;
-  const int n = tall ? cols : rows;
-  // B = M (tall) or M^H (wide), column-major m x n
-  for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
-    const int r = (int)(idx / cols), c = (int)(idx % cols);
-    if (tall) B[(long long)c * m + r] = M[idx];
-    else B[(long long)r * m + c] = cconj(M[idx]);
-  }
-  __syncthreads();
-  const bool precond = n > 1 && m >= 2 * n;
-  int mm = m;
-  if (precond) {
-    block_qr(s, B, m, n, Qb, Vh, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
-    __syncthreads();
-    for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
-      const int i = (int)(idx / n), c = (int)(idx % n);
-      B[(long long)c * n + i] = Vh[idx];
-    }
-    __syncthreads();
-    mm = n;
-  }
-  const int sweeps = jacobi_orthogonalize(s, B, mm, n, W, 60);
-  if (threadIdx.x == 0) {
-    if (sweeps < 0) set_failure(C, GCAMPS_ENOCONV, 1, rows, cols);
-    const int sw = sweeps < 0 ? 60 : sweeps;
-    C.stats[S_SVD] += 1;
-    C.stats[S_JSWEEPS] += sw;
-    if (sw > C.stats[S_JMAX]) C.stats[S_JMAX] = sw;
-  }
-  sorted_column_norms(B, mm, n, svt, sing, perm);
-  // rank rule
-  if (threadIdx.x == 0) {
-    int k = 0;
-    const double s0 = sing[0];
-    if (s0 > 0) {
-      while (k < n && sing[k] > e.cutoff * s0) ++k;
-    }
-    if (k > cap) k = cap;
-    if (k < 1) k = 1;
-    double kept = 0, drop = 0;
-    for (int i = 0; i < n; ++i) (i < k ? kept : drop) += sing[i] * sing[i];
-    s.ival[0] = k;
-    s.dval[0] = drop;
-    s.dval[1] = (renorm && kept > 0) ? 1.0 / sqrt(kept) : 1.0;
-  }
-  __syncthreads();
-  const int k = s.ival[0];
-  const double scale = s.dval[1];
-  Factor F;
-  F.U = U;
-  F.Vh = Vh;
-  F.k = k;
-  F.disc = s.dval[0];
-  // X[:, i] = (long side) orthogonalised column perm[i] / sigma_i, an m-vector
-  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
-    const int r = (int)(idx / k), i = (int)(idx % k);
-    const int pj = perm[i];
-    const double sv = sing[i];
-    double2 x = cz();
-    if (sv > 0) {
-      if (precond) {
-        const double2* col = B + (long long)pj * n;
-        for (int t = 0; t < n; ++t) x = cfma(Qb[(long long)t * m + r], col[t], x);
-      } else {
-        x = B[(long long)pj * m + r];
-      }
-      x = cscale(x, 1.0 / sv);
-    }
-    if (tall) U[idx] = x;                              // U[r][i], r < rows
-    else Vh[(long long)i * cols + r] = cconj(x);       // Vh[i][r], r < cols
-  }
-  if (tall) {
-    for (long long idx = threadIdx.x; idx < (long long)k * cols; idx += blockDim.x) {
-      const int i = (int)(idx / cols), c = (int)(idx % cols);
-      Vh[idx] = cconj(W[(long long)perm[i] * n + c]);
-    }
-  } else {
-    for (long long idx = threadIdx.x; idx < (long long)rows * k; idx += blockDim.x) {
-      const int r = (int)(idx / k), i = (int)(idx % k);
-      U[idx] = W[(long long)perm[i] * n + r];
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sing[i] *= scale;
-  __syncthreads();
-  return F;
-}
-
-// ------------------------------------------------------------ Householder QR (block level)
-// Reduced QR of B (m x n, column-major, overwritten): B = Q R with k = min(m, n); Q (m x k,
-// column-major) in Q, R (k x n, row-major) in R.  Reflector k is H = I - beta v v^H with
-// v = x + e^{i arg x_0} |x| e_1 on rows k..m-1 (x = column k), so H x = -e^{i arg x_0} |x| e_1.
-// Columns handled by warps in parallel; no rank decision (the reduced Q keeps k columns).
-__device__ int block_qr(Smem& s, double2* B, int m, int n, double2* Q, double2* R, double* beta, double2* rdiag) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = m < n ? m : n;
-  // columns whose remaining part is below 1e-15 |B|_F are left unreflected (the reflector would
-  // underflow); R keeps their diagonal entry and drops the rest (<= 1e-15 |B|_F)
-  double fro = 0;
-  for (long long i = threadIdx.x; i < (long long)m * n; i += blockDim.x) fro += cabs2(B[i]);
-  fro = block_sum(fro, s);
-  const double tiny = 1e-30 * fro;
-  for (int j = 0; j < k; ++j) {
-    double2* x = B + (long long)j * m;
-    double nrm2 = 0;
-    for (int r = j + threadIdx.x; r < m; r += blockDim.x) nrm2 += cabs2(x[r]);
-    nrm2 = block_sum(nrm2, s);
-    const double2 x0 = x[j];
-    const double ax0 = hypot(x0.x, x0.y);
-    const double alpha = sqrt(nrm2);
-    __syncthreads();
-    if (nrm2 <= tiny) {
-      if (threadIdx.x == 0) {
-        beta[j] = 0.0;
-        rdiag[j] = x0;
-      }
-      __syncthreads();
-      continue;
-    }
-    const double2 ph = unit_phase(x0);
-    const double bt = 1.0 / (alpha * (alpha + ax0));
-    if (threadIdx.x == 0) {
-      x[j] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
-      beta[j] = bt;
-      rdiag[j] = make_double2(-ph.x * alpha, -ph.y * alpha);
-    }
-    __syncthreads();
-    for (int c = j + 1 + warp; c < n; c += kWarps) {
-      double2* y = B + (long long)c * m;
-      double wr = 0, wi = 0;   // w = v^H y
-      for (int r = j + lane; r < m; r += 32) {
-        const double2 v = x[r], t = y[r];
-        wr = fma(v.x, t.x, fma(v.y, t.y, wr));
-        wi = fma(v.x, t.y, fma(-v.y, t.x, wi));
-      }
-      wr = warp_sum(wr) * bt;
-      wi = warp_sum(wi) * bt;
-      const double2 w = make_double2(wr, wi);
-      for (int r = j + lane; r < m; r += 32) y[r] = csub(y[r], cmul(x[r], w));
-    }
-    __syncthreads();
-  }
-  // R (k x n, row-major)
-  for (long long idx = threadIdx.x; idx < (long long)k * n; idx += blockDim.x) {
-    const int i = (int)(idx / n), c = (int)(idx % n);
-    R[idx] = (c < i) ? cz() : (c == i ? rdiag[i] : B[(long long)c * m + i]);
-  }
-  // Q = H_0 ... H_{k-1} [I_k; 0]
-  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
-    const int r = (int)(idx % m), c = (int)(idx / m);
-    Q[idx] = (r == c) ? make_double2(1.0, 0.0) : cz();
-  }
-  __syncthreads();
-  for (int j = k - 1; j >= 0; --j) {
-    const double bt = beta[j];
-    if (bt == 0.0) continue;
-    const double2* x = B + (long long)j * m;
-    for (int c = j + warp; c < k; c += kWarps) {
-      double2* y = Q + (long long)c * m;
-      double wr = 0, wi = 0;
-      for (int r = j + lane; r < m; r += 32) {
-        const double2 v = x[r], t = y[r];
-        wr = fma(v.x, t.x, fma(v.y, t.y, wr));
-        wi = fma(v.x, t.y, fma(-v.y, t.x, wi));
-      }
-      wr = warp_sum(wr) * bt;
-      wi = warp_sum(wi) * bt;
-      const double2 w = make_double2(wr, wi);
-      for (int r = j + lane; r < m; r += 32) y[r] = csub(y[r], cmul(x[r], w));
-    }
-    __syncthreads();
-  }
-  return k;
-}
-
-// ---------------------------------------------------------------- canonical-form moves (Sec. 2.4)
-__device__ void note_chi(const Ctx& C, int k) {
-  if (threadIdx.x == 0 && k > C.stats[S_MAXCHI]) C.stats[S_MAXCHI] = k;
-}
-
-// Centre j -> j+1 without truncation (Sec. 2.4 canonical form): A_j = Q R (reduced QR of the
-// (chi_l d) x chi_r matrix), A_j <- Q, A_{j+1} <- R A_{j+1}; the bond keeps min(chi_l d, chi_r).
-__device__ void move_right(Smem& s, const Ctx& C, int j) {
-  const Engine& e = *C.e;
-  const int d = C.d;
-  const int cl = C.dims[j], cr = C.dims[j + 1], cr2 = C.dims[j + 2];
-  double2* A = site_ptr(C, j);
-  double2* A2 = site_ptr(C, j + 1);
-  double2* B = C.scr + e.sl.b;
-  double2* Q = C.scr + e.sl.u;
-  double2* R = C.scr + e.sl.vh;
-  double2* tmp = C.scr + e.sl.tmp;
-  const int m = cl * d, n = cr;
-  for (long long idx = threadIdx.x; idx < (long long)m * n; idx += blockDim.x) {
-    const int r = (int)(idx / n), c = (int)(idx % n);
-    B[(long long)c * m + r] = A[idx];
-  }
-  __syncthreads();
-  const int k = block_qr(s, B, m, n, Q, R, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
-  if (threadIdx.x == 0) C.stats[S_QR] += 1;
-  __syncthreads();
-  for (long long idx = threadIdx.x; idx < (long long)m * k; idx += blockDim.x) {
-    const int r = (int)(idx / k), c = (int)(idx % k);
-    A[idx] = Q[(long long)c * m + r];
-  }
-  block_matmul(tmp, R, A2, k, n, d * cr2);
-  __syncthreads();
-  block_copy(A2, tmp, (long long)k * d * cr2);
-  if (threadIdx.x == 0) {
-    C.dims[j + 1] = k;
-    C.meta[M_OC] = j + 1;
-  }
-  __syncthreads();
-}
-
-// Centre j -> j-1 without truncation: M = A_j (chi_l x d chi_r) = L Q from the QR of M^H
-// (M^H = Q' R', M = R'^H Q'^H); A_j <- Q'^H, A_{j-1} <- A_{j-1} R'^H.
-__device__ void move_left_qr(Smem& s, const Ctx& C, int j) {
-  const Engine& e = *C.e;
-  const int d = C.d;
-  const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
-  double2* A = site_ptr(C, j);
-  double2* A0 = site_ptr(C, j - 1);
-  double2* B = C.scr + e.sl.b;
-  double2* Q = C.scr + e.sl.u;
-  double2* R = C.scr + e.sl.vh;
-  double2* tmp = C.scr + e.sl.tmp;
-  double2* RH = C.scr + e.sl.w;
-  const int m = d * cr, n = cl;   // M^H is m x n
-  for (long long idx = threadIdx.x; idx < (long long)n * m; idx += blockDim.x) {
-    const int a = (int)(idx / m), c = (int)(idx % m);      // M[a][c]
-    B[(long long)a * m + c] = cconj(A[idx]);
-  }
-  __syncthreads();
-  const int k = block_qr(s, B, m, n, Q, R, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
-  if (threadIdx.x == 0) C.stats[S_QR] += 1;
-  __syncthreads();
-  for (long long idx = threadIdx.x; idx < (long long)k * m; idx += blockDim.x) {
-    const int i = (int)(idx / m), c = (int)(idx % m);
-    A[idx] = cconj(Q[(long long)i * m + c]);
-  }
-  for (long long idx = threadIdx.x; idx < (long long)n * k; idx += blockDim.x) {
-    const int a = (int)(idx / k), i = (int)(idx % k);
-    RH[idx] = cconj(R[(long long)i * n + a]);
-  }
-  __syncthreads();
-  block_matmul(tmp, A0, RH, cl2 * d, n, k);
-  __syncthreads();
-  block_copy(A0, tmp, (long long)cl2 * d * k);
-  if (threadIdx.x == 0) {
-    C.dims[j] = k;
-    C.meta[M_OC] = j - 1;
-  }
-  __syncthreads();
-}
-
-// Centre j -> j-1: A_j = U S Vh, A_j <- Vh, A_{j-1} <- A_{j-1} U S.  With truncation (cap, renorm)
-// this is one step of the right-to-left compression sweep.
-__device__ double move_left(Smem& s, const Ctx& C, int j, int cap, bool renorm) {
-  const int d = C.d;
-  const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
-  double2* A = site_ptr(C, j);
-  double2* A0 = site_ptr(C, j - 1);
-  const int bb = C.bond_bound[j];
-  Factor F = svd_factor(s, C, A, cl, d * cr, cap < bb ? cap : bb, renorm);
-  const int k = F.k;
-  block_copy(A, F.Vh, (long long)k * d * cr);
-  for (long long idx = threadIdx.x; idx < (long long)cl * k; idx += blockDim.x)
-    F.U[idx] = cscale(F.U[idx], C.sing[idx % k]);
-  __syncthreads();
-  double2* tmp = C.scr + C.e->sl.tmp;
-  block_matmul(tmp, A0, F.U, cl2 * d, cl, k);
-  __syncthreads();
-  block_copy(A0, tmp, (long long)cl2 * d * k);
-  if (threadIdx.x == 0) {
-    C.dims[j] = k;
-    C.meta[M_OC] = j - 1;
-  }
-  __syncthreads();
-  return F.disc;
-}
-
-__device__ void move_center(Smem& s, const Ctx& C, int target) {
-  while (true) {
-    const int oc = C.meta[M_OC];
-    __syncthreads();
-    if (oc < target) move_right(s, C, oc);
-    else if (oc > target) move_left_qr(s, C, oc);
-    else break;
-  }
-}
-
-// ------------------------------------------------- non-Clifford step (Sec. 2.3.1, Sec. 2.4, Sec. 3)
-// sum_m c_m P^m for a Weyl string P = tau^r (x)_j X_j^{x_j} Z_j^{z_j} (row: x in [0, n), z in [n, 2n))
-// and base coefficients c_m in s.coef[0..d), applied to the circuit's MPS as an MPO of bond dimension
-// d that is diagonal in m, over the support span [f, l] of P, then [f, l] recompressed (Sec. 2.4).
-// (X^a Z^b)_{s s'} = omega^{b s'} delta_{s, s'+a}, so each MPO tensor is a gather with phases.
-// record: this is the circuit's non-Clifford step (span, string and counters are kept); the adjoint
-// passes false.  The identity string (f > l) sets EINVAL.
-__device__ void mpo_apply(Smem& s, const Ctx& C, const uint8_t* row, int r, bool record) {
-  const int n = C.n, d = C.d;
-  // support span and sum_j x_j z_j
-  if (threadIdx.x == 0) {
-    s.ival[0] = n;
-    s.ival[1] = -1;
-    s.ival[2] = 0;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int x = row[j], z = row[n + j];
-    if (record) {
-      C.weyl[j] = (int8_t)x;
-      C.weyl[n + j] = (int8_t)z;
-    }
-    if (x | z) {
-      atomicMin(&s.ival[0], j);
-      atomicMax(&s.ival[1], j);
-    }
-    if (x * z) atomicAdd(&s.ival[2], x * z);
-  }
-  __syncthreads();
-  const int f = s.ival[0], l = s.ival[1];
-  const int sxz = s.ival[2] % d;
-  __syncthreads();
-  if (f > l) {  // a row of a valid tableau is never the identity
-    if (threadIdx.x == 0) set_status(C, GCAMPS_EINVAL);
-    __syncthreads();
-    return;
-  }
-  if (threadIdx.x == 0) {
-    if (record) {
-      C.meta[M_WEYL_R] = r;
-      C.meta[M_F] = f;
-      C.meta[M_L] = l;
-      C.meta[M_HAVE_SPAN] = 1;
-      C.stats[S_T] += 1;
-    }
-    // the phase of P^m: (tau^r W)^m = tau^{r m} omega^{sxz m(m-1)/2} W(m x, m z)
-    for (int m = 0; m < d; ++m) {
-      const int ph = (r * m + 2 * sxz * (m * (m - 1) / 2)) % (2 * d);
-      s.coef[m] = cmul(s.coef[m], s.tau[ph]);
-    }
-  }
-  __syncthreads();
-  // centre into [f, l]
-  {
-    int oc = C.meta[M_OC];
-    __syncthreads();
-    const int target = oc < f ? f : (oc > l ? l : oc);
-    move_center(s, C, target);
-  }
-  double2* stage = C.scr + C.e->sl.theta;
-  for (int j = f; j <= l; ++j) {
-    const int cl = C.dims[j], cr = C.dims[j + 1];
-    const int x = row[j], z = row[n + j];
-    const double2* A = site_ptr(C, j);
-    const bool first = (j == f), last = (j == l);
-    const int ml = (first ? 1 : d), mr = (last ? 1 : d);
-    const int ncl = cl * ml, ncr = cr * mr;
-    const long long total = (long long)ncl * d * ncr;
-    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int B = (int)(idx % ncr);
-      const int sidx = (int)((idx / ncr) % d);
-      const int Aa = (int)(idx / ((long long)ncr * d));
-      double2 v = cz();
-      if (f == l) {
-        for (int m = 0; m < d; ++m) {
-          const int am = (m * x) % d, bm = (m * z) % d;
-          const int sp = (sidx - am + d) % d;
-          const double2 ph = s.tau[(2 * bm * sp) % (2 * d)];
-          v = cadd(v, cmul(s.coef[m], cmul(ph, A[((long long)Aa * d + sp) * cr + B])));
-        }
-      } else {
-        const int ml_idx = first ? -1 : Aa / cl;
-        const int mr_idx = last ? -1 : B / cr;
-        const int a = first ? Aa : Aa % cl;
-        const int b = last ? B : B % cr;
-        int m = first ? mr_idx : ml_idx;
-        if (!first && !last && ml_idx != mr_idx) m = -1;
-        if (m >= 0) {
-          const int am = (m * x) % d, bm = (m * z) % d;
-          const int sp = (sidx - am + d) % d;
-          v = cmul(s.tau[(2 * bm * sp) % (2 * d)], A[((long long)a * d + sp) * cr + b]);
-          if (first) v = cmul(s.coef[m], v);
-        }
-      }
-      stage[idx] = v;
-    }
-    __syncthreads();
-    block_copy(site_ptr(C, j), stage, total);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int j = f + 1; j <= l; ++j) C.dims[j] *= d;
-  __syncthreads();
-  if (l > f) {
-    // canonicalise [f, l] left to right from f, then truncate right to left
-    if (threadIdx.x == 0) C.meta[M_OC] = f;
-    __syncthreads();
-    for (int j = f; j < l; ++j) move_right(s, C, j);
-    double disc = 0;
-    for (int j = l; j > f; --j) {
-      disc += move_left(s, C, j, C.e->chi_max, true);
-      note_chi(C, C.dims[j]);
-    }
-    if (threadIdx.x == 0) {
-      C.dstats[0] += disc;
-      if (C.e->strict_weight > 0 && disc > C.e->strict_weight) set_status(C, GCAMPS_ECHI);
-    }
-  }
-  __syncthreads();
-}
-
-// Snapshot of the MPS right after non-Clifford gate k (for the adjoint): the site tensors packed in the
-// circuit's arena, and a header with the arena offset, the gate's site, the string's phase r, the
-// first decision index of the disentangling that follows, the bond dimensions and the string.
-__device__ void take_snapshot(Smem& s, const Ctx& C, int site, const double* phases) {
-  const Engine& e = *C.e;
-  const int n = C.n, d = C.d;
-  const int k = C.meta[M_NSNAP];
-  long long need = 0;
-  for (int j = 0; j < n; ++j) need += (long long)C.dims[j] * d * C.dims[j + 1];
-  const long long off = C.meta[M_SNAPOFF];
-  __syncthreads();
-  if (k >= e.snap_max || off + need > e.snap_stride) {
-    if (threadIdx.x == 0) set_status(C, GCAMPS_ESNAP);
-    __syncthreads();
-    return;
-  }
-  int* hd = e.snap_hdr + ((long long)C.c * e.snap_max + k) * kSnapHdr;
-  double2* dst = e.snap + (long long)C.c * e.snap_stride + off;
-  long long pos = 0;
-  for (int j = 0; j < n; ++j) {
-    const long long nel = (long long)C.dims[j] * d * C.dims[j + 1];
-    block_copy(dst + pos, site_ptr(C, j), nel);
-    pos += nel;
-  }
-  const uint8_t* row = C.ix + (long long)site * 2 * n;
-  for (int j = threadIdx.x; j <= n; j += blockDim.x) hd[kSnapDims + j] = C.dims[j];
-  for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) hd[kSnapDims + kMaxN + 1 + j] = row[j];
-  if (threadIdx.x == 0) {
-    hd[0] = (int)off;
-    hd[1] = site;
-    hd[2] = C.ir[site];
-    hd[3] = C.meta[M_NDEC];
-    double* ph = e.snap_ph + ((long long)C.c * e.snap_max + k) * 4;
-    for (int j = 0; j < d; ++j) ph[j] = phases[j];
-    C.meta[M_NSNAP] = k + 1;
-    C.meta[M_SNAPOFF] = (int)(off + need);
-  }
-  __syncthreads();
-}
-
-// Diagonal non-Clifford gate diag(e^{i phases[j]}) on `site`: P = C^dag Z_site C is row `site` of the
-// inverse tableau; diag(t) = sum_m c_m Z^m with c_m = (1/d) sum_j t_j omega^{-mj}; C^dag diag(t) C =
-// sum_m c_m P^m goes through mpo_apply.
-__device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double* phases) {
-  const int n = C.n, d = C.d;
-  if (threadIdx.x == 0)
-    for (int m = 0; m < d; ++m) {
-      double re = 0, im = 0;
-      for (int j = 0; j < d; ++j) {
-        double sn, cs;
-        sincos(phases[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
-        re += cs;
-        im += sn;
-      }
-      s.coef[m] = make_double2(re / d, im / d);
-    }
-  __syncthreads();
-  mpo_apply(s, C, C.ix + (long long)site * 2 * n, C.ir[site], true);
-  if (C.e->snap && C.meta[M_STATUS] == 0) take_snapshot(s, C, site, phases);
-}
-
-// --------------------------------------------------------------- candidate scoring (Sec. 3)
-// The same routines run on a warp (small problems, one class per warp) or on a whole CTA (large
-// problems, one class per CTA); the group type supplies the thread index, barrier and reduction.
-struct WarpGroup {
-  int tid;
-  static constexpr int n = 32;
-  __device__ void sync() const { __syncwarp(); }
-  __device__ double sum(double v) const { return warp_sum(v); }
-  __device__ double bcast(double v) const { return __shfl_sync(0xffffffffu, v, 0); }
-};
-struct BlockGroup {
-  Smem* s;
-  int tid, n;
-  __device__ void sync() const { __syncthreads(); }
-  __device__ double sum(double v) const { return block_sum(v, *s); }
-  __device__ double bcast(double v) const {
-    __syncthreads();
-    if (tid == 0) s->dval[2] = v;
-    __syncthreads();
-    const double r = s->dval[2];
-    __syncthreads();
-    return r;
-  }
-};
-
-// Householder reduction of a Hermitian m x m matrix (row-major, full storage, overwritten) to a
-// real symmetric tridiagonal (diag dg, off-diagonal magnitudes od).  A column whose entries below
-// the subdiagonal have norm below 1e-16 |A|_F is taken as already reduced (dropping them moves
-// eigenvalues by at most that much).  Column k below the diagonal keeps the reflector v, row k right
-// of it p and w.
-template <class Grp>
-__device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, double* od) {
-  double fro2 = 0;
-  for (int idx = g.tid; idx < m * m; idx += g.n) fro2 += cabs2(A[idx]);
-  fro2 = g.sum(fro2);
-  for (int k = 0; k + 2 < m; ++k) {
-    const int r = m - k - 1;
-    // the tail below x0 is summed on its own: |x|^2 - |x0|^2 cancels when x0 dominates and would
-    // hide a small tail (which, inside a degenerate eigenspace, moves eigenvalues at first order)
-    double tail2 = 0;
-    for (int i = 1 + g.tid; i < r; i += g.n) tail2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
-    tail2 = g.sum(tail2);
-    const double2 x0 = A[(long long)(k + 1) * m + k];
-    const double ax0 = hypot(x0.x, x0.y);
-    const double nrm2 = tail2 + ax0 * ax0;
-    if (g.tid == 0) dg[k] = A[(long long)k * m + k].x;
-    g.sync();
-    const double alpha = sqrt(nrm2);
-    if (tail2 <= 1e-32 * fro2) {
-      if (g.tid == 0) od[k] = ax0;
-      g.sync();
-      continue;
-    }
-    const double2 ph = unit_phase(x0);
-    const double h = alpha * (alpha + ax0);  // v^H v / 2
-    if (g.tid == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
-    g.sync();
-    const double hinv = 1.0 / h;
-    for (int i = g.tid; i < r; i += g.n) {
-      double2 acc = cz();
-      const double2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
-      for (int j = 0; j < r; ++j) acc = cfma(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
-      A[(long long)k * m + k + 1 + i] = cscale(acc, hinv);
-    }
-    g.sync();
-    double kr = 0;
-    for (int i = g.tid; i < r; i += g.n) {
-      const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
-      kr += v.x * p.x + v.y * p.y;
-    }
-    kr = g.sum(kr) * 0.5 * hinv;
-    g.sync();
-    for (int i = g.tid; i < r; i += g.n) {
-      const double2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
-      A[(long long)k * m + k + 1 + i] = make_double2(p.x - kr * v.x, p.y - kr * v.y);
-    }
-    g.sync();
-    for (int idx = g.tid; idx < r * (r + 1) / 2; idx += g.n) {
-      int i, j;
-      tri_index(idx, i, j);
-      const double2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
-      const double2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
-      // a - (vi conj(wj) + wi conj(vj)), as eight fused multiply-adds
-      double2* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
-      double2 nv = *a;
-      nv.x = fma(-vi.x, wj.x, fma(-vi.y, wj.y, fma(-wi.x, vj.x, fma(-wi.y, vj.y, nv.x))));
-      nv.y = fma(-vi.y, wj.x, fma(vi.x, wj.y, fma(-wi.y, vj.x, fma(wi.x, vj.y, nv.y))));
-      *a = nv;
-      if (j != i) A[(long long)(k + 1 + j) * m + (k + 1 + i)] = cconj(nv);
-    }
-    if (g.tid == 0) od[k] = alpha;
-    g.sync();
-  }
-  if (g.tid == 0) {
-    if (m >= 2) {
-      dg[m - 2] = A[(long long)(m - 2) * m + (m - 2)].x;
-      const double2 e = A[(long long)(m - 1) * m + (m - 2)];
-      od[m - 2] = hypot(e.x, e.y);
-    }
-    dg[m - 1] = A[(long long)(m - 1) * m + (m - 1)].x;
-  }
-  g.sync();
-}
-
-// Integer key with the order of the double v (no NaN): sorting keys sorts values, off the FP64 pipe.
-__device__ __forceinline__ long long order_key(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-
-// Number of eigenvalues below x of the symmetric tridiagonal (dg, e2 = off-diagonal squared): the
-// number of sign changes along the leading principal minors f_0 = 1, f_1, ..., f_m of T - x I,
-// f_{i+1} = (d_i - x) f_i - e2_{i-1} f_{i-1} (Sturm sequence; a sign change is a negative LDL^T pivot
-// f_{i+1} / f_i, Sylvester's law of inertia).  A minor that is exactly zero counts as a negative pivot
-// (its sign is taken opposite to the previous one).  The pair (f_i, f_{i+1}) is rescaled by 2^-+500
-// whenever the larger leaves [2^-500, 2^500]; scaling by a positive power of two changes no sign.
-// Three FP64 instructions per step; the sign and exponent tests are integer operations.
-__device__ __forceinline__ int sturm_count(const double* dg, const double* e2, int m, double x) {
-  double f0 = 1.0, f1 = dg[0] - x;
-  long long b1 = __double_as_longlong(f1);
-  unsigned s1 = (b1 & 0x7fffffffffffffffLL) == 0 ? 1u : (unsigned)((unsigned long long)b1 >> 63);
-  int cnt = (int)s1;
-  for (int i = 1; i < m; ++i) {
-    double f2 = fma(dg[i] - x, f1, -e2[i - 1] * f0);
-    const long long b2 = __double_as_longlong(f2);
-    const int ex1 = (int)((b1 >> 52) & 0x7ff), ex2 = (int)((b2 >> 52) & 0x7ff);
-    const int ex = ex1 > ex2 ? ex1 : ex2;
-    if (ex > 1023 + 500) {
-      f1 *= 3.054936363499605e-151;   // 2^-500
-      f2 *= 3.054936363499605e-151;
-    } else if (ex < 1023 - 500) {
-      f1 *= 3.273390607896142e+150;   // 2^500
-      f2 *= 3.273390607896142e+150;
-    }
-    const long long c2 = __double_as_longlong(f2);
-    const unsigned s2 = (c2 & 0x7fffffffffffffffLL) == 0 ? (s1 ^ 1u) : (unsigned)((unsigned long long)c2 >> 63);
-    cnt += (int)(s2 != s1);
-    s1 = s2;
-    f0 = f1;
-    f1 = f2;
-    b1 = c2;
-  }
-  return cnt;
-}
-
-// FP32 version of sturm_count (rescaling by 2^-+40 outside [2^-40, 2^40]); it is exact for a matrix
-// within a few FP32 units of T, which bounds the bracket it gives (see tridiag_bisect).
-__device__ __forceinline__ int sturm_count32(const float* dg, const float* e2, int m, float x) {
-  float f0 = 1.0f, f1 = dg[0] - x;
-  int b1 = __float_as_int(f1);
-  unsigned s1 = (b1 & 0x7fffffff) == 0 ? 1u : ((unsigned)b1 >> 31);
-  int cnt = (int)s1;
-  for (int i = 1; i < m; ++i) {
-    float f2 = fmaf(dg[i] - x, f1, -e2[i - 1] * f0);
-    const int b2 = __float_as_int(f2);
-    const int ex1 = (b1 >> 23) & 0xff, ex2 = (b2 >> 23) & 0xff;
-    const int ex = ex1 > ex2 ? ex1 : ex2;
-    if (ex > 127 + 40) {
-      f1 *= 9.094947017729282e-13f;   // 2^-40
-      f2 *= 9.094947017729282e-13f;
-    } else if (ex < 127 - 40) {
-      f1 *= 1099511627776.0f;         // 2^40
-      f2 *= 1099511627776.0f;
-    }
-    const int c2 = __float_as_int(f2);
-    const unsigned s2 = (c2 & 0x7fffffff) == 0 ? (s1 ^ 1u) : ((unsigned)c2 >> 31);
-    cnt += (int)(s2 != s1);
-    s1 = s2;
-    f0 = f1;
-    f1 = f2;
-    b1 = c2;
-  }
-  return cnt;
-}
-
-// Eigenvalues of a positive semidefinite tridiagonal (the reduced Gram) by multisection, P lanes per
-// eigenvalue (see below): eigenvalue j (ascending) is where the Sturm count passes j.  The spectrum
-// lies in [0, tr] (span = |tr|); each eigenvalue is located within 2^-50 span (an entropy error below
-// 1e-12 for the Gram sizes used here).
-//   sh, sh32: shared arrays of 2 cap entries for (diagonal | off-diagonal squared), or null.  With them
-//   (m <= cap) FP32 steps worth 24 halvings first bracket eigenvalue j; since an FP32 Sturm count is
-//   exact for a matrix within 8 FP32 units of span of T, the bracket padded by 40 units holds it, which
-//   two FP64 counts confirm (else the full interval is used), and FP64 steps worth 33 halvings finish.
-//   Without them, FP64 steps worth 50 halvings of [0, span] on the global arrays.
-// Off-diagonal squares are at least 1e-300 span^2 (1e-20 span^2 in FP32), which moves no eigenvalue
-// by more than 1e-150 span (1e-10 span, inside the FP32 padding) and keeps an exactly zero minor from
-// zeroing the rest of the sequence.  od is overwritten with its squares; ev receives the m eigenvalues.
-// m <= 2 in closed form.
-template <class Grp>
-__device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m, double* ev, double* sh,
-                               float* sh32, int cap) {
-  if (m <= 2) {
-    if (g.tid == 0) {
-      if (m == 1) {
-        ev[0] = dg[0];
-      } else {
-        const double mean = 0.5 * (dg[0] + dg[1]), r = hypot(0.5 * (dg[0] - dg[1]), od[0]);
-        ev[0] = mean - r;
-        ev[1] = mean + r;
-      }
-    }
-    g.sync();
-    return;
-  }
-  double tr = 0;
-  for (int i = g.tid; i < m; i += g.n) tr += dg[i];
-  tr = g.sum(tr);
-  const double span = fabs(tr) + 1e-300;
-  const double e2min = 1e-300 * span * span;
-  const double gl = -4.440892098500626e-16 * span, gu = tr + 4.440892098500626e-16 * span;
-  const bool fast = sh != nullptr && m <= cap;
-  const double* D = dg;
-  const double* E = od;
-  if (fast) {
-    const float e2min32 = (float)(1e-20 * span * span);
-    for (int i = g.tid; i < m; i += g.n) {
-      sh[i] = dg[i];
-      sh32[i] = (float)dg[i];
-      if (i + 1 < m) {
-        const double e2 = fmax(od[i] * od[i], e2min);
-        sh[cap + i] = e2;
-        sh32[cap + i] = fmaxf((float)e2, e2min32);
-      }
-    }
-    D = sh;
-    E = sh + cap;
-  } else {
-    for (int i = g.tid; i + 1 < m; i += g.n) od[i] = fmax(od[i] * od[i], e2min);
-  }
-  g.sync();
-  // Multisection: P lanes of a warp share eigenvalue j and count at P interior points of its
-  // interval, which then shrinks by P + 1 per step (P as large as the group's warps allow).  All
-  // lanes of a warp run the same number of steps (the group's outcome is combined by a ballot).
-  const int nw = (g.n + 31) / 32;
-  int P = 1;
-  for (int p = 8; p >= 1; --p)
-    if (nw * (32 / p) >= m) {
-      P = p;
-      break;
-    }
-  const int per_warp = 32 / P;
-  const int lane = g.tid & 31, warp = g.tid >> 5;
-  const int grp = lane / P, pidx = lane % P;
-  const unsigned gmask = ((1u << P) - 1u) << (grp < per_warp ? grp * P : 0);
-  constexpr double kLog2[9] = {0.0, 1.0, 1.584962500721156, 2.0, 2.321928094887362, 2.584962500721156,
-                               2.807354922057604, 3.0, 3.169925001442312};
-  const int it32 = (int)ceil(24.0 / kLog2[P] - 1e-9);
-  const int it64 = (int)ceil(33.0 / kLog2[P] - 1e-9);
-  const int itfull = (int)ceil(50.0 / kLog2[P] - 1e-9);
-  for (int base = 0; base < m; base += nw * per_warp) {
-    const int jr = base + warp * per_warp + grp;
-    const bool active = grp < per_warp && jr < m;
-    const int j = active ? jr : 0;
-    double lo = gl, hi = gu;
-    int nit = itfull;
-    if (fast) {
-      float lo32 = (float)gl, hi32 = (float)gu;
-      for (int it = 0; it < it32; ++it) {
-        const float step = (hi32 - lo32) / (float)(P + 1);
-        const float x = lo32 + (float)(pidx + 1) * step;
-        const bool flag = active && sturm_count32(sh32, sh32 + cap, m, x) > j;
-        const unsigned bits = (__ballot_sync(0xffffffffu, flag) & gmask) >> (grp < per_warp ? grp * P : 0);
-        const int ps = bits ? __ffs(bits) - 1 : P;
-        const float nlo = ps == 0 ? lo32 : lo32 + (float)ps * step;
-        const float nhi = ps == P ? hi32 : lo32 + (float)(ps + 1) * step;
-        lo32 = nlo;
-        hi32 = nhi;
-      }
-      const double pad = 40.0 * 5.960464477539063e-08 * span;   // 40 FP32 units
-      const double a = (double)lo32 - pad, b = (double)hi32 + pad;
-      bool ok;
-      if (P == 1) {
-        ok = !active || (sturm_count(D, E, m, a) <= j && sturm_count(D, E, m, b) > j);
-      } else {
-        bool mine = true;
-        if (active && pidx == 0) mine = sturm_count(D, E, m, a) <= j;
-        if (active && pidx == 1) mine = sturm_count(D, E, m, b) > j;
-        const unsigned fails = __ballot_sync(0xffffffffu, !mine) & gmask;
-        ok = !active || fails == 0u;
-      }
-      if (__all_sync(0xffffffffu, ok)) {
-        lo = a;
-        hi = b;
-        nit = it64;
-      }
-    }
-    for (int it = 0; it < nit; ++it) {
-      const double step = (hi - lo) / (double)(P + 1);
-      const double x = lo + (double)(pidx + 1) * step;
-      const bool flag = active && sturm_count(D, E, m, x) > j;
-      const unsigned bits = (__ballot_sync(0xffffffffu, flag) & gmask) >> (grp < per_warp ? grp * P : 0);
-      const int ps = bits ? __ffs(bits) - 1 : P;
-      const double nlo = ps == 0 ? lo : lo + (double)ps * step;
-      const double nhi = ps == P ? hi : lo + (double)(ps + 1) * step;
-      lo = nlo;
-      hi = nhi;
-    }
-    if (active && pidx == 0) ev[j] = 0.5 * (lo + hi);
-  }
-  g.sync();
-}
-
-struct Score {
-  double s2, vn;
-  int rank;   // eigenvalues above max(1e-12, 4 cutoff^2) tr G (von Neumann evaluations only)
-  bool ok;
-};
-
-// One class Q on theta: theta' = Q theta over (a, s) x (t, b); its Gram G on the smaller side (lower
-// triangle computed, mirrored); the Renyi-2 entropy S2 = -ln(|G|_F^2 / tr(G)^2); and, if asked, the
-// von Neumann entropy -sum p ln p from the eigenvalues of G (p = lambda / tr G).  S2 <= S_vN always.
-template <class Grp>
-__device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
-                             double2* ws, long long gram_off, bool want_vn, double* tri, float* tri32, int tricap) {
-  const int d = C.d, dd = d * d;
-  const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols;
-  double2* tp = ws;
-  double2* G = ws + gram_off;
-  double* dg = reinterpret_cast<double*>(G + (long long)m * m);
-  double* od = dg + m;
-  for (long long idx = g.tid; idx < (long long)rows * cols; idx += g.n) {
-    const int rr = (int)(idx / cols), col = (int)(idx % cols);
-    const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
-    const double2* q = Q + (sd * d + t) * dd;
-    const double2* th = theta + (long long)a * dd * cr + b;
-    double2 acc = cz();
-    for (int u = 0; u < dd; ++u) acc = cfma(q[u], th[(long long)u * cr], acc);
-    tp[idx] = acc;
-  }
-  g.sync();
-  double tr = 0, fro = 0;
-  const int ntri = m * (m + 1) / 2;
-  for (int idx = g.tid; idx < ntri; idx += g.n) {
-    int i, j;
-    tri_index(idx, i, j);
-    double2 acc = cz();
-    if (rows <= cols) {
-      const double2* ri = tp + (long long)i * cols;
-      const double2* rj = tp + (long long)j * cols;
-      for (int c = 0; c < cols; ++c) acc = cfmac(rj[c], ri[c], acc);   // sum_c ri conj(rj)
-    } else {
-      for (int r = 0; r < rows; ++r) acc = cfmac(tp[(long long)r * cols + i], tp[(long long)r * cols + j], acc);
-    }
-    G[(long long)i * m + j] = acc;
-    if (i == j) {
-      tr += acc.x;
-      fro += acc.x * acc.x;
-    } else {
-      G[(long long)j * m + i] = cconj(acc);
-      fro += 2.0 * cabs2(acc);
-    }
-  }
-  tr = g.sum(tr);
-  fro = g.sum(fro);
-  Score sc;
-  sc.ok = true;
-  sc.s2 = (tr > 0.0 && fro > 0.0) ? -log(fro / (tr * tr)) : 0.0;
-  sc.vn = sc.s2;
-  sc.rank = -1;
-  if (!want_vn) return sc;
-  g.sync();
-  group_tridiag(g, G, m, dg, od);
-  double* ev = reinterpret_cast<double*>(G);   // G is dead after the reduction
-  tridiag_bisect(g, dg, od, m, ev, tri, tri32, tricap);
-  // entropy -sum p ln p (p = lambda / tr) and the numerical rank, summed over the group
-  double tot = 0;
-  for (int i = g.tid; i < m; i += g.n) tot += fmax(ev[i], 0.0);
-  tot = g.sum(tot);
-  double ent = 0.0, rk = 0.0;
-  if (tot > 0) {
-    const double inv = 1.0 / tot;
-    const double rthr = fmax(1e-12, 4.0 * C.e->cutoff * C.e->cutoff);
-    for (int i = g.tid; i < m; i += g.n) {
-      const double p = fmax(ev[i], 0.0) * inv;
-      if (p > 0) ent -= p * log(p);
-      if (p > rthr) rk += 1.0;
-    }
-  }
-  sc.vn = g.sum(ent);
-  sc.rank = (int)g.sum(rk);
-  sc.ok = true;
-  return sc;
-}
-
-// Renyi-2 entropy of class Q on theta in FP32, and a lower bound on the exact value.  theta' = Q theta
-// (FP32 inputs, d^2-term sums) is off by at most e1 |theta|_F with e1 = d (d^2 + 6) u (u = 2^-24),
-// and the Gram on the smaller side (sums of 2M + 4 rounded terms, M the longer side) by at most
-// (2M + 4) u |theta'|_F^2, so |G^ - G|_F <= eta tr G with eta = 2 e1 + e1^2 + (2M + 4) u (1 + e1)^2;
-// the same bound holds for the trace.  Then |ln |G^|_F - ln |G|_F| <= eta tr / |G|_F <= eta sqrt(m) and
-// |ln tr^ - ln tr| <= eta, so |S2^ - S2| <= 2 eta sqrt(m) + 2 eta.  The lower bound subtracts twice that
-// plus the rounding of the partial sums.  Outside 1e-12 < tr < 1e12 (where FP32 squares of the Gram
-// entries could underflow or overflow and break the bound) the lower bound is 0 (S2 >= 0).
-template <class Grp>
-__device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, int cr, const float2* Q, float2* X,
-                        double* s2_out, double* lo_out) {
-  const int d = C.d, dd = d * d;
-  const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols, M = rows < cols ? cols : rows;
-  for (int idx = g.tid; idx < rows * cols; idx += g.n) {
-    const int rr = idx / cols, col = idx % cols;
-    const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
-    const float2* q = Q + (sd * d + t) * dd;
-    const float2* tp = th + (long long)a * dd * cr + b;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int v = 0; v < dd; ++v) acc = ffma2(q[v], tp[(long long)v * cr], acc);
-    X[idx] = acc;
-  }
-  g.sync();
-  float tr = 0.f, fro = 0.f;
-  const int ntri = m * (m + 1) / 2;
-  for (int idx = g.tid; idx < ntri; idx += g.n) {
-    int i, j;
-    tri_index(idx, i, j);
-    float2 acc = make_float2(0.f, 0.f);
-    if (rows <= cols) {
-      const float2* ri = X + (long long)i * cols;
-      const float2* rj = X + (long long)j * cols;
-      for (int c = 0; c < cols; ++c) acc = ffmac2(ri[c], rj[c], acc);
-    } else {
-      for (int r = 0; r < rows; ++r) acc = ffmac2(X[(long long)r * cols + i], X[(long long)r * cols + j], acc);
-    }
-    if (i == j) {
-      tr += acc.x;
-      fro = fmaf(acc.x, acc.x, fro);
-    } else {
-      fro = fmaf(2.f * acc.x, acc.x, fmaf(2.f * acc.y, acc.y, fro));
-    }
-  }
-  const double trd = g.sum((double)tr), frod = g.sum((double)fro);
-  double s2 = 0.0, lo = 0.0;
-  if (trd > 1e-12 && trd < 1e12 && frod > 0.0) {
-    const double u = 5.960464477539063e-08;
-    const double e1 = d * (dd + 6) * u;
-    const double eta = 2.0 * e1 + e1 * e1 + (2.0 * M + 4.0) * u * (1.0 + e1) * (1.0 + e1);
-    const double delta = 4.0 * eta * sqrt((double)m) + 4.0 * eta + ((double)m * m / 16.0 + 16.0) * u;
-    s2 = -log(frod / (trd * trd));
-    lo = s2 - delta;
-  }
-  *s2_out = s2;
-  *lo_out = lo;
-}
-
-// Scores classes list[0..cnt) (all K classes if list is null) on the whole cluster: small problems
-// one class per warp, large ones one class per CTA.  Results go to the leader CTA's shared memory.
-// mode kExact: S2 and S_vN in FP64; kScreen: S2 in FP32 with its lower bound (lead->s2lo).
-// kS2Exact: S2 in FP64 only (class 0 still gets kExact: its eigenvalues certify QR moves).
-enum ScoreMode { kExact = 0, kScreen = 1, kS2Exact = 2 };
-__device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
-                              const int* list, int cnt, int mode) {
-  const Engine& e = *C.e;
-  const int d = C.d, dd = d * d;
-  const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols;
-  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (small) {
-    WarpGroup g{lane};
-    double2* ws = C.cta + e.cl.warp + (long long)warp * kSmallStride;
-    // consecutive list entries go to different CTAs, then to different warps: the first 4 csize
-    // entries land on distinct FP64 pipes (SM sub-partitions)
-    const int gw = warp * C.csize + C.rank, nw = C.csize * kWarps;
-    for (int t = gw; t < cnt; t += nw) {
-      const int k = list ? list[t] : t;
-      if (mode == kScreen) {
-        double v, lo;
-        s2_fp32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws), &v, &lo);
-        if (lane == 0) {
-          lead->s2[k] = v;
-          lead->s2lo[k] = lo;
-        }
-        continue;
-      }
-      const bool want_vn = mode == kExact || k == 0;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn,
-                                   s.wtri[warp], s.wtri32[warp], 32);
-      if (lane == 0) {
-        lead->s2[k] = sc.s2;
-        lead->evald[k] = 1;
-        lead->vn[k] = want_vn ? sc.vn : CUDART_NAN;
-        lead->rk[k] = sc.rank;
-        if (k == 0) lead->rank0 = sc.rank;
-        if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
-      }
-    }
-  } else {
-    BlockGroup g{&s, (int)threadIdx.x, (int)blockDim.x};
-    double2* ws = C.cta + e.cl.block;
-    for (int t = C.rank; t < cnt; t += C.csize) {
-      const int k = list ? list[t] : t;
-      if (mode == kScreen) {
-        double v, lo;
-        s2_fp32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws), &v, &lo);
-        if (threadIdx.x == 0) {
-          lead->s2[k] = v;
-          lead->s2lo[k] = lo;
-        }
-        __syncthreads();
-        continue;
-      }
-      const bool want_vn = mode == kExact || k == 0;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.scap, want_vn,
-                                   s.btri, s.btri32, kBTri);
-      if (threadIdx.x == 0) {
-        lead->s2[k] = sc.s2;
-        lead->evald[k] = 1;
-        lead->vn[k] = want_vn ? sc.vn : CUDART_NAN;
-        lead->rk[k] = sc.rank;
-        if (k == 0) lead->rank0 = sc.rank;
-        if (!sc.ok) set_failure(C, GCAMPS_ENOCONV, 2, rows, cols);
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
-
-// ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
-// One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
-// decides, applies and splits.  With the Renyi-2 bound (S2 <= S_vN): phase A gives S2 of every class
-// from an FP32 screen with a rigorous lower bound s2lo (s2_fp32), and the passes below use s2lo;
-// the first pass evaluates S_vN of the identity and of the classes with the smallest S2 (as many as the
-// cluster evaluates at once), giving an upper bound B on the best entropy; the second pass evaluates every
-// other class with S2 <= B + tie_tol (usually none: they are a prefix of the S2 order).  A class left out
-// has S_vN >= S2 > best + tie_tol, so the decision equals the one from evaluating every class.
-// Cluster-wide choice of the class for one theta (shape chi_l x d x d x chi_r in global memory,
-// readable by every CTA).  Returns the chosen class on the leader (-1 on the other CTAs); the
-// leader's s.vn / s.evald hold the evaluated entropies and *nev their count.
-__device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out) {
-  const Engine& e = *C.e;
-  const bool leader = C.rank == 0;
-  const int d = C.d;
-  const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols;
-  const bool prune = m > kPruneMin;
-  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
-  if (prune) {   // FP32 copy of theta for the screen, shared by the cluster
-    if (leader)
-      for (int i = threadIdx.x; i < rows * cols; i += blockDim.x)
-        C.th32[i] = make_float2((float)theta[i].x, (float)theta[i].y);
-    cluster_sync();
-  }
-  score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, prune ? kScreen : kExact);
-  cluster_sync();
-  const int kind = e.score_kind;
-  // weight-rank threshold (the same as the QR-move certificate) and the rank lower bound from S2:
-  // the weights above tau carry at least 1 - m tau of the trace, so sum p^2 >= (1 - m tau)^2 / rank and
-  // rank >= exp(S2 + 2 ln(1 - m tau)) >= exp(S2 - 2.01 m tau)
-  const double tau_w = fmax(1e-12, 4.0 * e.cutoff * e.cutoff);
-  auto rank_lo = [&](int k) -> int {
-    const double x = s.s2lo[k] - 2.01 * m * tau_w;
-    if (!(x > 0.0) || m * tau_w >= 0.25) return 0;
-    return (int)ceil(exp(x) * (1.0 - 1e-12));
-  };
-  if (prune) {
-    if (kind == 1) {
-      // Renyi-2 score: exact S2 for every class whose lower bound is within tie_tol of the smallest
-      // upper bound (upper = screen value + the same margin), and for the identity
-      if (leader && threadIdx.x == 0) {
-        double ub = 1e300;
-        for (int k = 0; k < C.K; ++k) {
-          s.evald[k] = 0;
-          ub = fmin(ub, 2.0 * s.s2[k] - s.s2lo[k]);
-        }
-        int cnt = 1;
-        s.list[0] = 0;
-        for (int k = 1; k < C.K; ++k)
-          if (s.s2lo[k] <= ub + e.tie_tol + 1e-12) s.list[cnt++] = k;
-        s.nlist = cnt;
-      }
-      cluster_sync();
-      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kS2Exact);
-      cluster_sync();
-    } else {
-      if (leader) {
-        // first pass: the identity and the classes of smallest S2 lower bound, one per FP64 pipe of the
-        // cluster (warp-level scoring) or one per CTA (CTA-level scoring)
-        const int L = (small ? 4 * C.csize : C.csize) - 1;
-        for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-          s.evald[k] = 0;
-          const long long bk = order_key(s.s2lo[k]);
-          int r = 0;
-          for (int q = 0; q < C.K; ++q) {
-            const long long bq = order_key(s.s2lo[q]);
-            r += (bq < bk) || (bq == bk && q < k);
-          }
-          s.ord[k] = r;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          int cnt = 1;
-          s.list[0] = 0;
-          for (int k = 1; k < C.K; ++k)
-            if (s.ord[k] < L) s.list[cnt++] = k;
-          s.nlist = cnt;
-        }
-      }
-      cluster_sync();
-      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
-      cluster_sync();
-      if (leader && threadIdx.x == 0) {
-        // second pass: every class the bounds cannot exclude.  Kind 0: S2 lower bound within tie_tol of the
-        // best exact entropy.  Kind 2: rank bound below the best exact rank, or equal to it with the S2
-        // bound within tie_tol of the best entropy among the classes of that rank.
-        int rmin = 1 << 30;
-        if (kind == 2)
-          for (int k = 0; k < C.K; ++k)
-            if (s.evald[k] && s.rk[k] < rmin) rmin = s.rk[k];
-        double bound = 1e300;
-        for (int k = 0; k < C.K; ++k)
-          if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) bound = fmin(bound, s.vn[k]);
-        int cnt = 0;
-        for (int k = 0; k < C.K; ++k) {
-          if (s.evald[k]) continue;
-          bool need = s.s2lo[k] <= bound + e.tie_tol + 1e-12;
-          if (kind == 2) {
-            const int rl = rank_lo(k);
-            need = rl < rmin || (rl == rmin && need);
-          }
-          if (need) s.list[cnt++] = k;
-        }
-        s.nlist = cnt;
-      }
-      cluster_sync();
-      score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
-      cluster_sync();
-    }
-  }
-  if (!leader) return -1;
-  if (threadIdx.x == 0) {
-    // the decision over the exactly evaluated classes: key = S_vN (kind 0), S2 (kind 1), or the
-    // weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
-    // class is applied only if it beats the identity
-    int nev = 0, rmin = 1 << 30;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k]) {
-        ++nev;
-        if (s.rk[k] < rmin) rmin = s.rk[k];
-      }
-    auto key = [&](int k) { return kind == 1 ? s.s2[k] : s.vn[k]; };
-    double best = 1e300;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) best = fmin(best, key(k));
-    int kb = 0;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin) && key(k) <= best + e.tie_tol) {
-        kb = k;
-        break;
-      }
-    const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
-    if (!better) kb = 0;
-    s.ival[4] = kb;
-    s.ival[5] = nev;
-  }
-  {
-    double* out = e.lastsc + (long long)C.c * (3 * kMaxK + 2 + 2 * kSmall);
-    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-      out[k] = s.s2[k];
-      out[kMaxK + k] = s.vn[k];
-      out[2 * kMaxK + k] = s.evald[k];
-    }
-    if (threadIdx.x == 0) {
-      out[3 * kMaxK] = cl;
-      out[3 * kMaxK + 1] = cr;
-    }
-    if ((long long)rows * cols <= kSmall)
-      for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
-        out[3 * kMaxK + 2 + 2 * k] = theta[k].x;
-        out[3 * kMaxK + 3 + 2 * k] = theta[k].y;
-      }
-  }
-  __syncthreads();
-  *nev_out = s.ival[5];
-  return s.ival[4];
-}
-
-__device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, int* accepted) {
-  const Engine& e = *C.e;
-  const bool leader = C.rank == 0;
-  const int d = C.d, dd = d * d;
-  double2* theta = C.scr + e.sl.theta;
-  double2* tmp = C.scr + e.sl.tmp;
-  if (leader) {
-    const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
-    block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
-    if (threadIdx.x == 0) s.rank0 = -1;
-  }
-  cluster_sync();
-  const int cl = C.dims[i], cr = C.dims[i + 2];
-  const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols;
-  int nev = 0;
-  const int kbsel = select_class(s, lead, C, theta, cl, cr, &nev);
-  if (!leader) return;
-  if (threadIdx.x == 0) {
-    const int kb = kbsel;
-    C.stats[S_BONDS] += 1;
-    C.stats[S_CANDS] += C.K;
-    C.stats[S_VN] += nev;
-    {
-      const double R = rows, Cc = cols, mm = m, M = rows < cols ? cols : rows;
-      const double per_class = 8.0 * dd * R * Cc + 4.0 * mm * (mm + 1.0) * M;
-      const double tri = (16.0 / 3.0) * mm * mm * mm;
-      // exact evaluations, FP64 (Renyi-2 scores need no eigenvalues except the identity's)
-      C.dstats[1] += e.score_kind == 1 ? nev * per_class + tri : nev * (per_class + tri);
-      if (m > kPruneMin) C.dstats[2] += C.K * per_class;                // FP32 screen of every class
-    }
-    const int nd = C.meta[M_NDEC];
-    if (nd < kDecCap) {
-      C.dec[2 * nd] = i;
-      C.dec[2 * nd + 1] = kb;
-    }
-    C.meta[M_NDEC] = nd + 1;
-  }
-  __syncthreads();
-  const int kb = s.ival[4];
-  if (kb != 0) {
-    const double2* Q = e.candU + (long long)kb * dd * dd;
-    const long long total = (long long)cl * dd * cr;
-    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int b = (int)(idx % cr), u = (int)((idx / cr) % dd);
-      const long long a = idx / ((long long)cr * dd);
-      double2 acc = cz();
-      for (int v = 0; v < dd; ++v) acc = cfma(Q[u * dd + v], theta[(a * dd + v) * cr + b], acc);
-      tmp[idx] = acc;
-    }
-    __syncthreads();
-    block_copy(theta, tmp, total);
-    __syncthreads();
-    fold_candidate(s, C, kb, i);
-    if (threadIdx.x == 0) C.stats[S_ACC] += 1;
-    ++*accepted;
-  }
-  const int bb = C.bond_bound[i + 1];
-  const int cap = e.chi_max < bb ? e.chi_max : bb;
-  // Nothing applied and the identity class's Gram has exactly chi eigenvalues above
-  // max(1e-12, 4 cutoff^2) tr (theta has rank <= chi, the bond dimension): every one of those
-  // Schmidt values is above 1e-6 s_0 and above the cutoff, so the truncated SVD would keep the bond
-  // as it is.  A QR move of the centre gives the same state and bond dimension without it.
-  const int chim = C.dims[i + 1];
-  if (kb == 0 && s.rank0 == chim && chim <= cap) {
-    if (ltr) move_right(s, C, i);
-    else move_left_qr(s, C, i + 1);
-    note_chi(C, chim);
-    __syncthreads();
-    return;
-  }
-  Factor F = svd_factor(s, C, theta, rows, cols, cap, true);
-  const int k = F.k;
-  if (ltr) {
-    for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
-      F.Vh[idx] = cscale(F.Vh[idx], C.sing[idx / (d * cr)]);
-  } else {
-    for (long long idx = threadIdx.x; idx < (long long)cl * d * k; idx += blockDim.x)
-      F.U[idx] = cscale(F.U[idx], C.sing[idx % k]);
-  }
-  __syncthreads();
-  block_copy(site_ptr(C, i), F.U, (long long)cl * d * k);
-  block_copy(site_ptr(C, i + 1), F.Vh, (long long)k * d * cr);
-  if (threadIdx.x == 0) {
-    C.dims[i + 1] = k;
-    C.meta[M_OC] = ltr ? i + 1 : i;
-    C.dstats[0] += F.disc;
-  }
-  note_chi(C, k);
-  __syncthreads();
-}
-
-// Alternating sweeps over the bonds of the last span; every CTA of the cluster runs the loop, only
-// the leader touches the MPS and the tableau.
-// sweep_cap > 0 overrides the handle's max_sweeps for this call; visit_cap > 0 stops after that
-// many bond visits (the centre is then left where the last split put it).
-__device__ void disentangle(Smem& s, Smem* lead, const Ctx& C, int sweep_cap, int visit_cap) {
-  cluster_sync();
-  if (C.meta[M_STATUS] != 0) return;   // a failed circuit does no further work
-  if (!C.meta[M_HAVE_SPAN]) return;
-  const int f = C.meta[M_F], l = C.meta[M_L];
-  if (l <= f) return;
-  const int max_sweeps = sweep_cap > 0 ? sweep_cap : C.e->max_sweeps;
-  int visits = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    const bool ltr = (sweep & 1) == 0;
-    if (C.rank == 0) move_center(s, C, ltr ? f : l);
-    int acc = 0;
-    bool capped = false;
-    for (int t = 0; t < l - f; ++t) {
-      if (visit_cap > 0 && visits >= visit_cap) {
-        capped = true;
-        break;
-      }
-      const int i = ltr ? f + t : l - 1 - t;
-      visit_bond(s, lead, C, i, ltr, &acc);
-      ++visits;
-    }
-    if (capped) break;
-    if (C.rank == 0 && threadIdx.x == 0) {
-      C.stats[S_SWEEPS] += 1;
-      s.bcast = acc;
-    }
-    cluster_sync();
-    const int acc_all = lead->bcast;
-    const int failed = C.meta[M_STATUS];
-    cluster_sync();   // every CTA has read bcast and the status before either changes
-    if (acc_all == 0 || failed != 0) break;
-  }
-}
-
-__device__ void init_tau(Smem& s, int d) {
-  if (threadIdx.x < 2 * d) {
-    double sn, cs;
-    sincospi((double)threadIdx.x / d, &sn, &cs);
-    s.tau[threadIdx.x] = make_double2(cs, sn);
-  }
-  __syncthreads();
-}
-
-// Clifford and non-Clifford steps touch only the leader's state; disentangling uses the cluster.
-__device__ void run_op(Smem& s, Smem* lead, const Ctx& C, const gcamps_op& op) {
-  switch (op.kind) {
-    case GCAMPS_OP_CLIFFORD:
-      if (C.rank == 0) apply_clifford(s, C, op.q0, op.q1, op.img);
-      break;
-    case GCAMPS_OP_NONCLIFFORD:
-      if (C.rank == 0 && C.meta[M_STATUS] == 0) apply_nonclifford(s, C, op.q0, op.phases);
-      break;
-    case GCAMPS_OP_DISENTANGLE:
-      disentangle(s, lead, C, op.q0, op.q1);
-      break;
-    default:
-      break;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(kThreads) k_run(Engine e, const gcamps_op* ops, const int32_t* begin) {
+__global__ void __launch_bounds__(kThreads, kMinCtas) k_run(Engine e, const gcamps_op* ops, const int32_t* begin) {
   __shared__ Smem s;
   const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
   Ctx C = make_ctx(e, c, rank);
@@ -1862,231 +17,6 @@ __global__ void __launch_bounds__(kThreads) k_run(Engine e, const gcamps_op* ops
   cluster_sync();
 }
 
-__global__ void __launch_bounds__(kThreads) k_run_all(Engine e, const gcamps_op* ops, int nops) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  for (int i = 0; i < nops; ++i) run_op(s, lead, C, ops[i]);
-  cluster_sync();
-}
-
-__global__ void __launch_bounds__(kThreads) k_single(Engine e, gcamps_op op) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  run_op(s, lead, C, op);
-  cluster_sync();
-}
-
-// Scores of every class on a caller-provided theta (chi_l, d, d, chi_r), through the same cluster
-// code as the disentangler: S2 of all classes and S_vN of all classes (no pruning).  Used to test
-// the scoring step on its own.
-__global__ void __launch_bounds__(kThreads) k_score_theta(Engine e, const double2* th, int cl, int cr,
-                                                          double* out_s2, double* out_vn, int* out_choice) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
-  cluster_sync();
-  if (c == 0 && rank == 0)
-    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-      out_s2[k] = s.s2[k];
-      out_vn[k] = s.vn[k];
-    }
-  cluster_sync();
-  int nev = 0;
-  const int kb = select_class(s, lead, C, th, cl, cr, &nev);   // the disentangler's own choice
-  if (c == 0 && rank == 0 && threadIdx.x == 0) {
-    out_choice[0] = kb;
-    out_choice[1] = nev;
-  }
-  cluster_sync();
-}
-
-__device__ void conj_weyl(Smem& s, const Ctx& C, const int8_t* xz, int* acc_x, int* acc_z, int* acc_r);
-
-// ---------------------------------------------------------------- adjoint phase gradient
-// <B| W(m a, m b) |M> for two MPS on the same n sites, W(a, b) = (x)_j X_j^{a_j} Z_j^{b_j} (no phase):
-// B's sites through site_ptr(CB, j) and CB.dims, M packed at mbase with bond dimensions mdims and
-// site offsets moff.  Transfer matrices E[a, a'] left to right, scratch in CB.
-__device__ double2 overlap_weyl(Smem& s, const Ctx& CB, const double2* mbase, const int* mdims,
-                                const long long* moff, const uint8_t* row, int mp) {
-  const Engine& e = *CB.e;
-  const int n = CB.n, d = CB.d;
-  double2* E = CB.scr + e.sl.b;
-  double2* T = CB.scr + e.sl.tmp;
-  double2* E2 = CB.scr + e.sl.u;
-  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    const int bl = CB.dims[j], br = CB.dims[j + 1], ml = mdims[j], mr = mdims[j + 1];
-    const double2* A = site_ptr(CB, j);
-    const double2* M = mbase + moff[j];
-    const int ax = (mp * row[j]) % d, bz = (mp * row[n + j]) % d;
-    // T[a, s, b'] = sum_{a'} E[a, a'] omega^{bz (s - ax)} M[a', s - ax, b']
-    for (long long idx = threadIdx.x; idx < (long long)bl * d * mr; idx += blockDim.x) {
-      const int bp = (int)(idx % mr), sd = (int)((idx / mr) % d), a = (int)(idx / ((long long)mr * d));
-      const int sp = (sd - ax + d) % d;
-      double2 acc = cz();
-      for (int ap = 0; ap < ml; ++ap) acc = cfma(E[(long long)a * ml + ap], M[((long long)ap * d + sp) * mr + bp], acc);
-      T[idx] = cmul(s.tau[(2 * bz * sp) % (2 * d)], acc);
-    }
-    __syncthreads();
-    // E'[b, b'] = sum_{a, s} conj(A[a, s, b]) T[a, s, b']
-    for (long long idx = threadIdx.x; idx < (long long)br * mr; idx += blockDim.x) {
-      const int b = (int)(idx / mr), bp = (int)(idx % mr);
-      double2 acc = cz();
-      for (int a = 0; a < bl; ++a)
-        for (int sd = 0; sd < d; ++sd)
-          acc = cfmac(A[((long long)a * d + sd) * br + b], T[((long long)a * d + sd) * mr + bp], acc);
-      E2[idx] = acc;
-    }
-    __syncthreads();
-    block_copy(E, E2, (long long)br * mr);
-    __syncthreads();
-  }
-  const double2 v = E[0];
-  __syncthreads();
-  return v;
-}
-
-// theta <- Q_q^dag theta on sites (i, i+1) of CB's MPS (undoing an applied disentangler), split by SVD
-// with the centre left at i + 1.
-__device__ void undo_disentangler(Smem& s, const Ctx& CB, int i, int q) {
-  const Engine& e = *CB.e;
-  const int d = CB.d, dd = d * d;
-  move_center(s, CB, i);
-  const int cl = CB.dims[i], ch = CB.dims[i + 1], cr = CB.dims[i + 2];
-  double2* theta = CB.scr + e.sl.theta;
-  double2* tmp = CB.scr + e.sl.tmp;
-  block_matmul(theta, site_ptr(CB, i), site_ptr(CB, i + 1), cl * d, ch, d * cr);
-  __syncthreads();
-  const double2* Q = e.candU + (long long)q * dd * dd;
-  const long long total = (long long)cl * dd * cr;
-  for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int b = (int)(idx % cr), u = (int)((idx / cr) % dd);
-    const long long a = idx / ((long long)cr * dd);
-    double2 acc = cz();
-    for (int v = 0; v < dd; ++v) acc = cfmac(Q[v * dd + u], theta[(a * dd + v) * cr + b], acc);   // conj(Q[v][u])
-    tmp[idx] = acc;
-  }
-  __syncthreads();
-  block_copy(theta, tmp, total);
-  __syncthreads();
-  const int bb = CB.bond_bound[i + 1];
-  Factor F = svd_factor(s, CB, theta, cl * d, d * cr, e.chi_max < bb ? e.chi_max : bb, false);
-  const int k = F.k;
-  for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)
-    F.Vh[idx] = cscale(F.Vh[idx], CB.sing[idx / (d * cr)]);
-  __syncthreads();
-  block_copy(site_ptr(CB, i), F.U, (long long)cl * d * k);
-  block_copy(site_ptr(CB, i + 1), F.Vh, (long long)k * d * cr);
-  if (threadIdx.x == 0) {
-    CB.dims[i + 1] = k;
-    CB.meta[M_OC] = i + 1;
-  }
-  __syncthreads();
-}
-
-// d Re<W> / d phi_{k,j} for every recorded non-Clifford gate k of circuit cf (gate k =
-// diag(e^{i phi_{k,j}})), by the adjoint method in the forward run's own Clifford frames:
-//   lambda_K = O psi with O = (W + W^dag)/2 = C (P + P^dag)/2 C^dag, P = C^dag W C (final frame);
-//   for k = K-1 .. 0: undo the disentanglers applied after gate k (Q^dag, reverse order), which puts
-//   lambda in the frame C'_k of gate k's MPO; take g_{k,j} = -2 Im <lambda| Pi_j |phi_k> with
-//   phi_k = snapshot k and Pi_j = (1/d) sum_m omega^{-mj} P_k^m (P_k = gate k's string); apply
-//   D_k^dag = sum_m c_m(-phi) P_k^m.  Cliffords between gates only change the frame.
-// Circuit slot cb holds lambda (its first n sites).  grad: d doubles per gate.
-__global__ void __launch_bounds__(kThreads) k_adjoint(Engine e, int cf, int cb, const int8_t* xz, double* grad) {
-  __shared__ Smem s;
-  __shared__ int ax[kMaxN], az[kMaxN], ar;
-  __shared__ uint8_t row[2 * kMaxN];
-  __shared__ long long moff[kMaxN + 1];
-  Ctx F = make_ctx(e, cf);
-  Ctx B = make_ctx(e, cb);
-  const int n = F.n, d = e.d;
-  B.n = n;   // the workspace slot has room for n_max >= n sites
-  init_tau(s, d);
-  for (int j = 0; j < n; ++j) block_copy(site_ptr(B, j), site_ptr(F, j), (long long)F.dims[j] * d * F.dims[j + 1]);
-  for (int j = threadIdx.x; j <= n; j += blockDim.x) B.dims[j] = F.dims[j];
-  if (threadIdx.x < M_COUNT) B.meta[threadIdx.x] = 0;
-  if (threadIdx.x < 4) B.dstats[threadIdx.x] = 0.0;
-  __syncthreads();
-  if (threadIdx.x == 0) B.meta[M_OC] = F.meta[M_OC];
-  conj_weyl(s, F, xz, ax, az, &ar);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    row[j] = (uint8_t)ax[j];
-    row[n + j] = (uint8_t)az[j];
-  }
-  if (threadIdx.x == 0) {
-    for (int m = 0; m < d; ++m) s.coef[m] = cz();
-    s.coef[1].x += 0.5;
-    s.coef[d - 1].x += 0.5;   // P^(d-1) = P^dag
-  }
-  __syncthreads();
-  bool has_w = false;
-  for (int j = 0; j < n; ++j) has_w |= (row[j] | row[n + j]) != 0;
-  if (has_w) mpo_apply(s, B, row, ar, false);
-  const int K = F.meta[M_NSNAP];
-  const int ndec = F.meta[M_NDEC];
-  for (int k = K - 1; k >= 0 && B.meta[M_STATUS] == 0; --k) {
-    const int* hd = e.snap_hdr + ((long long)cf * e.snap_max + k) * kSnapHdr;
-    const int dec0 = hd[3];
-    const int dec1 = k + 1 < K ? hd[kSnapHdr + 3] : ndec;
-    if (dec1 > kDecCap) {
-      if (threadIdx.x == 0) set_status(B, GCAMPS_EINVAL);
-      __syncthreads();
-      break;
-    }
-    for (int idx = dec1 - 1; idx >= dec0; --idx) {
-      const int bond = F.dec[2 * idx], q = F.dec[2 * idx + 1];
-      if (q) undo_disentangler(s, B, bond, q);
-    }
-    // gate k's string, phase and snapshot
-    for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) row[j] = (uint8_t)hd[kSnapDims + kMaxN + 1 + j];
-    if (threadIdx.x == 0) {
-      long long o = 0;
-      for (int j = 0; j < n; ++j) {
-        moff[j] = o;
-        o += (long long)hd[kSnapDims + j] * d * hd[kSnapDims + j + 1];
-      }
-      int sxz = 0;
-      for (int j = 0; j < n; ++j) sxz += row[j] * row[n + j];
-      s.ival[6] = sxz % d;
-    }
-    __syncthreads();
-    const int rk = hd[2], sxz = s.ival[6];
-    const double2* mbase = e.snap + (long long)cf * e.snap_stride + hd[0];
-    double2 proj[3] = {cz(), cz(), cz()};
-    for (int m = 0; m < d; ++m) {
-      const double2 ov = overlap_weyl(s, B, mbase, hd + kSnapDims, moff, row, m);
-      const double2 pm = cmul(s.tau[(rk * m + 2 * sxz * (m * (m - 1) / 2)) % (2 * d)], ov);   // <B|P^m|M>
-      for (int j = 0; j < d; ++j) proj[j] = cadd(proj[j], cscale(cmul(s.tau[(2 * d - (2 * m * j) % (2 * d)) % (2 * d)], pm), 1.0 / d));
-    }
-    if (threadIdx.x == 0)
-      for (int j = 0; j < d; ++j) grad[(long long)k * d + j] = -2.0 * proj[j].y;
-    // D_k^dag = sum_m c_m(-phi) P_k^m
-    const double* ph = e.snap_ph + ((long long)cf * e.snap_max + k) * 4;
-    if (threadIdx.x == 0)
-      for (int m = 0; m < d; ++m) {
-        double re = 0, im = 0;
-        for (int j = 0; j < d; ++j) {
-          double sn, cs;
-          sincos(-ph[j] - 2.0 * CUDART_PI * (double)(m * j) / d, &sn, &cs);
-          re += cs;
-          im += sn;
-        }
-        s.coef[m] = make_double2(re / d, im / d);
-      }
-    __syncthreads();
-    mpo_apply(s, B, row, rk, false);
-  }
-}
 
 // |0...0> with C = I, counters cleared.
 __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
@@ -2111,40 +41,13 @@ __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
   for (int j = threadIdx.x; j <= n; j += blockDim.x) C.dims[j] = 1;
   if (threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;
   if (threadIdx.x < S_COUNT) C.stats[threadIdx.x] = (threadIdx.x == S_MAXCHI) ? 1 : 0;
+  if (C.prof && threadIdx.x < P_COUNT) C.prof[threadIdx.x] = 0;
   if (threadIdx.x < 4) C.dstats[threadIdx.x] = 0.0;
 }
 
 // ------------------------------------------------------------------------------ readouts
 // <MPS| P' |MPS> with P' = C^dag W C = tau^r (x)_j X^{a_j} Z^{b_j}: the inverse-tableau rows are
 // multiplied in the order of W = prod_j X_j^{x_j} Z_j^{z_j}, then transfer matrices left to right.
-// P' = C^dag W C for W = (x)_j X_j^{x_j} Z_j^{z_j} (xz = x | z): the inverse-tableau rows multiplied in
-// the order of W with the Weyl product rule; exponents into acc_x, acc_z and the phase (units of tau)
-// into *acc_r, all in shared memory.
-__device__ void conj_weyl(Smem& s, const Ctx& C, const int8_t* xz, int* acc_x, int* acc_z, int* acc_r) {
-  const int n = C.n, d = C.d;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) acc_x[j] = acc_z[j] = 0;
-  if (threadIdx.x == 0) *acc_r = 0;
-  __syncthreads();
-  for (int q = 0; q < n; ++q) {
-    for (int kind = 0; kind < 2; ++kind) {
-      const int pw = kind == 0 ? xz[q] : xz[n + q];
-      const int rowi = kind == 0 ? n + q : q;
-      const uint8_t* R = C.ix + (long long)rowi * 2 * n;
-      for (int p = 0; p < pw; ++p) {
-        double loc = 0;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) loc += acc_z[j] * R[j];
-        const int tot = (int)llround(block_sum(loc, s));
-        __syncthreads();
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-          acc_x[j] = (acc_x[j] + R[j]) % d;
-          acc_z[j] = (acc_z[j] + R[n + j]) % d;
-        }
-        if (threadIdx.x == 0) *acc_r = (*acc_r + C.ir[rowi] + 2 * tot) % (2 * d);
-        __syncthreads();
-      }
-    }
-  }
-}
 
 __global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8_t* xz, double2* out) {
   __shared__ Smem s;
@@ -2188,20 +91,6 @@ __global__ void __launch_bounds__(kThreads) k_expect(Engine e, int c, const int8
     __syncthreads();
   }
   if (threadIdx.x == 0) out[0] = cmul(s.tau[acc_r], E[0]);
-}
-
-// Schmidt values of one bond: move the centre next to it and take the singular values.
-__global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond, double* sv, int* cnt) {
-  __shared__ Smem s;
-  Ctx C = make_ctx(e, c);
-  init_tau(s, e.d);
-  move_center(s, C, bond);
-  const int cl = C.dims[bond], cr = C.dims[bond + 1];
-  Factor F = svd_factor(s, C, site_ptr(C, bond), cl * e.d, cr, 1 << 30, false);
-  (void)F;
-  const int m = cl * e.d < cr ? cl * e.d : cr;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = C.sing[i];
-  if (threadIdx.x == 0) *cnt = m;
 }
 
 // Dense MPS vector mv[x] (d^n entries): contraction left to right through two ping-pong buffers
@@ -2367,46 +256,11 @@ __global__ void k_apply_clifford_dense(Engine e, int c, long long dim, const dou
   out[t] = acc;
 }
 
+
 }  // namespace
-
-// ---------------------------------------------------------------------------- host launchers
-// Engine kernels are launched with one thread-block cluster of e.csize CTAs per circuit.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_cluster(void (*kern)(KArgs...), const Engine& e, cudaStream_t st, Args... args) {
-  if (e.csize > 8) {
-    cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (a != cudaSuccess) return a;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(e.batch * e.csize), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)e.csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
-                               int* choice, cudaStream_t st) {
-  return launch_cluster(k_score_theta, e, st, e, th, cl, cr, s2, vn, choice);
-}
 
 cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st) {
   return launch_cluster(k_run, e, st, e, ops_dev, begin_dev);
-}
-
-cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
-  return launch_cluster(k_run_all, e, st, e, ops_dev, nops);
-}
-
-cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
-  return launch_cluster(k_single, e, st, e, op);
 }
 
 cudaError_t launch_reset(const Engine& e, cudaStream_t st) {
@@ -2416,16 +270,6 @@ cudaError_t launch_reset(const Engine& e, cudaStream_t st) {
 
 cudaError_t launch_expect(const Engine& e, int circuit, const int8_t* xz_dev, double2* out_dev, cudaStream_t st) {
   k_expect<<<1, kThreads, 0, st>>>(e, circuit, xz_dev, out_dev);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint(const Engine& e, int cf, int cb, const int8_t* xz_dev, double* grad_dev, cudaStream_t st) {
-  k_adjoint<<<1, kThreads, 0, st>>>(e, cf, cb, xz_dev, grad_dev);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev, cudaStream_t st) {
-  k_schmidt<<<1, kThreads, 0, st>>>(e, circuit, bond, s_dev, cnt_dev);
   return cudaGetLastError();
 }
 
@@ -2449,127 +293,6 @@ cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, l
   k_apply_clifford_dense<<<(unsigned)((nys + blk - 1) / blk), blk, 0, st>>>(e, circuit, dim, mv, s0, aidx, bdig, rho,
                                                                           ys_dev, nys, out_dev);
   return cudaGetLastError();
-}
-
-// ------------------------------------------------------ class scores without device allocation
-// gcamps_score_theta_noalloc runs the scoring and the class choice of k_score_theta with all of its
-// scratch in the static array below instead of a handle's allocation.  Per CTA: kWarps warp-level
-// buffers of kSmallStride entries and one CTA-level buffer (theta' of up to kStaticSide^2 entries,
-// its Gram, eigenvalue arrays); then the last-visit score record, the status words and the FP32 copy
-// of theta used by the screen.
-constexpr long long kStaticTcap = (long long)kStaticSide * kStaticSide;
-constexpr long long kStaticCtaRaw = (long long)kWarps * kSmallStride + 2 * kStaticTcap + kStaticSide + 64;
-constexpr long long kStaticCta = (kStaticCtaRaw + 15) / 16 * 16;                  // 256-byte multiples
-constexpr long long kStaticScores = ((3LL * kMaxK + 2 + 2LL * kSmall + 1) / 2 + 15) / 16 * 16;
-constexpr long long kStaticMeta = 16;                                             // >= M_COUNT ints
-constexpr long long kStaticTh32 = ((kStaticTcap + 1) / 2 + 15) / 16 * 16;          // float2 pairs
-constexpr long long kStaticWords = kStaticCluster * kStaticCta + kStaticScores + kStaticMeta + kStaticTh32;
-static_assert(2 * kStaticMeta >= M_COUNT, "status words");
-static_assert(kStaticWords * 16 == 1696256, "scratch size stated in gcamps.h");
-// 1,696,256 bytes, held by every device that loads the library.  Calls reuse it and it keeps the
-// last call's contents; only the status words must start at zero, and each call clears them itself.
-static __device__ __align__(256) double2 g_static_scratch[kStaticWords];
-// Class unitaries for d = 2 then d = 3 ([K][d^4]) and their images ([K][20]), set once per device.
-static __device__ __align__(256) double2 g_static_candU[kStaticK2 * 16 + kStaticK3 * 81];
-static __device__ __align__(256) float2 g_static_candU32[kStaticK2 * 16 + kStaticK3 * 81];
-static __device__ __align__(256) int32_t g_static_candImg[(kStaticK2 + kStaticK3) * 20];
-
-// Device addresses of the arrays above, per device (host code only sees host-side stand-ins under
-// their names).
-struct StaticPtrs {
-  double2* scratch;
-  double2* candU;
-  float2* candU32;
-  int32_t* candImg;
-};
-static StaticPtrs g_static_ptrs[kStaticMaxDevices];
-
-// The same steps as k_score_theta for one theta; the cluster is the only one of the launch.
-__global__ void __launch_bounds__(kThreads) k_score_theta_static(Engine e, const double2* th, int cl, int cr,
-                                                                 double* out_s2, double* out_vn,
-                                                                 int32_t* out_choice) {
-  __shared__ Smem s;
-  const int rank = blockIdx.x % e.csize;
-  Ctx C = {};
-  C.e = &e;
-  C.c = 0;
-  C.rank = rank;
-  C.csize = e.csize;
-  C.d = e.d;
-  C.K = e.K;
-  C.cta = e.cscr + (long long)rank * e.cl.total;
-  C.meta = e.meta;
-  C.th32 = reinterpret_cast<float2*>(e.cscr + kStaticCluster * kStaticCta + kStaticScores + kStaticMeta);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  if (rank == 0 && threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;   // status of this call only
-  cluster_sync();
-  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
-  cluster_sync();
-  if (rank == 0)
-    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-      out_s2[k] = s.s2[k];
-      out_vn[k] = s.vn[k];
-    }
-  cluster_sync();
-  int nev = 0;
-  const int kb = select_class(s, lead, C, th, cl, cr, &nev);
-  cluster_sync();
-  if (rank == 0 && threadIdx.x == 0) {
-    out_choice[0] = kb;
-    out_choice[1] = nev;
-    out_choice[2] = C.meta[M_STATUS];
-  }
-}
-
-cudaError_t static_setup(int device, const double* u2, const int32_t* img2, const double* u3,
-                         const int32_t* img3) {
-  if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
-  StaticPtrs p = {};
-  cudaError_t ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.scratch), g_static_scratch);
-  if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candU), g_static_candU);
-  if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candU32), g_static_candU32);
-  if (ce == cudaSuccess) {
-    float u32[2 * (kStaticK2 * 16 + kStaticK3 * 81)];
-    for (int i = 0; i < 2 * kStaticK2 * 16; ++i) u32[i] = (float)u2[i];
-    for (int i = 0; i < 2 * kStaticK3 * 81; ++i) u32[2 * kStaticK2 * 16 + i] = (float)u3[i];
-    ce = cudaMemcpyToSymbol(g_static_candU32, u32, sizeof u32, 0);
-  }
-  if (ce == cudaSuccess) ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&p.candImg), g_static_candImg);
-  if (ce == cudaSuccess) ce = cudaMemcpyToSymbol(g_static_candU, u2, sizeof(double2) * kStaticK2 * 16, 0);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyToSymbol(g_static_candU, u3, sizeof(double2) * kStaticK3 * 81, sizeof(double2) * kStaticK2 * 16);
-  if (ce == cudaSuccess) ce = cudaMemcpyToSymbol(g_static_candImg, img2, sizeof(int32_t) * kStaticK2 * 20, 0);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyToSymbol(g_static_candImg, img3, sizeof(int32_t) * kStaticK3 * 20, sizeof(int32_t) * kStaticK2 * 20);
-  if (ce == cudaSuccess) g_static_ptrs[device] = p;
-  return ce;
-}
-
-cudaError_t launch_score_theta_static(int device, int d, double tie_tol, const double2* th, int cl, int cr,
-                                      double* s2, double* vn, int32_t* choice, cudaStream_t st) {
-  if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
-  const StaticPtrs& p = g_static_ptrs[device];
-  if (!p.scratch || !p.candU || !p.candU32 || !p.candImg) return cudaErrorInitializationError;
-  Engine e = {};
-  e.d = d;
-  e.K = d == 2 ? kStaticK2 : kStaticK3;
-  e.batch = 1;
-  e.csize = kStaticCluster;
-  e.tie_tol = tie_tol;
-  e.tcap = kStaticTcap;
-  e.wcap = kStaticTcap;
-  e.scap = kStaticTcap;
-  e.cscr = p.scratch;
-  e.cl.warp = 0;
-  e.cl.block = (long long)kWarps * kSmallStride;
-  e.cl.total = kStaticCta;
-  e.lastsc = reinterpret_cast<double*>(p.scratch + kStaticCluster * kStaticCta);
-  e.meta = reinterpret_cast<int*>(p.scratch + kStaticCluster * kStaticCta + kStaticScores);
-  e.candU = p.candU + (d == 2 ? 0 : kStaticK2 * 16);
-  e.candU32 = p.candU32 + (d == 2 ? 0 : kStaticK2 * 16);
-  e.candImg = p.candImg + (d == 2 ? 0 : kStaticK2 * 20);
-  return launch_cluster(k_score_theta_static, e, st, e, th, cl, cr, s2, vn, choice);
 }
 
 }  // namespace gcx

@@ -1,0 +1,60 @@
+// Single-operation and all-circuits launches of libgcamps (arxiv 2511.06672, Sec. 3), and the
+// Schmidt-value readout of one bond (Sec. 2.4).
+
+#include "gcamps_device.cuh"
+
+namespace gcx {
+namespace {
+
+__global__ void __launch_bounds__(kThreads, kMinCtas) k_run_all(Engine e, const gcamps_op* ops, int nops) {
+  __shared__ Smem s;
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  for (int i = 0; i < nops; ++i) run_op(s, lead, C, ops[i]);
+  cluster_sync();
+}
+
+__global__ void __launch_bounds__(kThreads, kMinCtas) k_single(Engine e, gcamps_op op) {
+  __shared__ Smem s;
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  run_op(s, lead, C, op);
+  cluster_sync();
+}
+
+
+// Schmidt values of one bond: move the centre next to it and take the singular values.
+__global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond, double* sv, int* cnt) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, c);
+  init_tau(s, e.d);
+  move_center(s, C, bond);
+  const int cl = C.dims[bond], cr = C.dims[bond + 1];
+  Factor F = svd_factor(s, C, site_ptr(C, bond), cl * e.d, cr, 1 << 30, false);
+  (void)F;
+  const int m = cl * e.d < cr ? cl * e.d : cr;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = C.sing[i];
+  if (threadIdx.x == 0) *cnt = m;
+}
+
+
+}  // namespace
+
+cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
+  return launch_cluster(k_run_all, e, st, e, ops_dev, nops);
+}
+
+cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
+  return launch_cluster(k_single, e, st, e, op);
+}
+
+cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev, cudaStream_t st) {
+  k_schmidt<<<1, kThreads, 0, st>>>(e, circuit, bond, s_dev, cnt_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace gcx

@@ -509,6 +509,10 @@ int gcamps_create_batch(int batch, int n, int d, int chi_max, const gcamps_opts*
   return gcamps_create_batch_uneven(batch, nv.data(), d, chi_max, o, out);
 }
 
+int gcamps_batch_create(int count, const int32_t* n, int d, int chi_max, const gcamps_opts* o, gcamps_t** out) {
+  return gcamps_create_batch_uneven(count, n, d, chi_max, o, out);
+}
+
 int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max, const gcamps_opts* o,
                                gcamps_t** out) {
   if (!out) return GCAMPS_EINVAL;
@@ -632,6 +636,8 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   bytes = align(bytes + (size_t)nslots * gcx::M_COUNT * sizeof(int));
   const size_t o_stats = bytes;
   bytes = align(bytes + (size_t)nslots * gcx::S_COUNT * sizeof(long long));
+  const size_t o_prof = bytes;
+  bytes = align(bytes + (size_t)nslots * gcx::P_COUNT * sizeof(long long));
   const size_t o_dstats = bytes;
   bytes = align(bytes + (size_t)nslots * 4 * sizeof(double));
   const size_t o_dec = bytes;
@@ -690,6 +696,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.dims = (int*)(base + o_dims);
   e.meta = (int*)(base + o_meta);
   e.stats = (long long*)(base + o_stats);
+  e.prof = (long long*)(base + o_prof);
   e.dstats = (double*)(base + o_dstats);
   e.dec = (int*)(base + o_dec);
   e.weyl = (int8_t*)(base + o_weyl);
@@ -916,7 +923,7 @@ static int check_circuit(gcamps_t* h, int circuit) {
   return GCAMPS_OK;
 }
 
-int gcamps_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* re, double* im) {
+int gcamps_batch_expect_weyl(gcamps_t* h, int circuit, const int32_t* x, const int32_t* z, double* re, double* im) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
   const int n = h->nq[circuit], d = h->e.d;
@@ -946,7 +953,7 @@ int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int
   if (!x || !z || !value || !ngates || cap_gates < 0 || (cap_gates > 0 && !grad))
     return fail(h, GCAMPS_EINVAL, "null argument");
   double re = 0, im = 0;
-  rc = gcamps_expect_weyl(h, circuit, x, z, &re, &im);   // also checks x, z and the device status
+  rc = gcamps_batch_expect_weyl(h, circuit, x, z, &re, &im);   // also checks x, z and the device status
   if (rc) return rc;
   *value = re;
   int meta[gcx::M_COUNT];
@@ -1034,7 +1041,7 @@ int gcamps_statevector(gcamps_t* h, int circuit, double* re, double* im) {
   return statevector_impl(h, circuit, nullptr, dim, re, im);
 }
 
-int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im) {
+int gcamps_batch_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re, double* im) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
   if (!digits || !re || !im) return fail(h, GCAMPS_EINVAL, "null argument");
@@ -1048,7 +1055,7 @@ int gcamps_amplitude(gcamps_t* h, int circuit, const int32_t* digits, double* re
   return statevector_impl(h, circuit, &yy, 1, re, im);
 }
 
-int gcamps_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
+int gcamps_batch_get_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t* phase) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
   const int n = h->nq[circuit];
@@ -1070,7 +1077,7 @@ int gcamps_get_inverse_tableau(gcamps_t* h, int circuit, uint8_t* exps, uint8_t*
   return device_status(h);
 }
 
-int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
+int gcamps_batch_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
   int rc = check_circuit(h, circuit);
   if (rc) return rc;
   if (!chi) return fail(h, GCAMPS_EINVAL, "null output");
@@ -1082,6 +1089,16 @@ int gcamps_get_bond_dims(gcamps_t* h, int circuit, int32_t* chi) {
   for (int j = 0; j < n - 1; ++j) chi[j] = dims[j + 1];
   return device_status(h);
 }
+
+// The single-circuit forms of the contract (circuit 0 of the handle).
+int gcamps_expect_weyl(gcamps_t* h, const int32_t* x, const int32_t* z, double* re, double* im) {
+  return gcamps_batch_expect_weyl(h, 0, x, z, re, im);
+}
+int gcamps_amplitude(gcamps_t* h, const int32_t* digits, double* re, double* im) {
+  return gcamps_batch_amplitude(h, 0, digits, re, im);
+}
+int gcamps_get_tableau(gcamps_t* h, uint8_t* exps, uint8_t* phase) { return gcamps_batch_get_tableau(h, 0, exps, phase); }
+int gcamps_get_bond_dims(gcamps_t* h, int32_t* chi) { return gcamps_batch_get_bond_dims(h, 0, chi); }
 
 int gcamps_get_schmidt(gcamps_t* h, int circuit, int bond, double* s, int32_t* count) {
   int rc = check_circuit(h, circuit);
@@ -1169,6 +1186,19 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   return device_status(h);
 }
 
+int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (cap < 0 || (cap > 0 && !out)) return fail(h, GCAMPS_EINVAL, "bad profile buffer");
+  long long p[gcx::P_COUNT];
+  GC_CUDA(h, cudaMemcpyAsync(p, h->e.prof + (long long)circuit * gcx::P_COUNT, sizeof p, cudaMemcpyDeviceToHost,
+                             h->stream));
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < cap && i < gcx::P_COUNT; ++i) out[i] = p[i];
+  if (count) *count = gcx::P_COUNT;
+  return device_status(h);
+}
+
 int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* s2, double* vn,
                        int32_t* choice) {
   if (!h) return GCAMPS_EINVAL;
@@ -1199,12 +1229,40 @@ int gcamps_score_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, d
   return device_status(h);
 }
 
+int gcamps_estimate_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta, double* est, double* bound) {
+  if (!h) return GCAMPS_EINVAL;
+  const int d = h->e.d;
+  if (!theta || !est || !bound || chi_l < 1 || chi_r < 1 || chi_l > h->e.maxdim / d || chi_r > h->e.maxdim / d)
+    return fail(h, GCAMPS_EINVAL, "bad theta shape or null pointer");
+  const size_t nel = (size_t)chi_l * d * d * chi_r;
+  double2* th = nullptr;
+  double* out = nullptr;
+  cudaError_t ce = cudaMalloc(&th, nel * sizeof(double2));
+  if (ce == cudaSuccess) ce = cudaMalloc(&out, 2 * gcx::kMaxK * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(th, theta, nel * sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess)
+    ce = gcx::launch_estimate_theta(h->e, th, chi_l, chi_r, out, out + gcx::kMaxK, h->stream);
+  std::vector<double> host(2 * gcx::kMaxK);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(host.data(), out, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (th) cudaFree(th);
+  if (out) cudaFree(out);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "estimate_theta");
+  for (int k = 0; k < h->e.K; ++k) {
+    est[k] = host[k];
+    bound[k] = host[gcx::kMaxK + k];
+  }
+  return device_status(h);
+}
+
 int gcamps_score_theta_noalloc(int d, int chi_l, int chi_r, const double* theta_dev, double* s2_dev, double* vn_dev,
                                int32_t* choice_dev, double tie_tol, void* cuda_stream) {
   if ((d != 2 && d != 3) || !theta_dev || !s2_dev || !vn_dev || !choice_dev || chi_l < 1 || chi_r < 1 ||
       !(tie_tol >= 0.0))
     return GCAMPS_EINVAL;
-  if (chi_l * d > GCAMPS_NOALLOC_MAX_SIDE || chi_r * d > GCAMPS_NOALLOC_MAX_SIDE) return GCAMPS_ESIZE;
+  // chi d <= the limit, compared without forming chi d (which could wrap for chi near INT_MAX)
+  if (chi_l > GCAMPS_NOALLOC_MAX_SIDE / d || chi_r > GCAMPS_NOALLOC_MAX_SIDE / d) return GCAMPS_ESIZE;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return GCAMPS_ECUDA;
   if (dev < 0 || dev >= gcx::kStaticMaxDevices) return GCAMPS_ECUDA;

@@ -10,6 +10,7 @@
 namespace gcx {
 
 constexpr int kThreads = 256;             // threads per CTA; a cluster of CTAs runs one circuit
+constexpr int kMinCtas = 2;               // resident CTAs per SM the engine kernels are compiled for (128 registers)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCluster = 16;           // CTAs per circuit (thread-block cluster)
 constexpr int kSmall = 729;               // warp-level scoring when theta' and its Gram fit this many entries
@@ -32,6 +33,13 @@ static_assert(kSnapDims + (kMaxN + 1) + 2 * kMaxN <= kSnapHdr, "snapshot header"
 // stats[] counters per circuit (int64)
 enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN, S_SVD, S_JSWEEPS, S_JMAX,
             S_QR, S_COUNT };
+// prof[] counters per circuit (int64, the layout gcamps_get_profile documents): SM cycles of the leader CTA
+// per phase, then per bond-visit size bucket (m = min(chi_l d, d chi_r) <= 9, 27, 54, 81, larger) the
+// visits, their cycles, their exact (FP64) evaluations and their FP32 von Neumann estimates.
+enum Prof { P_CLIFF = 0, P_MPO, P_CENTER, P_THETA, P_SCREEN, P_EST, P_EXACT, P_DECIDE, P_APPLYQ, P_SPLIT,
+            P_QRMOVE, P_VISITS = 12, P_VCYC = 17, P_VEXACT = 22, P_VEST = 27, P_COUNT = 32 };
+constexpr int kProfBuckets = 5;
+static_assert(P_COUNT == GCAMPS_PROF_WORDS, "profile layout stated in gcamps.h");
 
 // Scratch areas of one circuit, as element offsets (double2) from its scratch base.
 struct ScratchLayout {
@@ -70,6 +78,7 @@ struct Engine {
   int* dims;                                // [batch][n+1]
   int* meta;                                // [batch][M_COUNT]
   long long* stats;                         // [batch][S_COUNT]
+  long long* prof;                          // [batch][P_COUNT]
   double* dstats;                           // [batch][4]: discarded weight, FP64 scoring flops, FP32 screen flops, spare
   int* dec;                                 // [batch][kDecCap][2]
   int8_t* weyl;                             // [batch][2n]
@@ -98,6 +107,8 @@ cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, l
                                const int32_t* ys_dev, long long nys, void* work, cudaStream_t st);
 cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
                                int* choice, cudaStream_t st);
+cudaError_t launch_estimate_theta(const Engine& e, const double2* th, int cl, int cr, double* est, double* bd,
+                                  cudaStream_t st);
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
                            cudaStream_t st);
 // Adjoint gradient of Re<W> for circuit cf, using circuit slot cb as the backward workspace:

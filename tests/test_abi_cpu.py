@@ -160,3 +160,14 @@ def test_named_images_match_dense_conjugation(lib, d):
         G.named_images(d, 6)
     with pytest.raises(G.GcampsError):
         G.named_images(5, G.GATE_H)
+
+
+def test_noalloc_size_check_cannot_wrap(lib):
+    """gcamps_score_theta_noalloc rejects shapes above its static limit before any CUDA call, including
+    chi values whose product with d would wrap a 32-bit int (715827883 * 3 = 2^31 + 1).  The pointers are
+    never dereferenced on this path."""
+    from paper_2511_06672_gb300 import _native as N
+    fake = C.c_void_p(16)
+    for d, cl, cr in [(3, 715827883, 1), (3, 1, 715827883), (2, 1073741825, 1), (3, 28, 1), (2, 1, 41)]:
+        rc = lib.gcamps_score_theta_noalloc(d, cl, cr, fake, fake, fake, fake, 1e-10, None)
+        assert rc == N.ESIZE, (d, cl, cr, rc)

@@ -11,6 +11,8 @@ alone in a fresh process and after the other GPU tests.
 import numpy as np
 import pytest
 
+from oracle.gcamps import GCAMPS
+
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
@@ -77,6 +79,9 @@ def test_noalloc_matches_handle_scoring_twice(G, d, cl, cr):
             assert np.max(np.abs(vn - vn_ref)) <= TOL
             assert int(ch[0]) == choice_ref and int(ch[1]) == nev_ref
             assert int(ch[2]) == 0
+            # and directly against the oracle's SVD entropies of every class
+            vn_oracle = GCAMPS(2, d, chi_max=81).score_bond(theta)
+            assert np.max(np.abs(vn - vn_oracle)) <= TOL
     finally:
         sim.close()
 
@@ -88,7 +93,7 @@ def test_noalloc_rejects_shapes_above_the_static_limit(G):
     th = torch.zeros(4, dtype=torch.complex128, device=dev)
     out = torch.zeros(90, dtype=torch.float64, device=dev)
     ch = torch.zeros(3, dtype=torch.int32, device=dev)
-    for d, cl, cr in [(3, 28, 3), (3, 3, 28), (2, 41, 1)]:
+    for d, cl, cr in [(3, 28, 3), (3, 3, 28), (2, 41, 1), (3, 715827883, 1)]:
         with pytest.raises(G.GcampsError) as ei:
             G.score_theta_noalloc(d, cl, cr, th, out, out, ch)
         assert ei.value.code == N.ESIZE
