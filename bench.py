@@ -41,9 +41,22 @@ N, LAYERS, T, CHI, CUTOFF = 32, 24, 32, 256, 1e-12
 SEEDS_PER_D = 8
 WORKLOAD = "gcamps-brickwork-n32-L24-T32-chi256-d2+d3-8seeds"
 METRIC = "T-gates/s"
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the engine is FP64-ALU bound
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table), used only without a measurement
 # GB300 FP32 (non-tensor) nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAKS_FILE = os.path.join(ROOT, "profiles", "arith_peaks_gb300.json")
+
+
+def arith_peaks():
+    """(FP64 peak, FP32 peak, source): the measured multiply-add rates of profiles/arith_peaks_gb300.json
+    (python -m paper_2511_06672_gb300.peaks), else the nominal figures."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return (float(p["fp64_fma_tflops"]), float(p["fp32_fma_tflops"]),
+                f"measured ({os.path.relpath(PEAKS_FILE, ROOT)}, {p.get('when', '?')})")
+    except (OSError, ValueError, KeyError):
+        return FP64_NOMINAL_TFLOPS, FP32_NOMINAL_TFLOPS, "nominal (no measurement committed)"
 ENGINE_SRC = os.path.join(ROOT, "paper_2511_06672_gb300", "csrc", "gcamps_engine.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_run_dram_bench_workload.txt")
 
@@ -169,28 +182,47 @@ def workload_ops(G, d, rank):
     return np.concatenate(ops), np.array(begin, dtype=np.int32)
 
 
-def cpu_oracle_sample(budget_s: float = 20.0):
-    """Time the oracle (as it stands) on whole benchmark circuits, qubit then qutrit seeds in
-    turn, until ~budget_s of CPU time; single thread."""
+def bench_circuits(rank: int = 0):
+    """The benchmark's circuits of one rank, (d, seed), in the order the CPU oracle runs them: qubit and qutrit
+    circuits of each seed in turn."""
+    return [(d, seed) for seed in rank_seeds(rank) for d in (2, 3)]
+
+
+def cpu_oracle_sample(budget_s=None):
+    """Time the oracle (as it stands, one thread) on whole benchmark circuits in bench_circuits order: all 16
+    (budget_s None), or as many as start within budget_s seconds.  Returns (T gates / s, seconds, names,
+    per-circuit seconds)."""
     from synth import brickwork_circuit
     from oracle.gcamps import GCAMPS
-    t_gates = 0
-    circuits = []
+    t_gates, names, secs = 0, [], []
     t0 = time.perf_counter()
-    seed = 1
-    while True:
-        for d in (2, 3):
-            g = GCAMPS(N, d, chi_max=CHI, cutoff=CUTOFF)
-            for gt in brickwork_circuit(N, d, LAYERS, T, seed):
-                g.apply_gate(gt)
-                if not hasattr(gt, "sp_index"):
-                    g.disentangle()
-                    t_gates += 1
-            circuits.append(f"d{d}s{seed}")
-            if time.perf_counter() - t0 > budget_s:
-                el = time.perf_counter() - t0
-                return t_gates / el, el, circuits
-        seed += 1
+    for d, seed in bench_circuits(0):
+        if budget_s is not None and names and time.perf_counter() - t0 > budget_s:
+            break
+        c0 = time.perf_counter()
+        g = GCAMPS(N, d, chi_max=CHI, cutoff=CUTOFF)
+        for gt in brickwork_circuit(N, d, LAYERS, T, seed):
+            g.apply_gate(gt)
+            if not hasattr(gt, "sp_index"):
+                g.disentangle()
+                t_gates += 1
+        names.append(f"d{d}s{seed}")
+        secs.append(time.perf_counter() - c0)
+    el = time.perf_counter() - t0
+    return t_gates / el, el, names, secs
+
+
+def cpu_baseline_subprocess(budget_s: float):
+    """The oracle's bounded sample in a fresh single-threaded process (BLAS threads pinned to 1 before numpy
+    loads): the GPU arm's cpu_baseline."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1", RANK="0",
+               WORLD_SIZE="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--ref-budget-s", str(budget_s),
+           "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": line["value"], "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+            "sample": line["cpu_baseline"]["sample"]}
 
 
 def _oracle_whole_circuit(shape):
@@ -602,6 +634,10 @@ def run_case(args):
     for b in range(args.case_batch):
         o = G.ops_from_gates(brickwork_circuit(args.case_n, args.case_d, args.case_layers, args.case_t,
                                                args.case_seed + b), args.case_d)
+        if args.case_t_prefix > 0:   # the circuit up to the disentangling after its first case_t_prefix T gates
+            ends = np.nonzero(o["kind"] == G.OP_DISENTANGLE)[0]
+            if len(ends) > args.case_t_prefix:
+                o = o[: ends[args.case_t_prefix - 1] + 1]
         ops.append(o)
         begin.append(begin[-1] + len(o))
     ops = np.concatenate(ops)
@@ -617,6 +653,7 @@ def run_case(args):
         line = {"workload": "case", "rep": r, "seconds": el, "d": args.case_d, "n": args.case_n,
                 "layers": args.case_layers, "t_gates": args.case_t, "chi_max": args.case_chi,
                 "seed": args.case_seed, "batch": args.case_batch, "cluster": args.cluster,
+                "t_prefix": args.case_t_prefix,
                 "stats": st[0] if args.case_batch == 1 else st,
                 "profile": [sim.profile(c) for c in range(args.case_batch)]}
         print(json.dumps(line), flush=True)
@@ -625,32 +662,38 @@ def run_case(args):
 
 
 def run_reference(args):
+    """--impl reference: the FP64 CPU oracle (as it stands, one thread) on the GPU arm's own 16 circuits, one
+    whole pass of them in the timed region, split over the --steps steps in bench_circuits order (with
+    --ref-budget-s: only the circuits that start within that many seconds).  Warm-up steps run the first
+    circuit."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    per_step = []
-    tg_total = 0
-    samples = []
-    for i in range(args.warmup + args.steps):
-        rate, el, circ = cpu_oracle_sample(budget_s=args.ref_step_s)
-        if i >= args.warmup:
-            per_step.append(el)
-            tg_total += rate * el
-            samples.extend(circ)
-    el = sum(per_step)
-    value = tg_total / el
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_sample(budget_s=0.0)
+    rate, el, names, secs = cpu_oracle_sample(budget_s=args.ref_budget_s)
+    full = args.ref_budget_s is None
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "T-gates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "whole circuits d=2/d=3 alternating, seeds from 1"},
-        "cpu_baseline": {"value": value, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(samples)} whole circuits ({','.join(samples[:6])}...), ~{args.ref_step_s}s per step"},
-        "e2e": {"value": value, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": bench_config(world if full else 1),
+        "cpu_baseline": {"value": rate, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+                         "sample": (f"all {len(names)} benchmark circuits once" if full and len(names) == 2 * SEEDS_PER_D
+                                    else f"{len(names)} whole circuits {','.join(names)}") + f" ({el:.1f} s, 1 thread)",
+                         "seconds_per_circuit": {n_: round(t_, 3) for n_, t_ in zip(names, secs)}},
+        "e2e": {"value": rate, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_config(world: int) -> dict:
+    """The workload of both arms (the same dict in the GPU line and the reference line)."""
+    return {"workload": WORKLOAD, "n": N, "layers": LAYERS, "t_gates": T, "chi_max": CHI, "cutoff": CUTOFF,
+            "d": [2, 3], "seeds_per_d": SEEDS_PER_D, "circuits_per_rank": 2 * SEEDS_PER_D,
+            "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}"}
 
 
 def main():
@@ -671,6 +714,7 @@ def main():
     ap.add_argument("--case-seed", type=int, default=1)
     ap.add_argument("--case-batch", type=int, default=1)
     ap.add_argument("--case-repeat", type=int, default=2)
+    ap.add_argument("--case-t-prefix", type=int, default=0, help="run only up to the K-th T gate (0: all)")
     ap.add_argument("--chi-layers-d", default="2,3")
     ap.add_argument("--chi-layers-n", default="6,8")
     ap.add_argument("--chi-layers-factor", type=int, default=2, help="layers = this x n")
@@ -680,7 +724,9 @@ def main():
     ap.add_argument("--batched-count", type=int, default=64)
     ap.add_argument("--batched-nmax", type=int, default=24, help="n and layers uniform in [16, this]")
     ap.add_argument("--batched-clusters", default="8,4", help="CTAs per circuit tried by the autotuner")
-    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--ref-step-s", type=float, default=8.0, help="batched reference arm: seconds per step")
+    ap.add_argument("--ref-budget-s", type=float, default=None,
+                    help="bench reference arm: only the circuits that start within this many seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
     ap.add_argument("--cluster-qubit", type=int, default=4, help="CTAs per qubit circuit (0: --cluster)")
@@ -808,13 +854,14 @@ def main():
     launch_s = sum(engine_times) / len(engine_times)
     achieved = flops_per_launch / launch_s / 1e12
     screen_achieved = screen_per_launch / launch_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": engine_traffic(),
+    fp64_peak, fp32_peak, peak_src = arith_peaks()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": engine_traffic(),
                 "kernel": "k_run (engine, one launch per d)", "flops_per_launch": flops_per_launch,
-                "launch_ms": 1e3 * launch_s, "peak_source": "FP64 nominal, profiling recipe table",
+                "launch_ms": 1e3 * launch_s, "peak_source": "FP64 fma, " + peak_src,
                 "fp32_screen": {"flops_per_launch": screen_per_launch, "achieved": screen_achieved,
-                                "peak": FP32_PEAK_TFLOPS, "frac": screen_achieved / FP32_PEAK_TFLOPS,
-                                "peak_source": "FP32 nominal from unit counts and the 2.07 GHz maximum clock"}}
+                                "peak": fp32_peak, "frac": screen_achieved / fp32_peak,
+                                "peak_source": "FP32 fma, " + peak_src}}
 
     progress(f"timed steps: {[round(t, 3) for t in times]}")
     # end to end: host gate lists, copies and readback inside the timed region
@@ -825,6 +872,8 @@ def main():
     h2d = sum(ops_host[d][0].nbytes + ops_host[d][1].nbytes for d in (2, 3))
     d2h = 0
     for _ in range(max(2, args.steps)):
+        flush.fill_(1.0)   # L2 flushed as before the device-timed steps, outside the timed region
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for d in (2, 3):
             sims[d].reset()
@@ -842,10 +891,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "T-gates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "layers": LAYERS, "t_gates": T, "chi_max": CHI,
-                   "cutoff": CUTOFF, "d": [2, 3], "circuits_per_rank": 2 * SEEDS_PER_D,
-                   "l2": "512 MiB flush before every timed step", "parallelism": f"replicas x{world}",
-                   "cluster_ctas_per_circuit": {"d2": cluster[2], "d3": cluster[3]}},
+        "config": bench_config(world),
+        "launch": {"cluster_ctas_per_circuit": {"d2": cluster[2], "d3": cluster[3]}},
         "candidates_per_s": cand_rate,
         "vn_evaluated_fraction": vn_frac,
         "e2e": {"value": e2e_value, "unit": "T-gates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -855,9 +902,7 @@ def main():
     }
     progress(f"e2e steps: {[round(t, 3) for t in e2e_times]}")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el, circ = cpu_oracle_sample(budget_s=15.0)
-        line["cpu_baseline"] = {"value": rate, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
-                                "sample": f"whole circuits {','.join(circ)} ({el:.1f} s, 1 thread)"}
+        line["cpu_baseline"] = cpu_baseline_subprocess(15.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     for d in (2, 3):

@@ -186,6 +186,12 @@ int gcamps_num_qudits(gcamps_t* h, int circuit);
  * (a launch shape of this library).  EINVAL for other sizes. */
 int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
 
+/* Most sweeps one Jacobi SVD may take before the engine gives up with GCAMPS_ENOCONV (reported by the next
+ * synchronising call; the circuit does no further MPS work until gcamps_reset).  Default 60.  Synchronises
+ * the handle's stream; applies to the following launches.  No counterpart in the paper: an iteration cap of
+ * this library, settable so that the failure path can be exercised.  EINVAL outside 1..1000. */
+int gcamps_set_jacobi_cap(gcamps_t* h, int sweeps);
+
 /* C <- G C for a one- or two-qudit Clifford G (Sec. 3, top loop of Fig. 3): the tableau rows
  * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every
  * circuit of the handle. */
@@ -360,6 +366,13 @@ int gcamps_estimate_theta(gcamps_t* h, int chi_l, int chi_r, const double* theta
 #define GCAMPS_NOALLOC_MAX_SIDE 81
 int gcamps_score_theta_noalloc(int d, int chi_l, int chi_r, const double* theta_dev, double* s2_dev,
                                double* vn_dev, int32_t* choice_dev, double tie_tol, void* cuda_stream);
+
+/* Measured arithmetic peaks of the current GPU, the denominators of the engine's roofline (no counterpart in
+ * the paper): tflops[0] FP64 fused multiply-add, tflops[1] FP32 fused multiply-add, tflops[2] FP64
+ * tensor-core MMA (m8n8k4), in TFLOP/s counting 2 flops per multiply-add, from CUDA-event timings of grids
+ * of independent chains (under about a second each; one small allocation).  count: entries of tflops
+ * (>= 3).  Synchronising. */
+int gcamps_measure_peaks(double* tflops, int count);
 
 /* Wait for all enqueued work; returns the sticky device status of circuit 0..batch-1 folded.  No
  * counterpart in the paper. */

@@ -179,6 +179,10 @@ class Simulator:
     def set_cluster_size(self, cluster_size: int):
         self._c(self._lib.gcamps_set_cluster_size(self._h, cluster_size))
 
+    def set_jacobi_cap(self, sweeps: int):
+        """Most sweeps of one Jacobi SVD before the engine reports GCAMPS_ENOCONV (default 60)."""
+        self._c(self._lib.gcamps_set_jacobi_cap(self._h, sweeps))
+
     # -- lifetime
     def close(self):
         if getattr(self, "_h", None):

@@ -47,12 +47,13 @@ EXPORTS = [
     "gcamps_create",
     "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_batch_create",
     "gcamps_batch_expect_weyl", "gcamps_batch_amplitude", "gcamps_batch_get_tableau", "gcamps_batch_get_bond_dims", "gcamps_destroy", "gcamps_num_qudits",
-    "gcamps_set_cluster_size", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
+    "gcamps_set_cluster_size", "gcamps_set_jacobi_cap", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
     "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
     "gcamps_get_stats", "gcamps_get_profile",
     "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_estimate_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
+    "gcamps_measure_peaks",
 ]
 
 _lib = None
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
         "gcamps_destroy": (None, [vp]),
         "gcamps_num_qudits": (C.c_int, [vp, C.c_int]),
         "gcamps_set_cluster_size": (C.c_int, [vp, C.c_int]),
+        "gcamps_set_jacobi_cap": (C.c_int, [vp, C.c_int]),
         "gcamps_apply_clifford": (C.c_int, [vp, C.c_int, C.c_int, i32p]),
         "gcamps_apply_nonclifford": (C.c_int, [vp, C.c_int, dp]),
         "gcamps_disentangle": (C.c_int, [vp, C.POINTER(Stats)]),
@@ -110,6 +112,7 @@ def load(path: str = LIB_PATH):
         "gcamps_get_last_scores": (C.c_int, [vp, C.c_int, dp, dp, u8p]),
         "gcamps_get_last_theta": (C.c_int, [vp, C.c_int, dp, i32p]),
         "gcamps_sync": (C.c_int, [vp]),
+        "gcamps_measure_peaks": (C.c_int, [dp, C.c_int]),
         "gcamps_reset": (C.c_int, [vp]),
         "gcamps_last_error": (C.c_char_p, [vp]),
     }

@@ -132,7 +132,11 @@ struct Smem {
   float wtri32[kWarps][64];   // the same in FP32
   double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
   float btri32[2 * kBTri];
+  float2 hv[kBTri], hw[kBTri];  // FP32 Householder reduction: reflector v and w = p - K v of the current column
   int bcast;
+  int jmode, jm, jn;          // cluster split of a bond visit: 0 none, 2 cluster Jacobi; its matrix shape (leader)
+  int jflag[2];               // cluster Jacobi: a rotation happened in the sweep of this parity (leader)
+  double jfro;                // cluster Jacobi: |B|_F^2 (leader)
   double red[kWarps * 4];
   double2 coef[4];            // MPO term coefficients c_m tau^{...}
   double2 tau[6];             // tau^k, k < 2d
@@ -532,6 +536,83 @@ __device__ int jacobi_orthogonalize(Smem& s, double2* B, int m, int n, double2* 
   return -1;
 }
 
+__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+
+// jacobi_orthogonalize on the whole cluster of the circuit: the same rotations, pair order and stopping
+// rule, with the column pairs of each round spread over the warps of every CTA and a cluster barrier between
+// rounds (its release / acquire orders the global writes of one round before the reads of the next; B and W
+// are read through L2).  On entry (after a cluster barrier) the leader has set W = I, lead->jfro = |B|_F^2 and
+// lead->jflag[0] = lead->jflag[1] = 0.  Every CTA returns the number of sweeps, or -1 if max_sweeps were not
+// enough.
+__device__ int jacobi_cluster(Smem* lead, const Ctx& C, double2* B, int m, int n, double2* W, int max_sweeps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (n <= 1) return 0;
+  const double zero_col = 1e-30 * lead->jfro;
+  const long long zc_bits = __double_as_longlong(zero_col);
+  const int N = n + (n & 1);
+  const int npairs = N / 2;
+  const double tol2 = 1e-28;
+  const int gw = C.rank * kWarps + warp, nw = C.csize * kWarps;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    bool any = false;
+    for (int round = 0; round < N - 1; ++round) {
+      for (int p = gw; p < npairs; p += nw) {
+        const int pa = (p == 0) ? 0 : 1 + ((p - 1 + round) % (N - 1));
+        const int qa = 1 + ((N - 2 - p + round) % (N - 1));
+        const int i = pa < qa ? pa : qa, j = pa < qa ? qa : pa;
+        if (j >= n) continue;
+        double2* bi = B + (long long)i * m;
+        double2* bj = B + (long long)j * m;
+        double al = 0, be = 0, gr = 0, gi = 0;
+        for (int r = lane; r < m; r += 32) {
+          const double2 x = __ldcg(bi + r), y = __ldcg(bj + r);
+          al = fma(x.x, x.x, fma(x.y, x.y, al));
+          be = fma(y.x, y.x, fma(y.y, y.y, be));
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        if (__double_as_longlong(al) <= zc_bits || __double_as_longlong(be) <= zc_bits) continue;
+        const double g2 = fma(gr, gr, gi * gi);
+        if (!(g2 > tol2 * al * be) || g2 < 1e-290) continue;
+        const double ig = rsqrt(g2);
+        const double zeta = (be - al) * 0.5 * ig;
+        const double t = fabs(zeta) < 1e150 ? copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)))
+                                            : 0.5 / zeta;
+        const double cs = rsqrt(fma(t, t, 1.0));
+        const double sn = cs * t;
+        const double2 e = make_double2(gr * ig, gi * ig);
+        const double2 se = cscale(e, sn), sec = cscale(cconj(e), sn);
+        for (int r = lane; r < m; r += 32) {
+          const double2 x = __ldcg(bi + r), y = __ldcg(bj + r);
+          __stcg(bi + r, csub(cscale(x, cs), cmul(sec, y)));
+          __stcg(bj + r, cadd(cmul(se, x), cscale(y, cs)));
+        }
+        double2* wi = W + (long long)i * n;
+        double2* wj = W + (long long)j * n;
+        for (int r = lane; r < n; r += 32) {
+          const double2 x = __ldcg(wi + r), y = __ldcg(wj + r);
+          __stcg(wi + r, csub(cscale(x, cs), cmul(sec, y)));
+          __stcg(wj + r, cadd(cmul(se, x), cscale(y, cs)));
+        }
+        any = true;
+      }
+      cluster_sync();
+    }
+    // a rotation anywhere in the cluster: OR into the leader's flag of this sweep's parity
+    if (lane == 0 && any) atomicOr(&lead->jflag[sweep & 1], 1);
+    cluster_sync();
+    const int rotated = lead->jflag[sweep & 1];
+    // the other parity is set only after the next sweep's rounds (cluster barriers the leader passes too)
+    if (C.rank == 0 && threadIdx.x == 0) lead->jflag[(sweep + 1) & 1] = 0;
+    if (!rotated) return sweep + 1;
+  }
+  return -1;
+}
+
 // Singular values of the orthogonalised columns, sorted descending: sing[i] = |b_perm[i]|.
 __device__ void sorted_column_norms(const double2* B, int m, int n, double* sv_tmp, double* sing, int* perm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -571,9 +652,46 @@ __device__ __noinline__ int block_qr(Smem& s, double2* B, int m, int n, double2*
 
 // When the long side is at least twice the short one, the long side is first reduced by a QR
 // (B = Q R) and the Jacobi rotations act on the n x n factor R; the long factor is then Q times
-// the orthogonalised columns of R.
-__device__ __noinline__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, int cols, int cap,
-                             bool renorm) {
+// the orthogonalised columns of R.  The steps are svd_prepare (B and the QR), the Jacobi rotations
+// (jacobi_orthogonalize on this CTA, or jacobi_cluster on the circuit's cluster) and svd_finish.
+struct SvdPrep {
+  bool tall, precond;
+  int m, n, mm;   // B is m x n (column-major); the rotations act on its first mm rows (mm = n after the QR)
+};
+
+__device__ __noinline__ SvdPrep svd_prepare(Smem& s, const Ctx& C, const double2* M, int rows, int cols) {
+  const Engine& e = *C.e;
+  double2* B = C.scr + e.sl.b;
+  double2* Vh = C.scr + e.sl.vh;
+  double2* Qb = C.scr + e.sl.tmp;
+  SvdPrep p;
+  p.tall = rows >= cols;
+  p.m = p.tall ? rows : cols;
+  p.n = p.tall ? cols : rows;
+  // B = M (tall) or M^H (wide), column-major m x n
+  for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx % cols);
+    if (p.tall) B[(long long)c * p.m + r] = M[idx];
+    else B[(long long)r * p.m + c] = cconj(M[idx]);
+  }
+  __syncthreads();
+  p.precond = p.n > 1 && p.m >= 2 * p.n;
+  p.mm = p.m;
+  if (p.precond) {
+    block_qr(s, B, p.m, p.n, Qb, Vh, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
+    __syncthreads();
+    for (long long idx = threadIdx.x; idx < (long long)p.n * p.n; idx += blockDim.x) {
+      const int i = (int)(idx / p.n), c = (int)(idx % p.n);
+      B[(long long)c * p.n + i] = Vh[idx];
+    }
+    __syncthreads();
+    p.mm = p.n;
+  }
+  return p;
+}
+
+__device__ __noinline__ Factor svd_finish(Smem& s, const Ctx& C, const SvdPrep& p, int sweeps, int rows, int cols,
+                                          int cap, bool renorm) {
   const Engine& e = *C.e;
   double2* B = C.scr + e.sl.b;
   double2* W = C.scr + e.sl.w;
@@ -583,37 +701,16 @@ __device__ __noinline__ Factor svd_factor(Smem& s, const Ctx& C, const double2* 
   double* sing = C.sing;
   double* svt = C.sing + e.sing_stride / 2;
   int* perm = C.perm;
-  const bool tall = rows >= cols;
-  const int m = tall ? rows : cols;
-  const int n = tall ? cols : rows;
-  // B = M (tall) or M^H (wide), column-major m x n
-  for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
-    const int r = (int)(idx / cols), c = (int)(idx % cols);
-    if (tall) B[(long long)c * m + r] = M[idx];
-    else B[(long long)r * m + c] = cconj(M[idx]);
-  }
-  __syncthreads();
-  const bool precond = n > 1 && m >= 2 * n;
-  int mm = m;
-  if (precond) {
-    block_qr(s, B, m, n, Qb, Vh, C.sing, reinterpret_cast<double2*>(C.sing + e.sing_stride / 2));
-    __syncthreads();
-    for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
-      const int i = (int)(idx / n), c = (int)(idx % n);
-      B[(long long)c * n + i] = Vh[idx];
-    }
-    __syncthreads();
-    mm = n;
-  }
-  const int sweeps = jacobi_orthogonalize(s, B, mm, n, W, 60);
+  const bool tall = p.tall, precond = p.precond;
+  const int m = p.m, n = p.n;
   if (threadIdx.x == 0) {
     if (sweeps < 0) set_failure(C, GCAMPS_ENOCONV, 1, rows, cols);
-    const int sw = sweeps < 0 ? 60 : sweeps;
+    const int sw = sweeps < 0 ? e.jacobi_cap : sweeps;
     C.stats[S_SVD] += 1;
     C.stats[S_JSWEEPS] += sw;
     if (sw > C.stats[S_JMAX]) C.stats[S_JMAX] = sw;
   }
-  sorted_column_norms(B, mm, n, svt, sing, perm);
+  sorted_column_norms(B, p.mm, n, svt, sing, perm);
   // rank rule
   if (threadIdx.x == 0) {
     int k = 0;
@@ -670,6 +767,16 @@ __device__ __noinline__ Factor svd_factor(Smem& s, const Ctx& C, const double2* 
   for (int i = threadIdx.x; i < k; i += blockDim.x) sing[i] *= scale;
   __syncthreads();
   return F;
+}
+
+// Factor M (rows x cols, row-major) = U S Vh keeping the k largest singular values with
+// s_i > cutoff * s_0 (at most cap, at least one), on this CTA alone.
+__device__ __noinline__ Factor svd_factor(Smem& s, const Ctx& C, const double2* M, int rows, int cols, int cap,
+                                          bool renorm) {
+  const Engine& e = *C.e;
+  const SvdPrep p = svd_prepare(s, C, M, rows, cols);
+  const int sweeps = jacobi_orthogonalize(s, C.scr + e.sl.b, p.mm, p.n, C.scr + e.sl.w, e.jacobi_cap);
+  return svd_finish(s, C, p, sweeps, rows, cols, cap, renorm);
 }
 
 // ------------------------------------------------------------ Householder QR (block level)
@@ -1533,19 +1640,26 @@ __device__ double vn_est_bound(int d, int m, int M) {
 __device__ __forceinline__ float fabs2f(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
 // Householder reduction of a Hermitian m x m matrix (FP32, row-major, full storage, overwritten) to a real
-// symmetric tridiagonal (diag dg, off-diagonal magnitudes od), CTA-level; the steps of group_tridiag.  A column
+// symmetric tridiagonal (diag dg, off-diagonal magnitudes od), CTA-level; the reflections of group_tridiag,
+// arranged for latency: the reflector v and w = p - K v live in shared memory (m <= kBTri + 1), the
+// product p = A v is taken as p_i = sum_j conj(A_ji) v_j (consecutive rows, coalesced) with four
+// independent accumulators, and the rank-2 update covers the whole trailing block, a warp per row.  A column
 // whose part below the subdiagonal has norm below 1e-10 |A|_F is taken as reduced (far below FP32 rounding).
 __device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   float fro2 = 0.f;
   for (int idx = tid; idx < m * m; idx += nt) fro2 += fabs2f(A[idx]);
   fro2 = block_sum_f(fro2, s);
   for (int k = 0; k + 2 < m; ++k) {
     const int r = m - k - 1;
     float tail2 = 0.f;
-    for (int i = 1 + tid; i < r; i += nt) tail2 += fabs2f(A[(long long)(k + 1 + i) * m + k]);
-    tail2 = block_sum_f(tail2, s);
-    const float2 x0 = A[(long long)(k + 1) * m + k];
+    for (int i = tid; i < r; i += nt) {
+      const float2 x = A[(long long)(k + 1 + i) * m + k];
+      s.hv[i] = x;
+      if (i > 0) tail2 += fabs2f(x);
+    }
+    tail2 = block_sum_f(tail2, s);   // its barriers also publish hv
+    const float2 x0 = s.hv[0];
     const float ax0 = hypotf(x0.x, x0.y);
     if (tid == 0) dg[k] = A[(long long)k * m + k].x;
     if (tail2 <= 1e-20f * fro2) {
@@ -1557,39 +1671,51 @@ __device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
     const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
     const float hinv = 1.f / (alpha * (alpha + ax0));   // 2 / v^H v
     __syncthreads();
-    if (tid == 0) A[(long long)(k + 1) * m + k] = make_float2(fmaf(ph.x, alpha, x0.x), fmaf(ph.y, alpha, x0.y));
+    if (tid == 0) s.hv[0] = make_float2(fmaf(ph.x, alpha, x0.x), fmaf(ph.y, alpha, x0.y));
     __syncthreads();
-    // p = A22 v / h (row i of the trailing block times the reflector in column k)
+    // p_i = hinv sum_j conj(A_(k+1+j),(k+1+i)) v_j: thread i walks down column k+1+i
     for (int i = tid; i < r; i += nt) {
-      float2 acc = make_float2(0.f, 0.f);
-      const float2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
-      for (int j = 0; j < r; ++j) acc = ffma2(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
-      A[(long long)k * m + k + 1 + i] = make_float2(acc.x * hinv, acc.y * hinv);
+      const float2* col = A + (long long)(k + 1) * m + (k + 1 + i);
+      float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
+      int j = 0;
+      for (; j + 4 <= r; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 a = col[(long long)(j + u) * m], v = s.hv[j + u];
+          ax[u] = fmaf(a.x, v.x, fmaf(a.y, v.y, ax[u]));    // Re conj(a) v
+          ay[u] = fmaf(a.x, v.y, fmaf(-a.y, v.x, ay[u]));   // Im conj(a) v
+        }
+      }
+      for (; j < r; ++j) {
+        const float2 a = col[(long long)j * m], v = s.hv[j];
+        ax[0] = fmaf(a.x, v.x, fmaf(a.y, v.y, ax[0]));
+        ay[0] = fmaf(a.x, v.y, fmaf(-a.y, v.x, ay[0]));
+      }
+      s.hw[i] = make_float2(((ax[0] + ax[1]) + (ax[2] + ax[3])) * hinv, ((ay[0] + ay[1]) + (ay[2] + ay[3])) * hinv);
     }
     __syncthreads();
     float kr = 0.f;
     for (int i = tid; i < r; i += nt) {
-      const float2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
+      const float2 v = s.hv[i], p = s.hw[i];
       kr = fmaf(v.x, p.x, fmaf(v.y, p.y, kr));
     }
     const float krf = block_sum_f(kr, s) * 0.5f * hinv;
     for (int i = tid; i < r; i += nt) {
-      const float2 v = A[(long long)(k + 1 + i) * m + k], p = A[(long long)k * m + k + 1 + i];
-      A[(long long)k * m + k + 1 + i] = make_float2(fmaf(-krf, v.x, p.x), fmaf(-krf, v.y, p.y));
+      const float2 v = s.hv[i], p = s.hw[i];
+      s.hw[i] = make_float2(fmaf(-krf, v.x, p.x), fmaf(-krf, v.y, p.y));
     }
     __syncthreads();
-    // A22 <- A22 - v w^H - w v^H on the packed lower triangle, mirrored
-    for (int idx = tid; idx < r * (r + 1) / 2; idx += nt) {
-      int i, j;
-      tri_index(idx, i, j);
-      const float2 vi = A[(long long)(k + 1 + i) * m + k], vj = A[(long long)(k + 1 + j) * m + k];
-      const float2 wi = A[(long long)k * m + k + 1 + i], wj = A[(long long)k * m + k + 1 + j];
-      float2* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
-      float2 nv = *a;
-      nv.x = fmaf(-vi.x, wj.x, fmaf(-vi.y, wj.y, fmaf(-wi.x, vj.x, fmaf(-wi.y, vj.y, nv.x))));
-      nv.y = fmaf(-vi.y, wj.x, fmaf(vi.x, wj.y, fmaf(-wi.y, vj.x, fmaf(wi.x, vj.y, nv.y))));
-      *a = nv;
-      if (j != i) A[(long long)(k + 1 + j) * m + (k + 1 + i)] = make_float2(nv.x, -nv.y);
+    // A22 <- A22 - v w^H - w v^H, a warp per row, lanes along the row
+    for (int i = warp; i < r; i += kWarps) {
+      const float2 vi = s.hv[i], wi = s.hw[i];
+      float2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
+      for (int j = lane; j < r; j += 32) {
+        const float2 vj = s.hv[j], wj = s.hw[j];
+        float2 nv = arow[j];
+        nv.x = fmaf(-vi.x, wj.x, fmaf(-vi.y, wj.y, fmaf(-wi.x, vj.x, fmaf(-wi.y, vj.y, nv.x))));
+        nv.y = fmaf(-vi.y, wj.x, fmaf(vi.x, wj.y, fmaf(-wi.y, vj.x, fmaf(wi.x, vj.y, nv.y))));
+        arow[j] = nv;
+      }
     }
     if (tid == 0) od[k] = alpha;
     __syncthreads();
@@ -1684,6 +1810,7 @@ __device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, i
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (m > kBTri) return false;   // the reflector buffers of tridiag32 hold kBTri entries
   float2* X = ws;
   float2* G = ws + (long long)rows * cols;
   float* dg = reinterpret_cast<float*>(G + (long long)m * m);
@@ -1825,7 +1952,6 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
   }
 }
 
-__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 
 // ---------------------------------------------------------------- disentangling sweeps (Sec. 3)
 // One bond.  The leader CTA forms theta = A_i A_{i+1}; the cluster scores the classes; the leader
@@ -2083,7 +2209,15 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   const int m = rows < cols ? rows : cols;
   int nev = 0;
   const int kbsel = select_class(s, lead, C, theta, cl, cr, &nev);
-  if (!leader) return;
+  // Splits with many Jacobi columns run their rotations on the whole cluster: the other CTAs wait for the
+  // leader's choice (a QR move or such a split) at one more cluster barrier.
+  const bool big = C.csize > 1 && m >= kClusterJacobiMin;
+  if (!leader) {
+    if (!big) return;
+    cluster_sync();
+    if (lead->jmode == 2) jacobi_cluster(lead, C, C.scr + e.sl.b, lead->jm, lead->jn, C.scr + e.sl.w, e.jacobi_cap);
+    return;
+  }
   tp = prof_start(C);
   // visit counters of the size bucket; the visit's cycles are added when it ends
   if (prof_thread(C)) {
@@ -2140,6 +2274,11 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   // as it is.  A QR move of the centre gives the same state and bond dimension without it.
   const int chim = C.dims[i + 1];
   if (kb == 0 && s.rank0 == chim && chim <= cap) {
+    if (big) {   // release the other CTAs
+      if (threadIdx.x == 0) s.jmode = 0;
+      __syncthreads();
+      cluster_sync();
+    }
     if (ltr) move_right(s, C, i);
     else move_left_qr(s, C, i + 1);
     note_chi(C, chim);
@@ -2148,7 +2287,30 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     if (prof_thread(C)) C.prof[P_VCYC + prof_bucket(m)] += clock64() - tv;
     return;
   }
-  Factor F = svd_factor(s, C, theta, rows, cols, cap, true);
+  Factor F;
+  if (big) {
+    const SvdPrep p = svd_prepare(s, C, theta, rows, cols);
+    double2* B = C.scr + e.sl.b;
+    double2* W = C.scr + e.sl.w;
+    for (long long idx = threadIdx.x; idx < (long long)p.n * p.n; idx += blockDim.x)
+      W[idx] = ((idx % p.n) == (idx / p.n)) ? make_double2(1.0, 0.0) : cz();
+    double fro = 0;
+    for (long long idx = threadIdx.x; idx < (long long)p.mm * p.n; idx += blockDim.x) fro += cabs2(B[idx]);
+    fro = block_sum(fro, s);
+    if (threadIdx.x == 0) {
+      s.jfro = fro;
+      s.jflag[0] = s.jflag[1] = 0;
+      s.jm = p.mm;
+      s.jn = p.n;
+      s.jmode = 2;
+    }
+    __syncthreads();
+    cluster_sync();
+    const int sweeps = jacobi_cluster(lead, C, B, p.mm, p.n, W, e.jacobi_cap);
+    F = svd_finish(s, C, p, sweeps, rows, cols, cap, true);
+  } else {
+    F = svd_factor(s, C, theta, rows, cols, cap, true);
+  }
   const int k = F.k;
   if (ltr) {
     for (long long idx = threadIdx.x; idx < (long long)k * d * cr; idx += blockDim.x)

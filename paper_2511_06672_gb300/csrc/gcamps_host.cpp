@@ -546,6 +546,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.batch = batch;
   e.max_sweeps = opts.max_sweeps;
   e.score_kind = opts.score_kind;
+  e.jacobi_cap = 60;
   e.cutoff = opts.cutoff;
   e.tie_tol = opts.tie_tol;
   e.strict_weight = opts.strict_weight;
@@ -894,6 +895,14 @@ int gcamps_run_device(gcamps_t* h, const gcamps_op* ops_dev, const int32_t* begi
 int gcamps_num_qudits(gcamps_t* h, int circuit) {
   if (!h || circuit < 0 || circuit >= h->e.batch) return -1;
   return h->nq[circuit];
+}
+
+int gcamps_set_jacobi_cap(gcamps_t* h, int sweeps) {
+  if (!h) return GCAMPS_EINVAL;
+  if (sweeps < 1 || sweeps > 1000) return fail(h, GCAMPS_EINVAL, "Jacobi sweep cap outside 1..1000");
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->e.jacobi_cap = sweeps;
+  return GCAMPS_OK;
 }
 
 int gcamps_set_cluster_size(gcamps_t* h, int cluster_size) {

@@ -10,6 +10,7 @@
 namespace gcx {
 
 constexpr int kThreads = 256;             // threads per CTA; a cluster of CTAs runs one circuit
+constexpr int kClusterJacobiMin = 24;     // SVD splits of bond visits with at least this many Jacobi columns use the cluster
 constexpr int kMinCtas = 2;               // resident CTAs per SM the engine kernels are compiled for (128 registers)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCluster = 16;           // CTAs per circuit (thread-block cluster)
@@ -64,6 +65,7 @@ struct CtaLayout {
 struct Engine {
   int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;   // n: largest qudit count of the batch
   int score_kind;                 // 0 von Neumann, 1 Renyi-2, 2 weight rank then von Neumann
+  int jacobi_cap;                 // most sweeps of one Jacobi SVD before GCAMPS_ENOCONV (60)
   double cutoff, tie_tol, strict_weight;
   long long tcap;                 // elements of the largest two-site matrix
   long long wcap;                 // elements of the largest Jacobi rotation matrix
