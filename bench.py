@@ -661,6 +661,156 @@ def run_case(args):
     return 0
 
 
+PREC_N, PREC_LAYERS, PREC_T, PREC_CHI = 64, 40, 64, 1024
+PREC_WORKLOAD = "gcamps-brickwork-n64-L40-T64-chi1024-d3"
+
+
+def weyl_probes(n: int):
+    """Weyl strings whose expectation both forms report: Z_j (every 4th qudit), Z_0 Z_{n/5}, X_j Z_{j+1}."""
+    probes = []
+    for j in range(0, n, 4):
+        x, z = [0] * n, [0] * n
+        z[j] = 1
+        probes.append((x, z))
+    x, z = [0] * n, [0] * n
+    z[0], z[n // 5] = 1, 1
+    probes.append((x, z))
+    for j in range(0, n - 1, 8):
+        x, z = [0] * n, [0] * n
+        x[j], z[j + 1] = 1, 1
+        probes.append((x, z))
+    return probes
+
+
+def run_precision(args):
+    """The precision form against the FP64 form on the precision configuration: qutrits, n = 64, 40 brickwork
+    layers, 64 T gates, chi_max = 1024, cutoff 1e-12, seeds 1..S in one batch (one engine launch per step and
+    form).  value = T-gates/s of the precision form (device time, L2 flushed before every step); fp64 = the
+    same for the FP64 form.  Errors of the precision run against the FP64 run: |<W>| differences for the
+    probe strings (each form in its own Clifford frame), and, replaying the FP64 decisions, the fidelity
+    |<M|M'>|^2 (equal tableaux checked bit for bit)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2511_06672_gb300.build import build_library
+    build_library()
+    import paper_2511_06672_gb300 as G
+    from synth import brickwork_circuit
+    seeds = [1 + s + rank * args.prec_seeds for s in range(args.prec_seeds)]
+    ops, begin = [], [0]
+    for sd in seeds:
+        o = G.ops_from_gates(brickwork_circuit(PREC_N, 3, PREC_LAYERS, PREC_T, sd), 3)
+        ops.append(o)
+        begin.append(begin[-1] + len(o))
+    ops = np.concatenate(ops)
+    begin = np.array(begin, dtype=np.int32)
+    dev = f"cuda:{local}"
+    ops_dev = torch.from_numpy(ops.view(np.uint8)).to(dev)
+    begin_dev = torch.from_numpy(begin).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    S = len(seeds)
+    lines = {}
+    sims = {}
+    for prec in (0, 1):
+        stream = torch.cuda.Stream()
+        sim = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, batch=S, stream=stream, cluster_size=16,
+                          precision=prec)
+        sims[prec] = sim
+        for _ in range(args.warmup):
+            sim.reset()
+            sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
+        sim.sync()
+        times = []
+        clocks = ClockSampler(local)
+        clocks.start()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.reset()
+            sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        clk = clocks.stop()
+        st = [sim.stats(c) for c in range(S)]
+        if any(x["status"] for x in st):
+            raise RuntimeError(f"device status {[x['status'] for x in st]}")
+        tg = sum(x["t_gates"] for x in st)
+        lines[prec] = {"value": tg * args.steps / sum(times), "ms_per_step": 1e3 * sum(times) / args.steps,
+                       "max_chi": max(x["max_chi"] for x in st), "bond_visits": sum(x["bonds_visited"] for x in st),
+                       "exact_evaluations": sum(x["vn_evaluations"] for x in st),
+                       "tensor_flops_per_step": sum(x["tensor_flops"] for x in st), "clocks": clk,
+                       "launch_s": sum(times) / args.steps}
+    # errors of the precision run against the FP64 run
+    probes = weyl_probes(PREC_N)
+    werr = 0.0
+    same_dec = 0
+    for c in range(S):
+        for x, z in probes:
+            werr = max(werr, abs(sims[1].expect_weyl(x, z, c) - sims[0].expect_weyl(x, z, c)))
+        same_dec += sims[1].decisions(c) == sims[0].decisions(c)
+    rep = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, batch=S, cluster_size=16, precision=1)
+    for c in range(S):
+        rep.set_replay(sims[0].decisions(c), c)
+    rep.run(ops, begin)
+    rep.sync()
+    fid_err = 0.0
+    for c in range(S):
+        ea, pa = sims[0].tableau(c)
+        eb, pb = rep.tableau(c)
+        if not (np.array_equal(ea, eb) and np.array_equal(pa, pb)):
+            raise RuntimeError("replayed tableau differs")
+        fid_err = max(fid_err, 1.0 - abs(sims[0].overlap(rep, c, c)) ** 2)
+    rep.close()
+    # e2e of the precision form through the C ABI: host gate list copied in, bond dimensions read back
+    e2e_t = []
+    for _ in range(max(2, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sims[1].reset()
+        sims[1].run(ops, begin)
+        dims = [sims[1].bond_dims(c) for c in range(S)]
+        e2e_t.append(time.perf_counter() - t0)
+    tg = PREC_T * S
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        tf32_peak, tf32_src = bf16 * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16 ratio (1.1/2.25)"
+    except (OSError, ValueError, KeyError):
+        tf32_peak, tf32_src = 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16 ratio"
+    tc_ach = lines[1]["tensor_flops_per_step"] / lines[1]["launch_s"] / 1e12
+    line = {
+        "metric": "T-gates/s (precision form)", "value": lines[1]["value"], "unit": "T-gates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": lines[1]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 contractions (tf32x3 tensor cores), f64 eigen/SVD/score",
+        "data": "synthetic",
+        "config": {"workload": PREC_WORKLOAD, "n": PREC_N, "layers": PREC_LAYERS, "t_gates": PREC_T,
+                   "chi_max": PREC_CHI, "cutoff": CUTOFF, "d": 3, "seeds": seeds,
+                   "l2": "512 MiB flush before every timed step"},
+        "fp64": {k: v for k, v in lines[0].items() if k != "launch_s"},
+        "precision": {k: v for k, v in lines[1].items() if k != "launch_s"},
+        "speedup_vs_fp64": lines[1]["value"] / lines[0]["value"],
+        "errors_vs_fp64": {"max_abs_weyl_expectation": werr, "probes_per_circuit": len(probes),
+                           "replay_fidelity_error": fid_err, "circuits_with_identical_decisions": same_dec},
+        "roofline": {"bound": "tensor", "achieved": tc_ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": tc_ach / tf32_peak, "traffic": None, "peak_source": tf32_src,
+                     "kernel": "k_run_tc (tensor-core Grams of CTA-level class evaluations)"},
+        "e2e": {"value": tg * len(e2e_t) / sum(e2e_t), "unit": "T-gates/s", "h2d_bytes_per_step": ops.nbytes + begin.nbytes,
+                "d2h_bytes_per_step": sum(len(x) * 4 for x in dims)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": lines[1]["clocks"],
+    }
+    for sim in sims.values():
+        sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle (as it stands, one thread) on the GPU arm's own 16 circuits, one
     whole pass of them in the timed region, split over the --steps steps in bench_circuits order (with
@@ -702,7 +852,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
-    ap.add_argument("--workload", default="bench", choices=["bench", "batched", "gradient", "chi-layers", "case"],
+    ap.add_argument("--prec-seeds", type=int, default=4, help="precision workload: circuits per rank")
+    ap.add_argument("--workload", default="bench",
+                    choices=["bench", "batched", "gradient", "chi-layers", "case", "precision"],
                     help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch; "
                          "gradient: forward + adjoint; chi-layers: bond dimension after every layer (Fig. 5a); "
                          "case: one seeded circuit per launch with its engine profile (for ncu)")
@@ -746,6 +898,8 @@ def main():
         return run_reference(args)
     if args.workload == "case":
         return run_case(args)
+    if args.workload == "precision":
+        return run_precision(args)
     if args.workload == "chi-layers":
         return run_chi_layers(args)
     if args.workload == "batched":

@@ -58,7 +58,11 @@ typedef struct {
                        /* 1 = Renyi-2 entropy -ln sum p^2;                                     */
                        /* 2 = number of Schmidt weights p > max(1e-12, 4 cutoff^2), ties       */
                        /*     broken by the von Neumann entropy                               */
-  int precision;       /* 0 = FP64 everywhere (only mode now)                                  */
+  int precision;       /* 0 = FP64 contractions and scores; 1 = precision form: the class scores'  */
+                       /* contractions (Q theta and its Gram) in FP32, tensor cores (tcgen05 TF32, */
+                       /* three-term split) at CTA-level sizes, the Gram promoted to FP64 for the  */
+                       /* FP64 reduction, eigenvalues and score; SVD splits FP64; tie_tol at least */
+                       /* 1e-5 (the scores' FP32 resolution)                                      */
   double tie_tol;      /* accept Q only if S(Q) < S(I) - tie_tol; ties -> lowest index (1e-10) */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
   /* The fields above are the contract's options, in its order; the ones below extend it.           */
@@ -89,6 +93,8 @@ typedef struct {
   double discarded_weight;    /* sum of discarded s_i^2 over all truncations                */
   double scoring_flops;       /* algorithmic FP64 flops of exact class scoring (see below)  */
   double screen_flops;        /* algorithmic FP32 flops of the Renyi-2 screen (see below)   */
+  double tensor_flops;        /* algorithmic flops of the Grams run on the tensor cores     */
+                              /* (precision form: 8 m^2 K per m x m Gram of K columns)      */
 } gcamps_stats;
 /* Per class at a bond with R = chi_l d rows and C = d chi_r columns (m = min(R, C),
  * M = max(R, C)): scoring_flops adds 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram) +
@@ -281,6 +287,20 @@ int gcamps_get_site(gcamps_t* h, int circuit, int site, double* t, int64_t cap, 
 int gcamps_get_last_weyl(gcamps_t* h, int circuit, int32_t* x, int32_t* z, int32_t* r);
 /* Counters of circuit `circuit` (gcamps_stats; no counterpart in the paper). */
 int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st);
+/* Replay (the oracle's replay of Sec. 3 decisions, for comparing two runs of one circuit): from the next
+ * launch, circuit `circuit` applies pairs[2k], pairs[2k+1] = (bond, class) at its k-th disentangler bond
+ * visit instead of scoring the classes (gcamps_get_decisions gives such a list); each visit splits by SVD.
+ * Visit k at another bond, or more visits than count, set GCAMPS_EINVAL in the circuit's status.  count = 0
+ * turns replay off.  pairs: host memory, copied; bonds 0..n-2, classes 0..K-1 (EINVAL otherwise); count
+ * <= 65536.  Synchronises the handle's stream; the first call allocates the replay buffers (ENOMEM). */
+int gcamps_set_replay(gcamps_t* h, int circuit, const int32_t* pairs, int32_t count);
+
+/* <M1|M2> of the MPS of circuit1 of h1 and circuit2 of h2 (Sec. 2.4; transfer matrices in FP64): with equal
+ * tableaux (bit-exact, e.g. one run replaying the other's decisions) the two states C|M1>, C|M2> have
+ * overlap <M1|M2> and fidelity |<M1|M2>|^2.  The handles need the same n, d and chi_max (EINVAL otherwise);
+ * h2's stream is synchronised, the contraction runs on h1's stream in h1's scratch.  Synchronising. */
+int gcamps_overlap(gcamps_t* h1, int circuit1, gcamps_t* h2, int circuit2, double* re, double* im);
+
 /* Where the engine's time went for circuit `circuit` since creation (or gcamps_reset): no counterpart in
  * the paper, a measurement aid.  out receives min(cap, GCAMPS_PROF_WORDS) int64 words (*count, may be NULL,
  * receives GCAMPS_PROF_WORDS), all SM clock cycles (clock64) of the circuit's leader CTA, whose intervals

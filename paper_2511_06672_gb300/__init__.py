@@ -148,13 +148,14 @@ class Simulator:
     def __init__(self, n, d: int, chi_max: int, cutoff: float = 1e-12, max_sweeps: int = 8,
                  tie_tol: float = 1e-10, batch: int = 1, stream=None, strict_weight: float = 0.0,
                  cluster_size: int = 8, score_kind: int = 0, snapshot_entries: int = 0,
-                 snapshot_max_gates: int = 0):
+                 snapshot_max_gates: int = 0, precision: int = 0):
         self._lib = N.load()
         o = N.Opts()
         self._lib.gcamps_default_opts(C.byref(o))
         o.cutoff, o.max_sweeps, o.tie_tol, o.strict_weight = cutoff, max_sweeps, tie_tol, strict_weight
         o.cluster_size = cluster_size
         o.score_kind = score_kind
+        o.precision = precision
         o.snapshot_entries, o.snapshot_max_gates = snapshot_entries, snapshot_max_gates
         s = _stream_handle(stream)
         o.cuda_stream = C.c_void_p(s) if s else None
@@ -316,6 +317,18 @@ class Simulator:
         st = N.Stats()
         self._c(self._lib.gcamps_get_stats(self._h, circuit, C.byref(st)))
         return st.as_dict()
+
+    def set_replay(self, pairs, circuit: int = 0):
+        """Replay the (bond, class) decisions ``pairs`` (as from decisions()) at this circuit's bond visits from the
+        next launch on; an empty list turns replay off."""
+        a = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+        self._c(self._lib.gcamps_set_replay(self._h, circuit, N.ptr(a, C.c_int32) if a.size else None, a.size // 2))
+
+    def overlap(self, other: "Simulator", circuit: int = 0, other_circuit: int = 0) -> complex:
+        """<M|M'> of this circuit's MPS and another handle's (same n, d, chi_max)."""
+        re, im = C.c_double(), C.c_double()
+        self._c(self._lib.gcamps_overlap(self._h, circuit, other._h, other_circuit, C.byref(re), C.byref(im)))
+        return complex(re.value, im.value)
 
     def profile(self, circuit: int = 0) -> dict:
         """Leader-CTA cycles per engine phase and per bond-visit size bucket since the last reset

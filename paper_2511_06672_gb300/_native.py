@@ -35,7 +35,7 @@ class Stats(C.Structure):
                 ("vn_evaluations", C.c_int64), ("svd_calls", C.c_int64), ("jacobi_sweeps", C.c_int64),
                 ("jacobi_max_sweeps", C.c_int64), ("qr_calls", C.c_int64),
                 ("max_chi", C.c_int32), ("status", C.c_int32), ("discarded_weight", C.c_double),
-                ("scoring_flops", C.c_double), ("screen_flops", C.c_double)]
+                ("scoring_flops", C.c_double), ("screen_flops", C.c_double), ("tensor_flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -51,7 +51,7 @@ EXPORTS = [
     "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
     "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
     "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
-    "gcamps_get_stats", "gcamps_get_profile",
+    "gcamps_get_stats", "gcamps_get_profile", "gcamps_set_replay", "gcamps_overlap",
     "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_estimate_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
     "gcamps_measure_peaks",
 ]
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         "gcamps_get_last_weyl": (C.c_int, [vp, C.c_int, i32p, i32p, i32p]),
         "gcamps_get_stats": (C.c_int, [vp, C.c_int, C.POINTER(Stats)]),
         "gcamps_get_profile": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int64), C.c_int32, i32p]),
+        "gcamps_set_replay": (C.c_int, [vp, C.c_int, i32p, C.c_int32]),
+        "gcamps_overlap": (C.c_int, [vp, C.c_int, vp, C.c_int, dp, dp]),
         "gcamps_get_decisions": (C.c_int, [vp, C.c_int, i32p, C.c_int32, i32p]),
         "gcamps_score_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp, i32p]),
         "gcamps_estimate_theta": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, dp]),

@@ -4,6 +4,12 @@
 // includes it instantiates a few kernels, so the heavy kernels compile in parallel.
 #pragma once
 
+// GCAMPS_TC = 1 in the translation unit of the precision form's kernels: its CTA-level Grams run on the
+// tensor cores (tcgen05, TMEM, dynamic shared memory).  The FP64 kernels are compiled without any of it.
+#ifndef GCAMPS_TC
+#define GCAMPS_TC 0
+#endif
+
 //
 // One CTA runs one circuit.  A launch processes a whole gate list for every circuit of the
 // batch, so the control flow of the method (support span of the commuted Weyl string, bond
@@ -133,6 +139,7 @@ struct Smem {
   double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
   float btri32[2 * kBTri];
   float2 hv[kBTri], hw[kBTri];  // FP32 Householder reduction: reflector v and w = p - K v of the current column
+  float2 whv[kWarps][32], whw[kWarps][32];   // the same per warp (warp-level estimates, m <= 32)
   int bcast;
   int jmode, jm, jn;          // cluster split of a bond visit: 0 none, 2 cluster Jacobi; its matrix shape (leader)
   int jflag[2];               // cluster Jacobi: a rotation happened in the sweep of this parity (leader)
@@ -143,6 +150,9 @@ struct Smem {
   int flag;
   int ival[8];
   double dval[4];
+  uint64_t tc_mbar;           // tensor-core Gram: completion barrier of its MMAs
+  uint32_t tc_tmem;           // its TMEM accumulator (column base)
+  uint32_t tc_commits;        // commits on tc_mbar so far (its phase parity)
 };
 
 struct Ctx {
@@ -544,7 +554,7 @@ __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 // are read through L2).  On entry (after a cluster barrier) the leader has set W = I, lead->jfro = |B|_F^2 and
 // lead->jflag[0] = lead->jflag[1] = 0.  Every CTA returns the number of sweeps, or -1 if max_sweeps were not
 // enough.
-__device__ int jacobi_cluster(Smem* lead, const Ctx& C, double2* B, int m, int n, double2* W, int max_sweeps) {
+__device__ __noinline__ int jacobi_cluster(Smem* lead, const Ctx& C, double2* B, int m, int n, double2* W, int max_sweeps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (n <= 1) return 0;
   const double zero_col = 1e-30 * lead->jfro;
@@ -1479,8 +1489,19 @@ struct Score {
 // triangle computed, mirrored); the Renyi-2 entropy S2 = -ln(|G|_F^2 / tr(G)^2); and, if asked, the
 // von Neumann entropy -sum p ln p from the eigenvalues of G (p = lambda / tr G).  S2 <= S_vN always.
 template <class Grp>
-__device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
-                             double2* ws, long long gram_off, bool want_vn, double* tri, float* tri32, int tricap) {
+__device__ void gram_fp32(const Grp& g, const Ctx& C, const float2* X, int rows, int cols, float2* G);
+template <class Grp>
+__device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, double2* G, int m, double tr, double fro,
+                                                bool want_vn, double* dg, double* od, double* tri, float* tri32,
+                                                int tricap);
+
+// The precision form's class evaluation: theta' = Q theta and its Gram in FP32 (tensor cores at CTA level),
+// promoted to FP64 for the reduction, the eigenvalues and the score.  Kept out of line so that the FP64 path
+// compiles as on its own.
+template <class Grp>
+__device__ __noinline__ Score score_class_fp32(const Grp& g, const Ctx& C, int cl, int cr, const float2* Q32,
+                                               double2* ws, long long gram_off, bool want_vn, double* tri,
+                                               float* tri32, int tricap) {
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
@@ -1488,6 +1509,44 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   double2* G = ws + gram_off;
   double* dg = reinterpret_cast<double*>(G + (long long)m * m);
   double* od = dg + m;
+  float2* X32 = reinterpret_cast<float2*>(tp);
+  float2* G32 = X32 + (long long)rows * cols;
+  for (int idx = g.tid; idx < rows * cols; idx += g.n) {
+    const int rr = idx / cols, col = idx % cols;
+    const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
+    const float2* q = Q32 + (sd * d + t) * dd;
+    const float2* th = C.th32 + (long long)a * dd * cr + b;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int v = 0; v < dd; ++v) acc = ffma2(q[v], th[(long long)v * cr], acc);
+    X32[idx] = acc;
+  }
+  g.sync();
+  gram_fp32(g, C, X32, rows, cols, G32);
+  double tr = 0, fro = 0;
+  for (int idx = g.tid; idx < m * m; idx += g.n) {
+    const double2 v = make_double2((double)G32[idx].x, (double)G32[idx].y);
+    G[idx] = v;
+    if (idx / m == idx % m) tr += v.x;
+    fro += cabs2(v);
+  }
+  tr = g.sum(tr);
+  fro = g.sum(fro);
+  return score_spectrum(g, C, G, m, tr, fro, want_vn, dg, od, tri, tri32, tricap);
+}
+
+template <class Grp>
+__device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, int cl, int cr, const double2* Q,
+                             const float2* Q32, double2* ws, long long gram_off, bool want_vn, double* tri,
+                             float* tri32, int tricap) {
+  const int d = C.d, dd = d * d;
+  const int rows = cl * d, cols = d * cr;
+  const int m = rows < cols ? rows : cols;
+  double2* tp = ws;
+  double2* G = ws + gram_off;
+  double* dg = reinterpret_cast<double*>(G + (long long)m * m);
+  double* od = dg + m;
+  if (C.e->precision && m > kPruneMin && Q != C.e->candU)
+    return score_class_fp32(g, C, cl, cr, Q32, ws, gram_off, want_vn, tri, tri32, tricap);
   for (long long idx = g.tid; idx < (long long)rows * cols; idx += g.n) {
     const int rr = (int)(idx / cols), col = (int)(idx % cols);
     const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
@@ -1522,6 +1581,15 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   }
   tr = g.sum(tr);
   fro = g.sum(fro);
+  return score_spectrum(g, C, G, m, tr, fro, want_vn, dg, od, tri, tri32, tricap);
+}
+
+// S2 from the Gram's trace and squared Frobenius norm, and (want_vn) the von Neumann entropy and weight rank
+// from its eigenvalues (FP64 Householder reduction, multisection).
+template <class Grp>
+__device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, double2* G, int m, double tr, double fro,
+                                                bool want_vn, double* dg, double* od, double* tri, float* tri32,
+                                                int tricap) {
   Score sc;
   sc.ok = true;
   sc.s2 = (tr > 0.0 && fro > 0.0) ? -log(fro / (tr * tr)) : 0.0;
@@ -1640,39 +1708,42 @@ __device__ double vn_est_bound(int d, int m, int M) {
 __device__ __forceinline__ float fabs2f(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
 // Householder reduction of a Hermitian m x m matrix (FP32, row-major, full storage, overwritten) to a real
-// symmetric tridiagonal (diag dg, off-diagonal magnitudes od), CTA-level; the reflections of group_tridiag,
-// arranged for latency: the reflector v and w = p - K v live in shared memory (m <= kBTri + 1), the
-// product p = A v is taken as p_i = sum_j conj(A_ji) v_j (consecutive rows, coalesced) with four
-// independent accumulators, and the rank-2 update covers the whole trailing block, a warp per row.  A column
-// whose part below the subdiagonal has norm below 1e-10 |A|_F is taken as reduced (far below FP32 rounding).
-__device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+// symmetric tridiagonal (diag dg, off-diagonal magnitudes od) on a warp or a CTA; the reflections of
+// group_tridiag, arranged for latency: the reflector v and w = p - K v live in shared memory (hv, hw: at
+// least m - 1 entries), the product p = A v is taken as p_i = sum_j conj(A_ji) v_j (consecutive rows,
+// coalesced) with four independent accumulators, and the rank-2 update covers the whole trailing block, a
+// warp per row.  A column whose part below the subdiagonal has norm below 1e-10 |A|_F is taken as reduced
+// (far below FP32 rounding).
+template <class Grp>
+__device__ void tridiag32(const Grp& g, float2* A, int m, float* dg, float* od, float2* hv, float2* hw) {
+  const int tid = g.tid, nt = g.n, lane = tid & 31, wid = tid >> 5, nwarps = (nt + 31) >> 5;
   float fro2 = 0.f;
   for (int idx = tid; idx < m * m; idx += nt) fro2 += fabs2f(A[idx]);
-  fro2 = block_sum_f(fro2, s);
+  fro2 = g.sumf(fro2);
   for (int k = 0; k + 2 < m; ++k) {
     const int r = m - k - 1;
     float tail2 = 0.f;
     for (int i = tid; i < r; i += nt) {
       const float2 x = A[(long long)(k + 1 + i) * m + k];
-      s.hv[i] = x;
+      hv[i] = x;
       if (i > 0) tail2 += fabs2f(x);
     }
-    tail2 = block_sum_f(tail2, s);   // its barriers also publish hv
-    const float2 x0 = s.hv[0];
+    g.sync();
+    tail2 = g.sumf(tail2);
+    const float2 x0 = hv[0];
     const float ax0 = hypotf(x0.x, x0.y);
     if (tid == 0) dg[k] = A[(long long)k * m + k].x;
     if (tail2 <= 1e-20f * fro2) {
       if (tid == 0) od[k] = ax0;
-      __syncthreads();
+      g.sync();
       continue;
     }
     const float alpha = sqrtf(fmaf(ax0, ax0, tail2));
     const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
     const float hinv = 1.f / (alpha * (alpha + ax0));   // 2 / v^H v
-    __syncthreads();
-    if (tid == 0) s.hv[0] = make_float2(fmaf(ph.x, alpha, x0.x), fmaf(ph.y, alpha, x0.y));
-    __syncthreads();
+    g.sync();
+    if (tid == 0) hv[0] = make_float2(fmaf(ph.x, alpha, x0.x), fmaf(ph.y, alpha, x0.y));
+    g.sync();
     // p_i = hinv sum_j conj(A_(k+1+j),(k+1+i)) v_j: thread i walks down column k+1+i
     for (int i = tid; i < r; i += nt) {
       const float2* col = A + (long long)(k + 1) * m + (k + 1 + i);
@@ -1681,36 +1752,36 @@ __device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
       for (; j + 4 <= r; j += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 a = col[(long long)(j + u) * m], v = s.hv[j + u];
+          const float2 a = col[(long long)(j + u) * m], v = hv[j + u];
           ax[u] = fmaf(a.x, v.x, fmaf(a.y, v.y, ax[u]));    // Re conj(a) v
           ay[u] = fmaf(a.x, v.y, fmaf(-a.y, v.x, ay[u]));   // Im conj(a) v
         }
       }
       for (; j < r; ++j) {
-        const float2 a = col[(long long)j * m], v = s.hv[j];
+        const float2 a = col[(long long)j * m], v = hv[j];
         ax[0] = fmaf(a.x, v.x, fmaf(a.y, v.y, ax[0]));
         ay[0] = fmaf(a.x, v.y, fmaf(-a.y, v.x, ay[0]));
       }
-      s.hw[i] = make_float2(((ax[0] + ax[1]) + (ax[2] + ax[3])) * hinv, ((ay[0] + ay[1]) + (ay[2] + ay[3])) * hinv);
+      hw[i] = make_float2(((ax[0] + ax[1]) + (ax[2] + ax[3])) * hinv, ((ay[0] + ay[1]) + (ay[2] + ay[3])) * hinv);
     }
-    __syncthreads();
+    g.sync();
     float kr = 0.f;
     for (int i = tid; i < r; i += nt) {
-      const float2 v = s.hv[i], p = s.hw[i];
+      const float2 v = hv[i], p = hw[i];
       kr = fmaf(v.x, p.x, fmaf(v.y, p.y, kr));
     }
-    const float krf = block_sum_f(kr, s) * 0.5f * hinv;
+    const float krf = g.sumf(kr) * 0.5f * hinv;
     for (int i = tid; i < r; i += nt) {
-      const float2 v = s.hv[i], p = s.hw[i];
-      s.hw[i] = make_float2(fmaf(-krf, v.x, p.x), fmaf(-krf, v.y, p.y));
+      const float2 v = hv[i], p = hw[i];
+      hw[i] = make_float2(fmaf(-krf, v.x, p.x), fmaf(-krf, v.y, p.y));
     }
-    __syncthreads();
+    g.sync();
     // A22 <- A22 - v w^H - w v^H, a warp per row, lanes along the row
-    for (int i = warp; i < r; i += kWarps) {
-      const float2 vi = s.hv[i], wi = s.hw[i];
+    for (int i = wid; i < r; i += nwarps) {
+      const float2 vi = hv[i], wi = hw[i];
       float2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
       for (int j = lane; j < r; j += 32) {
-        const float2 vj = s.hv[j], wj = s.hw[j];
+        const float2 vj = hv[j], wj = hw[j];
         float2 nv = arow[j];
         nv.x = fmaf(-vi.x, wj.x, fmaf(-vi.y, wj.y, fmaf(-wi.x, vj.x, fmaf(-wi.y, vj.y, nv.x))));
         nv.y = fmaf(-vi.y, wj.x, fmaf(vi.x, wj.y, fmaf(-wi.y, vj.x, fmaf(wi.x, vj.y, nv.y))));
@@ -1718,7 +1789,7 @@ __device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
       }
     }
     if (tid == 0) od[k] = alpha;
-    __syncthreads();
+    g.sync();
   }
   if (tid == 0) {
     if (m >= 2) {
@@ -1728,15 +1799,16 @@ __device__ void tridiag32(Smem& s, float2* A, int m, float* dg, float* od) {
     }
     dg[m - 1] = A[(long long)(m - 1) * m + (m - 1)].x;
   }
-  __syncthreads();
+  g.sync();
 }
 
 // Eigenvalues of a real symmetric tridiagonal (dg, off-diagonal magnitudes od; od is overwritten with its
-// squares) in FP32, CTA-level: multisection on FP32 Sturm counts, P lanes per eigenvalue, over [-R, R]
-// (R >= spectral radius) until the bracket is below R 2^-24; ev receives the m eigenvalues (ascending).
-// sh: 2 cap shared floats used when m <= cap.
-__device__ void tridiag_eig32(Smem& s, const float* dg, float* od, int m, float* ev, float* sh, int cap) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+// squares) in FP32 on a warp or a CTA: multisection on FP32 Sturm counts, P lanes per eigenvalue, over
+// [-R, R] (R >= spectral radius) until the bracket is below R 2^-24; ev receives the m eigenvalues
+// (ascending).  sh: 2 cap shared floats used when m <= cap.
+template <class Grp>
+__device__ void tridiag_eig32(const Grp& g, const float* dg, float* od, int m, float* ev, float* sh, int cap) {
+  const int tid = g.tid, nt = g.n;
   if (m <= 2) {
     if (tid == 0) {
       if (m == 1) {
@@ -1747,13 +1819,13 @@ __device__ void tridiag_eig32(Smem& s, const float* dg, float* od, int m, float*
         ev[1] = mean + r;
       }
     }
-    __syncthreads();
+    g.sync();
     return;
   }
   // [-R, R] with R the Frobenius norm of T (it bounds the spectral radius), widened by 0.1 % for its rounding
   float f2 = 0.f;
   for (int i = tid; i < m; i += nt) f2 = fmaf(dg[i], dg[i], i + 1 < m ? fmaf(2.f * od[i], od[i], f2) : f2);
-  const float R = sqrtf(block_sum_f(f2, s)) * 1.001f + 1e-30f;
+  const float R = sqrtf(g.sumf(f2)) * 1.001f + 1e-30f;
   const float e2min = 1e-20f * R * R;
   const bool fast = m <= cap;
   float* D = fast ? sh : const_cast<float*>(dg);
@@ -1763,7 +1835,7 @@ __device__ void tridiag_eig32(Smem& s, const float* dg, float* od, int m, float*
     if (fast) D[i] = dg[i];
     E[i] = e2;
   }
-  __syncthreads();
+  g.sync();
   const int nw = (nt + 31) / 32;
   int P = 1;
   for (int p = 8; p >= 1; --p)
@@ -1795,22 +1867,25 @@ __device__ void tridiag_eig32(Smem& s, const float* dg, float* od, int m, float*
     }
     if (active && pidx == 0) ev[j] = 0.5f * (lo + hi);
   }
-  __syncthreads();
+  g.sync();
 }
 
-// FP32 estimate of the von Neumann entropy of class Q on theta (CTA-level), whose error vn_est_bound bounds:
-// theta' = Q theta and its Gram on the smaller side in FP32, scaled to unit trace, tridiagonalised and its
-// eigenvalues found in FP32; -sum p ln p of the eigenvalues clipped at 0 and normalised by their sum, in FP32
-// (its rounding, of order m u ln m, is covered by the factor 2 of the bound).  Returns false (no estimate)
-// outside 1e-12 < tr G < 1e12, the FP32 range of the Gram's squares.  The value is valid on thread 0.
-// ws: rows cols + m^2 + 3 m float2 of scratch.
-__device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, int cl, int cr, const float2* Q,
-                                      float2* ws, float* est_out) {
+// FP32 estimate of the von Neumann entropy of class Q on theta (a warp or a CTA), whose error vn_est_bound
+// bounds: theta' = Q theta and its Gram on the smaller side in FP32, scaled to unit trace, tridiagonalised
+// and its eigenvalues found in FP32; -sum p ln p of the eigenvalues clipped at 0 and normalised by their
+// sum, in FP32 (its rounding, of order m u ln m, is covered by the factor 2 of the bound).  From the same
+// Gram, the Renyi-2 entropy and its lower bound as s2_fp32 computes them (s2 may be NULL).  Returns false
+// (no estimate; s2 and its bound still set) outside 1e-12 < tr G < 1e12, the FP32 range of the Gram's
+// squares, or for m above the reflector buffers (hcap).  Values are valid on the group's first thread.
+// ws: rows cols + m^2 + 3 m float2 of scratch; sh: 2 shcap floats of shared memory.
+template <class Grp>
+__device__ __noinline__ bool vn_est32(const Grp& g, const Ctx& C, const float2* th, int cl, int cr, const float2* Q,
+                                      float2* ws, float2* hv, float2* hw, int hcap, float* sh, int shcap,
+                                      float* est_out, float* s2_out, float* s2lo_out) {
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
-  const int m = rows < cols ? rows : cols;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (m > kBTri) return false;   // the reflector buffers of tridiag32 hold kBTri entries
+  const int m = rows < cols ? rows : cols, M = rows < cols ? cols : rows;
+  const int tid = g.tid, nt = g.n;
   float2* X = ws;
   float2* G = ws + (long long)rows * cols;
   float* dg = reinterpret_cast<float*>(G + (long long)m * m);
@@ -1825,8 +1900,8 @@ __device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, i
     for (int v = 0; v < dd; ++v) acc = ffma2(q[v], tp[(long long)v * cr], acc);
     X[idx] = acc;
   }
-  __syncthreads();
-  float tr = 0.f;
+  g.sync();
+  float tr = 0.f, fro = 0.f;
   const int ntri = m * (m + 1) / 2;
   for (int idx = tid; idx < ntri; idx += nt) {
     int i, j;
@@ -1840,19 +1915,41 @@ __device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, i
       for (int r = 0; r < rows; ++r) acc = ffmac2(X[(long long)r * cols + i], X[(long long)r * cols + j], acc);
     }
     G[(long long)i * m + j] = acc;
-    if (i == j) tr += acc.x;
-    else G[(long long)j * m + i] = make_float2(acc.x, -acc.y);
+    if (i == j) {
+      tr += acc.x;
+      fro = fmaf(acc.x, acc.x, fro);
+    } else {
+      G[(long long)j * m + i] = make_float2(acc.x, -acc.y);
+      fro = fmaf(2.f * acc.x, acc.x, fmaf(2.f * acc.y, acc.y, fro));
+    }
   }
-  tr = block_sum_f(tr, s);
-  if (!(tr > 1e-12f && tr < 1e12f)) return false;
+  tr = g.sumf(tr);
+  fro = g.sumf(fro);
+  const bool in_range = tr > 1e-12f && tr < 1e12f && fro > 0.f;
+  if (s2_out && tid == 0) {   // the screen's value and lower bound (s2_fp32)
+    float s2 = 0.f, lo = 0.f;
+    if (in_range) {
+      const float u = 5.9604645e-08f;
+      const float e1 = d * (dd + 6) * u;
+      const float eta = (2.f * e1 + e1 * e1 + (2.f * M + 4.f) * u * (1.f + e1) * (1.f + e1)) * 1.0001f;
+      const float lf = logf(fro), lt = logf(tr);
+      const float delta = 4.f * eta * sqrtf((float)m) * 1.0001f + 4.f * eta + ((float)m * m / 16.f + 112.f) * u +
+                          4.f * u * (fabsf(lf) + 2.f * fabsf(lt) + 2.f);
+      s2 = 2.f * lt - lf;
+      lo = s2 - delta;
+    }
+    *s2_out = s2;
+    *s2lo_out = lo;
+  }
+  if (!in_range || m - 1 > hcap) return false;
   const float sc = 1.f / tr;
   for (int idx = tid; idx < m * m; idx += nt) G[idx] = make_float2(G[idx].x * sc, G[idx].y * sc);
-  __syncthreads();
-  tridiag32(s, G, m, dg, od);
-  tridiag_eig32(s, dg, od, m, ev, s.btri32, kBTri);
+  g.sync();
+  tridiag32(g, G, m, dg, od, hv, hw);
+  tridiag_eig32(g, dg, od, m, ev, sh, shcap);
   float tot = 0.f;
   for (int i = tid; i < m; i += nt) tot += fmaxf(ev[i], 0.f);
-  tot = block_sum_f(tot, s);
+  tot = g.sumf(tot);
   float ent = 0.f;
   if (tot > 0.f) {
     const float inv = 1.f / tot;
@@ -1861,9 +1958,222 @@ __device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, i
       if (p > 0.f) ent = fmaf(-p, logf(p), ent);
     }
   }
-  ent = block_sum_f(ent, s);
+  ent = g.sumf(ent);
   *est_out = ent;
   return true;
+}
+
+// ------------------------------------------------------------ tensor-core Gram (tcgen05, kind::tf32)
+// G = X X^H (rows <= cols) or X^T conj(X) (rows > cols), m x m on the smaller side, of X (rows x cols
+// complex FP32, row-major) as one real product D = A B^T on the tensor cores: A (128 x 2K) holds the m rows
+// of X as interleaved (re, im), B (N x 2K, N = 2m padded to 16) holds them and, in rows m..2m-1, the rows
+// times i ((-im, re)), so that D[i][j] = Re G_ij and D[i][m + j] = Im G_ij.  Each operand value a is split
+// as a_hi + a_lo with a_hi = tf32(a) and a_lo = tf32(a - a_hi); a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+// (three MMAs per K step) has error at most 3 2^-22 |a b|, and the FP32 accumulation in TMEM adds at most
+// 2 u per addition (u = 2^-24), so |G^ - G|_ij <= (3 2^-22 + (4K + 16) u) sum_c |x_ic| |x_jc|.
+// Operands are staged KC real columns at a time into dynamic shared memory in the canonical K-major layout
+// without swizzling: core matrices of 8 rows x 16 bytes, 128 bytes apart along K (leading byte offset) and
+// 256 bytes apart along the rows (stride byte offset), one block per MMA K step of 8.  One thread issues the
+// MMAs and commits them to tc_mbar; every thread waits for that barrier (bounded; on a timeout the circuit's
+// status becomes GCAMPS_ENOCONV and the Gram is not used) before the stage is overwritten.  The accumulator
+// (128 lanes x N columns of FP32) is read back with tcgen05.ld into G (FP32).  Needs m <= kTcMaxM and the
+// kernel's TMEM (tc_tmem, kTcCols columns) and dynamic shared memory (tc_smem bytes).
+#if GCAMPS_TC
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ float tf32_round(float a) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+               :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+// bounded wait for phase `parity` of the mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.b32 %0, 1, 0, q;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Set-up of a CTA that uses gram_tc: its mbarrier and TMEM columns (warp 0 allocates).  Every thread calls it.
+__device__ void tc_setup(Smem& s) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&s.tc_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s.tc_commits = 0;
+  }
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&s.tc_tmem)), "r"(kTcCols));
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+}
+__device__ void tc_teardown(Smem& s) {
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(s.tc_tmem), "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+}
+// Real K columns staged per round: 16 (hi and lo parts of A and B, at most 48 KB), small enough to leave
+// most of the SM's L1 to the engine's global-memory scratch.
+__device__ __host__ __forceinline__ int tc_kc(int npad) { return 16; }
+
+__device__ __noinline__ bool gram_tc(Smem& s, const Ctx& C, const float2* X, int rows, int cols, float2* G) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const bool wide = rows <= cols;
+  const int m = wide ? rows : cols, Kc = wide ? cols : rows;
+  const int Kr = 2 * Kc, npad = (2 * m + 15) / 16 * 16;
+  const int KC = tc_kc(npad);
+  const int asz = (KC / 8) * (128 / 8) * 256, bsz = (KC / 8) * (npad / 8) * 256;   // bytes per part
+  uint8_t* Ahi = dsm;
+  uint8_t* Alo = Ahi + asz;
+  uint8_t* Bhi = Alo + asz;
+  uint8_t* Blo = Bhi + bsz;
+  const float* Xf = reinterpret_cast<const float*>(X);
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t tmem = s.tc_tmem, mbar = smem_addr(&s.tc_mbar);
+  uint32_t commits = s.tc_commits;
+  bool ok = true;
+  // value (row, kk) of A (rows < m are X's rows as (re, im) pairs; 0 beyond)
+  auto aval = [&](int row, int kk) -> float {
+    if (row >= m || kk >= Kr) return 0.f;
+    const int c = kk >> 1;
+    return wide ? Xf[((long long)row * cols + c) * 2 + (kk & 1)] : Xf[((long long)c * cols + row) * 2 + (kk & 1)];
+  };
+  for (int k0 = 0; k0 < Kr; k0 += KC) {
+    // stage the quads (4 consecutive K values of one row) of A and B, hi and lo parts
+    const int qa = 128 * (KC / 4), qb = npad * (KC / 4);
+    for (int q = tid; q < qa + qb; q += nt) {
+      const bool isA = q < qa;
+      const int qq = isA ? q : q - qa;
+      const int row = qq / (KC / 4), quad = qq % (KC / 4);
+      const int kk = k0 + 4 * quad;
+      float v[4];
+      if (isA || row < m) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = aval(row, kk + u);
+      } else if (row < 2 * m) {   // the row times i: (re, im) -> (-im, re)
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+          const float re = aval(row - m, kk + u), im = aval(row - m, kk + u + 1);
+          v[u] = -im;
+          v[u + 1] = re;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = 0.f;
+      }
+      float4 hi, lo;
+      hi.x = tf32_round(v[0]);
+      hi.y = tf32_round(v[1]);
+      hi.z = tf32_round(v[2]);
+      hi.w = tf32_round(v[3]);
+      lo.x = tf32_round(v[0] - hi.x);
+      lo.y = tf32_round(v[1] - hi.y);
+      lo.z = tf32_round(v[2] - hi.z);
+      lo.w = tf32_round(v[3] - hi.w);
+      const int R = isA ? 128 : npad;
+      const int off = (quad >> 1) * (R / 8) * 256 + (row >> 3) * 256 + (quad & 1) * 128 + (row & 7) * 16;
+      *reinterpret_cast<float4*>((isA ? Ahi : Bhi) + off) = hi;
+      *reinterpret_cast<float4*>((isA ? Alo : Blo) + off) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int t = 0; t < KC / 8; ++t) {
+        const uint64_t ah = umma_desc(smem_addr(Ahi + t * (128 / 8) * 256)), al = umma_desc(smem_addr(Alo + t * (128 / 8) * 256));
+        const uint64_t bh = umma_desc(smem_addr(Bhi + t * (npad / 8) * 256)), bl = umma_desc(smem_addr(Blo + t * (npad / 8) * 256));
+        umma_tf32(tmem, ah, bl, idesc, (k0 > 0 || t > 0) ? 1u : 0u);
+        umma_tf32(tmem, al, bh, idesc, 1u);
+        umma_tf32(tmem, ah, bh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+    }
+    ok = mbar_wait(mbar, commits & 1) && ok;
+    ++commits;
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // epilogue: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the columns
+  const int row = 32 * (warp & 3) + lane;
+  const int half = npad / 2, c0 = (warp >> 2) * half;
+  float* Gf = reinterpret_cast<float*>(G);
+  for (int cc = c0; cc < c0 + half; cc += 8) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cc));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (row < m)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = cc + u;
+        if (j < m) Gf[2 * ((long long)row * m + j)] = __uint_as_float(r[u]);
+        else if (j < 2 * m) Gf[2 * ((long long)row * m + (j - m)) + 1] = __uint_as_float(r[u]);
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0) {
+    s.tc_commits = commits;
+    if (C.dstats) C.dstats[3] += 8.0 * m * m * Kc;   // algorithmic flops of the complex Gram
+  }
+  if (!ok && tid == 0) set_failure(C, GCAMPS_ENOCONV, 3, rows, cols);
+  __syncthreads();
+  return ok;
+}
+#else
+__device__ __forceinline__ void tc_setup(Smem&) {}
+__device__ __forceinline__ void tc_teardown(Smem&) {}
+#endif  // GCAMPS_TC
+
+// The full m x m Gram (smaller side) of X (rows x cols complex FP32) in FP32: SIMT on a warp; on a CTA the
+// tensor cores (gram_tc) when the kernel set them up and m <= kTcMaxM, else SIMT.
+__device__ void gram_fp32_simt(int tid, int nt, const float2* X, int rows, int cols, float2* G) {
+  const int m = rows < cols ? rows : cols;
+  for (int idx = tid; idx < m * (m + 1) / 2; idx += nt) {
+    int i, j;
+    tri_index(idx, i, j);
+    float2 acc = make_float2(0.f, 0.f);
+    if (rows <= cols) {
+      const float2* ri = X + (long long)i * cols;
+      const float2* rj = X + (long long)j * cols;
+      for (int c = 0; c < cols; ++c) acc = ffmac2(ri[c], rj[c], acc);
+    } else {
+      for (int r = 0; r < rows; ++r) acc = ffmac2(X[(long long)r * cols + i], X[(long long)r * cols + j], acc);
+    }
+    G[(long long)i * m + j] = acc;
+    if (i != j) G[(long long)j * m + i] = make_float2(acc.x, -acc.y);
+  }
+}
+template <>
+__device__ void gram_fp32<WarpGroup>(const WarpGroup& g, const Ctx& C, const float2* X, int rows, int cols, float2* G) {
+  gram_fp32_simt(g.tid, g.n, X, rows, cols, G);
+  g.sync();
+}
+template <>
+__device__ void gram_fp32<BlockGroup>(const BlockGroup& g, const Ctx& C, const float2* X, int rows, int cols,
+                                      float2* G) {
+#if GCAMPS_TC
+  const int m = rows < cols ? rows : cols;
+  if (C.e->tc_smem > 0 && m <= kTcMaxM && gram_tc(*g.s, C, X, rows, cols, G)) return;
+#endif
+  gram_fp32_simt(g.tid, g.n, X, rows, cols, G);
+  g.sync();
 }
 
 // Scores classes list[0..cnt) (all K classes if list is null) on the whole cluster: small problems
@@ -1872,7 +2182,7 @@ __device__ __noinline__ bool vn_est32(Smem& s, const Ctx& C, const float2* th, i
 // kS2Exact: S2 in FP64 only (class 0 still gets kExact: its eigenvalues certify QR moves).
 // kEstimate: the FP32 von Neumann estimate and its bound (lead->vest, lead->vbd; CTA-level sizes only).
 enum ScoreMode { kExact = 0, kScreen = 1, kS2Exact = 2, kEstimate = 3 };
-__device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
+__device__ __noinline__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
                               const int* list, int cnt, int mode) {
   const Engine& e = *C.e;
   const int d = C.d, dd = d * d;
@@ -1888,6 +2198,19 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
     const int gw = warp * C.csize + C.rank, nw = C.csize * kWarps;
     for (int t = gw; t < cnt; t += nw) {
       const int k = list ? list[t] : t;
+      if (mode == kEstimate) {
+        float est = 0.f, v = 0.f, lo = 0.f;
+        const bool ok = vn_est32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws),
+                                 s.whv[warp], s.whw[warp], 32, s.wtri32[warp], 32, &est, &v, &lo);
+        if (lane == 0) {
+          lead->s2[k] = v;
+          lead->s2lo[k] = lo;
+          lead->vest[k] = est;
+          lead->vbd[k] = ok ? lead->dval[3] : 1e300;   // the visit's bound (select_class), or none
+          lead->estd[k] = 1;
+        }
+        continue;
+      }
       if (mode == kScreen) {
         double v, lo;
         s2_fp32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, reinterpret_cast<float2*>(ws), &v, &lo);
@@ -1898,8 +2221,9 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         continue;
       }
       const bool want_vn = mode == kExact || k == 0;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, kSmall, want_vn,
-                                   s.wtri[warp], s.wtri32[warp], 32);
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd,
+                                   e.candU32 + (long long)k * dd * dd, ws, kSmall, want_vn, s.wtri[warp],
+                                   s.wtri32[warp], 32);
       if (lane == 0) {
         lead->s2[k] = sc.s2;
         lead->evald[k] = 1;
@@ -1926,8 +2250,9 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
       }
       if (mode == kEstimate) {
         float est = 0.f;
-        const bool ok = vn_est32(s, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd,
-                                 reinterpret_cast<float2*>(ws), &est);
+        const bool ok = vn_est32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd,
+                                 reinterpret_cast<float2*>(ws), s.hv, s.hw, kBTri, s.btri32, kBTri, &est,
+                                 (float*)nullptr, (float*)nullptr);
         if (threadIdx.x == 0) {
           lead->vest[k] = est;
           lead->vbd[k] = ok ? lead->dval[3] : 1e300;   // the visit's bound (select_class), or none
@@ -1937,8 +2262,8 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         continue;
       }
       const bool want_vn = mode == kExact || k == 0;
-      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd, ws, e.scap, want_vn,
-                                   s.btri, s.btri32, kBTri);
+      const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd,
+                                   e.candU32 + (long long)k * dd * dd, ws, e.scap, want_vn, s.btri, s.btri32, kBTri);
       if (threadIdx.x == 0) {
         lead->s2[k] = sc.s2;
         lead->evald[k] = 1;
@@ -1964,6 +2289,62 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
 // Cluster-wide choice of the class for one theta (shape chi_l x d x d x chi_r in global memory,
 // readable by every CTA).  Returns the chosen class on the leader (-1 on the other CTAs); the
 // leader's s.vn / s.evald hold the evaluated entropies and *nev their count.
+// The decision over the exactly evaluated classes of the leader's shared memory (select_class), and the
+// record of the visit's scores; -1 on the other CTAs.
+__device__ __noinline__ int decide_class(Smem& s, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out, long long& tp) {
+  const Engine& e = *C.e;
+  const bool leader = C.rank == 0;
+  const int d = C.d, kind = e.score_kind;
+  const int rows = cl * d, cols = d * cr;
+  if (!leader) return -1;
+  if (threadIdx.x == 0) {
+    // the decision over the exactly evaluated classes: key = S_vN (kind 0), S2 (kind 1), or the
+    // weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
+    // class is applied only if it beats the identity
+    int nev = 0, rmin = 1 << 30;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k]) {
+        ++nev;
+        if (s.rk[k] < rmin) rmin = s.rk[k];
+      }
+    auto key = [&](int k) { return kind == 1 ? s.s2[k] : s.vn[k]; };
+    double best = 1e300;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) best = fmin(best, key(k));
+    int kb = 0;
+    for (int k = 0; k < C.K; ++k)
+      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin) && key(k) <= best + e.tie_tol) {
+        kb = k;
+        break;
+      }
+    const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
+    if (!better) kb = 0;
+    s.ival[4] = kb;
+    s.ival[5] = nev;
+  }
+  {
+    double* out = e.lastsc + (long long)C.c * (3 * kMaxK + 2 + 2 * kSmall);
+    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
+      out[k] = s.s2[k];
+      out[kMaxK + k] = s.vn[k];
+      out[2 * kMaxK + k] = s.evald[k];
+    }
+    if (threadIdx.x == 0) {
+      out[3 * kMaxK] = cl;
+      out[3 * kMaxK + 1] = cr;
+    }
+    if ((long long)rows * cols <= kSmall)
+      for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
+        out[3 * kMaxK + 2 + 2 * k] = theta[k].x;
+        out[3 * kMaxK + 3 + 2 * k] = theta[k].y;
+      }
+  }
+  __syncthreads();
+  prof_lap(C, P_DECIDE, tp);
+  *nev_out = s.ival[5];
+  return s.ival[4];
+}
+
 __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out) {
   long long tp = prof_start(C);
   const Engine& e = *C.e;
@@ -1973,16 +2354,51 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
   const int m = rows < cols ? rows : cols;
   const bool prune = m > kPruneMin;
   const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
+  const int kind = e.score_kind;
+  // The von Neumann score prunes with FP32 estimates whose error bound depends on the shape only: the leader
+  // computes it once, published with the FP32 copy of theta by the barrier below.
+  const bool est_kind = prune && kind == 0;
+  if (leader && threadIdx.x == 0) {
+    s.ival[6] = 0;
+    if (est_kind) s.dval[3] = vn_est_bound(d, m, rows < cols ? cols : rows);
+  }
   if (prune) {   // FP32 copy of theta for the screen, shared by the cluster
     if (leader)
       for (int i = threadIdx.x; i < rows * cols; i += blockDim.x)
         C.th32[i] = make_float2((float)theta[i].x, (float)theta[i].y);
     cluster_sync();
   }
+  if (est_kind && small && lead->dval[3] < 1.0) {
+    // Warp-level sizes: one pass gives every class its FP32 von Neumann estimate (and its Renyi-2 value and
+    // bound, from the same Gram); exact FP64 entropies only for the identity and the classes whose estimate
+    // interval reaches down to U + tie_tol, U the smallest upper bound.  A class left out has S_vN above
+    // U + tie_tol >= best + tie_tol (the class that set U is evaluated exactly), so the decision equals
+    // evaluating every class.
+    score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, kEstimate);
+    cluster_sync();
+    prof_lap(C, P_EST, tp);
+    if (leader && threadIdx.x == 0) {
+      double U = 1e300;
+      for (int k = 0; k < C.K; ++k) {
+        s.evald[k] = 0;
+        U = fmin(U, s.vest[k] + s.vbd[k]);
+      }
+      int cnt = 1;
+      s.list[0] = 0;
+      for (int k = 1; k < C.K; ++k)
+        if (s.vest[k] - s.vbd[k] <= U + e.tie_tol + 1e-12) s.list[cnt++] = k;
+      s.nlist = cnt;
+      s.ival[6] = C.K;
+    }
+    cluster_sync();
+    score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
+    cluster_sync();
+    prof_lap(C, P_EXACT, tp);
+    return decide_class(s, C, theta, cl, cr, nev_out, tp);
+  }
   score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, prune ? kScreen : kExact);
   cluster_sync();
   prof_lap(C, prune ? P_SCREEN : P_EXACT, tp);
-  const int kind = e.score_kind;
   // weight-rank threshold (the same as the QR-move certificate) and the rank lower bound from S2:
   // the weights above tau carry at least 1 - m tau of the trace, so sum p^2 >= (1 - m tau)^2 / rank and
   // rank >= exp(S2 + 2 ln(1 - m tau)) >= exp(S2 - 2.01 m tau)
@@ -2000,13 +2416,7 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
   // tie_tol (the class that set U is evaluated exactly), so the decision equals evaluating every class.
   // the estimate bound depends on the shape only: computed once, on the leader, and read from its shared
   // memory by every CTA after the next cluster barrier
-  if (leader && threadIdx.x == 0) s.ival[6] = 0;
-  bool estimate = false;
-  if (prune && kind == 0 && !small) {
-    if (leader && threadIdx.x == 0) s.dval[3] = vn_est_bound(d, m, rows < cols ? cols : rows);
-    cluster_sync();
-    estimate = lead->dval[3] < 1.0;
-  }
+  const bool estimate = est_kind && !small && lead->dval[3] < 1.0;
   if (estimate) {
     if (leader) {
       const int L = C.csize - 1;
@@ -2140,53 +2550,7 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
     }
     prof_lap(C, P_EXACT, tp);
   }
-  if (!leader) return -1;
-  if (threadIdx.x == 0) {
-    // the decision over the exactly evaluated classes: key = S_vN (kind 0), S2 (kind 1), or the
-    // weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
-    // class is applied only if it beats the identity
-    int nev = 0, rmin = 1 << 30;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k]) {
-        ++nev;
-        if (s.rk[k] < rmin) rmin = s.rk[k];
-      }
-    auto key = [&](int k) { return kind == 1 ? s.s2[k] : s.vn[k]; };
-    double best = 1e300;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) best = fmin(best, key(k));
-    int kb = 0;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin) && key(k) <= best + e.tie_tol) {
-        kb = k;
-        break;
-      }
-    const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
-    if (!better) kb = 0;
-    s.ival[4] = kb;
-    s.ival[5] = nev;
-  }
-  {
-    double* out = e.lastsc + (long long)C.c * (3 * kMaxK + 2 + 2 * kSmall);
-    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-      out[k] = s.s2[k];
-      out[kMaxK + k] = s.vn[k];
-      out[2 * kMaxK + k] = s.evald[k];
-    }
-    if (threadIdx.x == 0) {
-      out[3 * kMaxK] = cl;
-      out[3 * kMaxK + 1] = cr;
-    }
-    if ((long long)rows * cols <= kSmall)
-      for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
-        out[3 * kMaxK + 2 + 2 * k] = theta[k].x;
-        out[3 * kMaxK + 3 + 2 * k] = theta[k].y;
-      }
-  }
-  __syncthreads();
-  prof_lap(C, P_DECIDE, tp);
-  *nev_out = s.ival[5];
-  return s.ival[4];
+  return decide_class(s, C, theta, cl, cr, nev_out, tp);
 }
 
 __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, int* accepted) {
@@ -2208,10 +2572,28 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
   int nev = 0;
-  const int kbsel = select_class(s, lead, C, theta, cl, cr, &nev);
   // Splits with many Jacobi columns run their rotations on the whole cluster: the other CTAs wait for the
   // leader's choice (a QR move or such a split) at one more cluster barrier.
   const bool big = C.csize > 1 && m >= kClusterJacobiMin;
+  if (e.replay && e.replay_n[C.c] > 0) {
+    // replay: the recorded class of this visit (every CTA reads the same list; a visit past its end or at
+    // another bond invalidates the circuit)
+    if (leader && threadIdx.x == 0) {
+      const int nd = C.meta[M_NDEC];
+      const int* rp = e.replay + ((long long)C.c * kDecCap + nd) * 2;
+      int kb = 0;
+      if (nd >= e.replay_n[C.c] || nd >= kDecCap || rp[0] != i) set_status(C, GCAMPS_EINVAL);
+      else kb = rp[1];
+      s.ival[4] = (kb >= 0 && kb < C.K) ? kb : 0;
+      s.ival[6] = 0;
+      s.rank0 = -1;   // no certificate: the visit splits by SVD
+    }
+    __syncthreads();
+    nev = -1;
+  }
+  const int kbsel = nev < 0 ? (leader ? s.ival[4] : -1)
+                            : select_class(s, lead, C, theta, cl, cr, &nev);
+  if (nev < 0) nev = 0;
   if (!leader) {
     if (!big) return;
     cluster_sync();
@@ -2434,6 +2816,64 @@ __device__ void conj_weyl(Smem& s, const Ctx& C, const int8_t* xz, int* acc_x, i
 }
 
 
+
+// ------------------------------------------------------------ bodies of the cluster kernels
+// Each is the whole kernel: the FP64 translation units and the precision form's (GCAMPS_TC = 1) wrap them
+// in kernels of their own.  One thread-block cluster of e.csize CTAs per circuit.
+__device__ __forceinline__ void run_body(const Engine& e, const gcamps_op* ops, int first, int stop, int c, int rank) {
+  __shared__ Smem s;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  if (GCAMPS_TC && e.tc_smem) tc_setup(s);
+  for (int i = first; i < stop; ++i) run_op(s, lead, C, ops[i]);
+  cluster_sync();
+  if (GCAMPS_TC && e.tc_smem) tc_teardown(s);
+}
+
+__device__ __forceinline__ void single_body(const Engine& e, const gcamps_op& op) {
+  __shared__ Smem s;
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  if (GCAMPS_TC && e.tc_smem) tc_setup(s);
+  run_op(s, lead, C, op);
+  cluster_sync();
+  if (GCAMPS_TC && e.tc_smem) tc_teardown(s);
+}
+
+// Scores of every class on a caller-provided theta (chi_l, d, d, chi_r), through the same cluster code as the
+// disentangler: S2 and S_vN of all classes (no pruning), then the disentangler's own choice.
+__device__ __forceinline__ void score_theta_body(const Engine& e, const double2* th, int cl, int cr, double* out_s2,
+                                                 double* out_vn, int* out_choice) {
+  __shared__ Smem s;
+  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
+  Ctx C = make_ctx(e, c, rank);
+  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
+  init_tau(s, e.d);
+  if (GCAMPS_TC && e.tc_smem) tc_setup(s);
+  if (rank == 0)   // the FP32 copy of theta (the precision form's contractions read it)
+    for (int i = threadIdx.x; i < cl * e.d * e.d * cr; i += blockDim.x)
+      C.th32[i] = make_float2((float)th[i].x, (float)th[i].y);
+  cluster_sync();
+  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
+  cluster_sync();
+  if (c == 0 && rank == 0)
+    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
+      out_s2[k] = s.s2[k];
+      out_vn[k] = s.vn[k];
+    }
+  cluster_sync();
+  int nev = 0;
+  const int kb = select_class(s, lead, C, th, cl, cr, &nev);
+  if (c == 0 && rank == 0 && threadIdx.x == 0) {
+    out_choice[0] = kb;
+    out_choice[1] = nev;
+  }
+  cluster_sync();
+  if (GCAMPS_TC && e.tc_smem) tc_teardown(s);
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------- host launchers
@@ -2444,10 +2884,21 @@ cudaError_t launch_cluster(void (*kern)(KArgs...), const Engine& e, cudaStream_t
     cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (a != cudaSuccess) return a;
   }
+  if (e.tc_smem > 0) {
+    cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, e.tc_smem);
+    if (a != cudaSuccess) return a;
+    // a shared-memory carveout for two such CTAs per SM, the rest of the SM's 256 KB left to L1
+    cudaFuncAttributes fa;
+    a = cudaFuncGetAttributes(&fa, kern);
+    if (a != cudaSuccess) return a;
+    const int pct = (int)((2.0 * (fa.sharedSizeBytes + e.tc_smem + 1024) * 100.0) / (228.0 * 1024.0)) + 1;
+    a = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+    if (a != cudaSuccess) return a;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(e.batch * e.csize), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)e.tc_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -7,14 +7,8 @@ namespace gcx {
 namespace {
 
 __global__ void __launch_bounds__(kThreads, kMinCtas) k_run(Engine e, const gcamps_op* ops, const int32_t* begin) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  const int stop = begin[c + 1];
-  for (int i = begin[c]; i < stop; ++i) run_op(s, lead, C, ops[i]);
-  cluster_sync();
+  const int c = blockIdx.x / e.csize;
+  run_body(e, ops, begin[c], begin[c + 1], c, blockIdx.x % e.csize);
 }
 
 
@@ -257,9 +251,47 @@ __global__ void k_apply_clifford_dense(Engine e, int c, long long dim, const dou
 }
 
 
+// <M1|M2> for circuit c1 of e1 and circuit c2 of e2 (same n and d; Sec. 2.4 MPS): transfer matrices
+// E[a1][a2] from the left, T[a1][s][b2] = sum_a2 E[a1][a2] B[a2][s][b2], then
+// E'[b1][b2] = sum_{a1, s} conj(A[a1][s][b1]) T[a1][s][b2]; FP64, one CTA, scratch of circuit c1.
+__global__ void __launch_bounds__(kThreads) k_overlap(Engine e1, int c1, Engine e2, int c2, double2* out) {
+  const Ctx A = make_ctx(e1, c1), B = make_ctx(e2, c2);
+  const int n = A.n, d = e1.d;
+  double2* E = A.scr + e1.sl.b;
+  double2* T = A.scr + e1.sl.tmp;
+  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int la = A.dims[j], ra = A.dims[j + 1], lb = B.dims[j], rb = B.dims[j + 1];
+    const double2* Aj = site_ptr(A, j);
+    const double2* Bj = site_ptr(B, j);
+    for (long long idx = threadIdx.x; idx < (long long)la * d * rb; idx += blockDim.x) {
+      const int a1 = (int)(idx / (d * rb)), sb = (int)(idx % (d * rb));
+      double2 acc = cz();
+      for (int a2 = 0; a2 < lb; ++a2) acc = cfma(E[(long long)a1 * lb + a2], Bj[(long long)a2 * d * rb + sb], acc);
+      T[idx] = acc;
+    }
+    __syncthreads();
+    for (long long idx = threadIdx.x; idx < (long long)ra * rb; idx += blockDim.x) {
+      const int b1 = (int)(idx / rb), b2 = (int)(idx % rb);
+      double2 acc = cz();
+      for (int as = 0; as < la * d; ++as) acc = cfmac(Aj[(long long)as * ra + b1], T[(long long)as * rb + b2], acc);
+      E[idx] = acc;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = E[0];
+}
+
 }  // namespace
 
+cudaError_t launch_overlap(const Engine& e1, int c1, const Engine& e2, int c2, double2* out_dev, cudaStream_t st) {
+  k_overlap<<<1, kThreads, 0, st>>>(e1, c1, e2, c2, out_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_run(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st) {
+  if (e.precision) return launch_run_tc(e, ops_dev, begin_dev, st);
   return launch_cluster(k_run, e, st, e, ops_dev, begin_dev);
 }
 

@@ -7,24 +7,10 @@ namespace gcx {
 namespace {
 
 __global__ void __launch_bounds__(kThreads, kMinCtas) k_run_all(Engine e, const gcamps_op* ops, int nops) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  for (int i = 0; i < nops; ++i) run_op(s, lead, C, ops[i]);
-  cluster_sync();
+  run_body(e, ops, 0, nops, blockIdx.x / e.csize, blockIdx.x % e.csize);
 }
 
-__global__ void __launch_bounds__(kThreads, kMinCtas) k_single(Engine e, gcamps_op op) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  run_op(s, lead, C, op);
-  cluster_sync();
-}
+__global__ void __launch_bounds__(kThreads, kMinCtas) k_single(Engine e, gcamps_op op) { single_body(e, op); }
 
 
 // Schmidt values of one bond: move the centre next to it and take the singular values.
@@ -45,10 +31,12 @@ __global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond,
 }  // namespace
 
 cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
+  if (e.precision) return launch_run_all_tc(e, ops_dev, nops, st);
   return launch_cluster(k_run_all, e, st, e, ops_dev, nops);
 }
 
 cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
+  if (e.precision) return launch_single_tc(e, op, st);
   return launch_cluster(k_single, e, st, e, op);
 }
 

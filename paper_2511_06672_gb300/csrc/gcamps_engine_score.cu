@@ -6,31 +6,10 @@
 namespace gcx {
 namespace {
 
-// Scores of every class on a caller-provided theta (chi_l, d, d, chi_r), through the same cluster
-// code as the disentangler: S2 of all classes and S_vN of all classes (no pruning).  Used to test
-// the scoring step on its own.
+// Scores of every class on a caller-provided theta (score_theta_body).
 __global__ void __launch_bounds__(kThreads, kMinCtas) k_score_theta(Engine e, const double2* th, int cl, int cr,
-                                                          double* out_s2, double* out_vn, int* out_choice) {
-  __shared__ Smem s;
-  const int c = blockIdx.x / e.csize, rank = blockIdx.x % e.csize;
-  Ctx C = make_ctx(e, c, rank);
-  Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
-  init_tau(s, e.d);
-  score_classes(s, lead, C, th, cl, cr, nullptr, C.K, kExact);
-  cluster_sync();
-  if (c == 0 && rank == 0)
-    for (int k = threadIdx.x; k < C.K; k += blockDim.x) {
-      out_s2[k] = s.s2[k];
-      out_vn[k] = s.vn[k];
-    }
-  cluster_sync();
-  int nev = 0;
-  const int kb = select_class(s, lead, C, th, cl, cr, &nev);   // the disentangler's own choice
-  if (c == 0 && rank == 0 && threadIdx.x == 0) {
-    out_choice[0] = kb;
-    out_choice[1] = nev;
-  }
-  cluster_sync();
+                                                                   double* out_s2, double* out_vn, int* out_choice) {
+  score_theta_body(e, th, cl, cr, out_s2, out_vn, out_choice);
 }
 
 // FP32 von Neumann estimates of every class on a caller-provided theta, with their error bounds (the pruning
@@ -50,7 +29,9 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) k_estimate_theta(Engine e,
   const double bound = vn_est_bound(d, rows < cols ? rows : cols, rows < cols ? cols : rows);
   for (int k = rank; k < C.K; k += C.csize) {
     float est = 0.f;
-    const bool ok = vn_est32(s, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, ws, &est);
+    BlockGroup g{&s, (int)threadIdx.x, (int)blockDim.x};
+    const bool ok = vn_est32(g, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, ws, s.hv, s.hw, kBTri,
+                             s.btri32, kBTri, &est, (float*)nullptr, (float*)nullptr);
     if (threadIdx.x == 0) {
       out_est[k] = est;
       out_bd[k] = ok ? bound : 1e300;
@@ -69,6 +50,7 @@ cudaError_t launch_estimate_theta(const Engine& e, const double2* th, int cl, in
 
 cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
                                int* choice, cudaStream_t st) {
+  if (e.precision) return launch_score_theta_tc(e, th, cl, cr, s2, vn, choice, st);
   return launch_cluster(k_score_theta, e, st, e, th, cl, cr, s2, vn, choice);
 }
 

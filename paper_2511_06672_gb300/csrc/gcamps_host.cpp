@@ -363,6 +363,8 @@ struct gcamps {
   double2* out_dev = nullptr;
   double* schmidt_dev = nullptr;
   int* cnt_dev = nullptr;
+  int* replay_dev = nullptr;           // [batch][kDecCap][2] recorded decisions to replay
+  int* replay_n_dev = nullptr;         // [batch] their counts (0: choose)
 };
 
 namespace {
@@ -527,7 +529,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   gcamps_default_opts(&opts);
   if (o) opts = *o;
   if (!(opts.cutoff >= 0.0) || opts.max_sweeps < 0 || opts.score_kind < 0 || opts.score_kind > 2 ||
-      opts.precision != 0 || opts.snapshot_entries < 0 || opts.snapshot_max_gates < 0 ||
+      opts.precision < 0 || opts.precision > 1 || opts.snapshot_entries < 0 || opts.snapshot_max_gates < 0 ||
       (opts.snapshot_entries > 0) != (opts.snapshot_max_gates > 0) || opts.snapshot_entries > (1LL << 31) - 1 ||
       !(opts.tie_tol >= 0.0))
     return GCAMPS_EINVAL;
@@ -547,8 +549,11 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.max_sweeps = opts.max_sweeps;
   e.score_kind = opts.score_kind;
   e.jacobi_cap = 60;
+  e.precision = opts.precision;
+  e.tc_smem = opts.precision ? gcx::kTcSmemBytes : 0;
   e.cutoff = opts.cutoff;
-  e.tie_tol = opts.tie_tol;
+  // FP32 contractions resolve scores to about 1e-6 nats: ties are taken at least that wide
+  e.tie_tol = opts.precision ? std::max(opts.tie_tol, gcx::kMixedTieTol) : opts.tie_tol;
   e.strict_weight = opts.strict_weight;
   // bond capacities of each circuit: after the MPO a bond holds at most d * min(chi_max, Schmidt
   // bound); slots of each circuit's sites laid out back to back, circuits one after another
@@ -757,6 +762,8 @@ void gcamps_destroy(gcamps_t* h) {
   if (h->ops_dev) cudaFree(h->ops_dev);
   if (h->begin_dev) cudaFree(h->begin_dev);
   if (h->schmidt_dev) cudaFree(h->schmidt_dev);
+  if (h->replay_dev) cudaFree(h->replay_dev);
+  if (h->replay_n_dev) cudaFree(h->replay_n_dev);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -1192,7 +1199,52 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   st->discarded_weight = ds[0];
   st->scoring_flops = ds[1];
   st->screen_flops = ds[2];
+  st->tensor_flops = ds[3];
   return device_status(h);
+}
+
+int gcamps_set_replay(gcamps_t* h, int circuit, const int32_t* pairs, int32_t count) {
+  int rc = check_circuit(h, circuit);
+  if (rc) return rc;
+  if (count < 0 || count > gcx::kDecCap || (count > 0 && !pairs)) return fail(h, GCAMPS_EINVAL, "bad replay list");
+  for (int k = 0; k < count; ++k)
+    if (pairs[2 * k] < 0 || pairs[2 * k] > h->nq[circuit] - 2 || pairs[2 * k + 1] < 0 || pairs[2 * k + 1] >= h->e.K)
+      return fail(h, GCAMPS_EINVAL, "replay pair out of range");
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!h->replay_dev) {
+    const size_t nb = (size_t)h->e.batch * gcx::kDecCap * 2 * sizeof(int);
+    if (cudaMalloc(&h->replay_dev, nb) != cudaSuccess || cudaMalloc(&h->replay_n_dev, h->e.batch * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GCAMPS_ENOMEM, "replay buffers");
+    }
+    GC_CUDA(h, cudaMemset(h->replay_n_dev, 0, h->e.batch * sizeof(int)));
+    h->e.replay = h->replay_dev;
+    h->e.replay_n = h->replay_n_dev;
+  }
+  if (count > 0)
+    GC_CUDA(h, cudaMemcpy(h->replay_dev + (size_t)circuit * gcx::kDecCap * 2, pairs, (size_t)count * 2 * sizeof(int),
+                          cudaMemcpyHostToDevice));
+  GC_CUDA(h, cudaMemcpy(h->replay_n_dev + circuit, &count, sizeof(int), cudaMemcpyHostToDevice));
+  return GCAMPS_OK;
+}
+
+int gcamps_overlap(gcamps_t* h1, int circuit1, gcamps_t* h2, int circuit2, double* re, double* im) {
+  int rc = check_circuit(h1, circuit1);
+  if (rc) return rc;
+  rc = check_circuit(h2, circuit2);
+  if (rc) return fail(h1, rc, "second handle or circuit invalid");
+  if (!re || !im) return fail(h1, GCAMPS_EINVAL, "null output");
+  if (h1->nq[circuit1] != h2->nq[circuit2] || h1->e.d != h2->e.d || h1->e.maxdim != h2->e.maxdim)
+    return fail(h1, GCAMPS_EINVAL, "overlap needs the same n, d and chi_max");
+  GC_CUDA(h1, cudaStreamSynchronize(h2->stream));
+  GC_CUDA(h1, gcx::launch_overlap(h1->e, circuit1, h2->e, circuit2, h1->out_dev, h1->stream));
+  double2 v;
+  GC_CUDA(h1, cudaMemcpyAsync(&v, h1->out_dev, sizeof v, cudaMemcpyDeviceToHost, h1->stream));
+  GC_CUDA(h1, cudaStreamSynchronize(h1->stream));
+  *re = v.x;
+  *im = v.y;
+  rc = device_status(h1);
+  return rc ? rc : device_status(h2);
 }
 
 int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count) {

@@ -11,6 +11,12 @@ namespace gcx {
 
 constexpr int kThreads = 256;             // threads per CTA; a cluster of CTAs runs one circuit
 constexpr int kClusterJacobiMin = 24;     // SVD splits of bond visits with at least this many Jacobi columns use the cluster
+constexpr int kTcMaxM = 128;               // tensor-core Grams: at most this many rows (one M = 128 tile)
+constexpr int kTcCols = 256;               // TMEM columns each engine CTA allocates for them
+// their staging buffers: hi and lo parts of A (128 rows) and B (up to 256 rows) for 16 real K columns, plus
+// alignment
+constexpr int kTcSmemBytes = 2 * 2 * (16 + 32) * 256 + 1024;
+constexpr double kMixedTieTol = 1e-5;      // tie tolerance of the precision form (FP32 contractions)
 constexpr int kMinCtas = 2;               // resident CTAs per SM the engine kernels are compiled for (128 registers)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCluster = 16;           // CTAs per circuit (thread-block cluster)
@@ -66,6 +72,8 @@ struct Engine {
   int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;   // n: largest qudit count of the batch
   int score_kind;                 // 0 von Neumann, 1 Renyi-2, 2 weight rank then von Neumann
   int jacobi_cap;                 // most sweeps of one Jacobi SVD before GCAMPS_ENOCONV (60)
+  int precision;                  // 0 FP64 contractions; 1 FP32 contractions (tensor cores at CTA-level sizes)
+  int tc_smem;                    // dynamic shared memory of the engine kernels (bytes; 0 without tensor cores)
   double cutoff, tie_tol, strict_weight;
   long long tcap;                 // elements of the largest two-site matrix
   long long wcap;                 // elements of the largest Jacobi rotation matrix
@@ -83,6 +91,10 @@ struct Engine {
   long long* prof;                          // [batch][P_COUNT]
   double* dstats;                           // [batch][4]: discarded weight, FP64 scoring flops, FP32 screen flops, spare
   int* dec;                                 // [batch][kDecCap][2]
+  // replay (null when unused): circuit c with replay_n[c] > 0 applies the recorded (bond, class) pairs
+  // replay[c][k] at its bond visits in order instead of choosing
+  const int* replay;                        // [batch][kDecCap][2]
+  const int* replay_n;                      // [batch]
   int8_t* weyl;                             // [batch][2n]
   double* lastsc;                           // [batch][3 * kMaxK + 2 + 2 * kSmall]: s2 | vn | evaluated | chi_l, chi_r | theta of the last visit
   double2* scr;     ScratchLayout sl;       // per-circuit scratch, stride sl.total
@@ -109,6 +121,14 @@ cudaError_t launch_statevector(const Engine& e, int circuit, double2* out_dev, l
                                const int32_t* ys_dev, long long nys, void* work, cudaStream_t st);
 cudaError_t launch_score_theta(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
                                int* choice, cudaStream_t st);
+// The precision form's variants of the cluster kernels (compiled with the tensor-core Gram).
+cudaError_t launch_run_tc(const Engine& e, const gcamps_op* ops_dev, const int32_t* begin_dev, cudaStream_t st);
+cudaError_t launch_run_all_tc(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st);
+cudaError_t launch_single_tc(const Engine& e, const gcamps_op& op, cudaStream_t st);
+cudaError_t launch_score_theta_tc(const Engine& e, const double2* th, int cl, int cr, double* s2, double* vn,
+                                  int* choice, cudaStream_t st);
+// <M1|M2> of circuit c1 of e1 and circuit c2 of e2 (same n and d; transfer matrices, FP64, scratch of c1).
+cudaError_t launch_overlap(const Engine& e1, int c1, const Engine& e2, int c2, double2* out_dev, cudaStream_t st);
 cudaError_t launch_estimate_theta(const Engine& e, const double2* th, int cl, int cr, double* est, double* bd,
                                   cudaStream_t st);
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev,
