@@ -57,16 +57,25 @@ def arith_peaks():
                 f"measured ({os.path.relpath(PEAKS_FILE, ROOT)}, {p.get('when', '?')})")
     except (OSError, ValueError, KeyError):
         return FP64_NOMINAL_TFLOPS, FP32_NOMINAL_TFLOPS, "nominal (no measurement committed)"
-ENGINE_SRC = os.path.join(ROOT, "paper_2511_06672_gb300", "csrc", "gcamps_engine.cu")
+ENGINE_SRCS = [os.path.join(ROOT, "paper_2511_06672_gb300", "csrc", f)
+               for f in ("gcamps_device.cuh", "gcamps_engine.cu", "gcamps_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_run_dram_bench_workload.txt")
 
 
-def engine_traffic():
-    """DRAM bytes per k_run launch from the committed ncu summary, if it was taken on this engine
-    source (sha256 recorded beside it); else None."""
+def engine_source_hash() -> str:
+    """sha256 over the sources of the benchmark's kernel (device code, its translation unit, the layout)."""
     import hashlib
+    h = hashlib.sha256()
+    for f in ENGINE_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def engine_traffic():
+    """DRAM bytes per k_run launch from the committed ncu summary, if it was taken on these engine
+    sources (sha256 recorded beside it); else None."""
     try:
-        want = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()
+        want = engine_source_hash()
         kv = dict(line.strip().split("=", 1) for line in open(TRAFFIC_FILE) if "=" in line and not line.startswith("#"))
         if kv.get("engine_sha256") == want:
             return float(kv["dram_bytes_per_launch"])
@@ -456,6 +465,16 @@ def run_gradient(args):
     import paper_2511_06672_gb300 as G
     d, n, layers, ngates, chi = 3, 24, 20, 48, 256
     gates, _ = param_phase_circuit(n, d, layers, ngates, 1 + rank)
+    if 0 < args.grad_prefix < ngates:   # the circuit up to its grad_prefix-th parametrised gate
+        k, cut = 0, len(gates)
+        for i, g in enumerate(gates):
+            if not hasattr(g, "sp_index"):
+                k += 1
+                if k == args.grad_prefix:
+                    cut = i + 1
+                    break
+        gates = gates[:cut]
+    nparam = sum(1 for g in gates if not hasattr(g, "sp_index"))
     ops = G.ops_from_gates(gates, d)
     x = np.zeros(n, dtype=np.int32)
     z = np.zeros(n, dtype=np.int32)
@@ -488,7 +507,7 @@ def run_gradient(args):
         "n_gpus": world, "steps": len(fwd), "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(fwd)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "gcamps-gradient-qutrit-n24-L20-48params-chi256", "observable": "Re<Z_0 Z_12>",
-                   "timing": "host wall clock around synchronising calls"},
+                   "parametrised_gates_run": nparam, "timing": "host wall clock around synchronising calls"},
         "forward_s": float(np.mean(fwd)) if fwd else None, "adjoint_s": float(np.mean(bwd)) if bwd else None,
         "value_re": val, "exact": exact, "error": err, "max_chi": st["max_chi"],
         "forward_discarded_weight": st["discarded_weight"],
@@ -642,7 +661,7 @@ def run_case(args):
         begin.append(begin[-1] + len(o))
     ops = np.concatenate(ops)
     sim = G.Simulator(args.case_n, args.case_d, chi_max=args.case_chi, cutoff=CUTOFF, batch=args.case_batch,
-                      cluster_size=args.cluster)
+                      cluster_size=args.cluster, precision=args.case_precision)
     for r in range(args.case_repeat):
         sim.reset()
         t0 = time.perf_counter()
@@ -653,7 +672,7 @@ def run_case(args):
         line = {"workload": "case", "rep": r, "seconds": el, "d": args.case_d, "n": args.case_n,
                 "layers": args.case_layers, "t_gates": args.case_t, "chi_max": args.case_chi,
                 "seed": args.case_seed, "batch": args.case_batch, "cluster": args.cluster,
-                "t_prefix": args.case_t_prefix,
+                "t_prefix": args.case_t_prefix, "precision": args.case_precision,
                 "stats": st[0] if args.case_batch == 1 else st,
                 "profile": [sim.profile(c) for c in range(args.case_batch)]}
         print(json.dumps(line), flush=True)
@@ -684,11 +703,12 @@ def weyl_probes(n: int):
 
 def run_precision(args):
     """The precision form against the FP64 form on the precision configuration: qutrits, n = 64, 40 brickwork
-    layers, 64 T gates, chi_max = 1024, cutoff 1e-12, seeds 1..S in one batch (one engine launch per step and
-    form).  value = T-gates/s of the precision form (device time, L2 flushed before every step); fp64 = the
-    same for the FP64 form.  Errors of the precision run against the FP64 run: |<W>| differences for the
-    probe strings (each form in its own Clifford frame), and, replaying the FP64 decisions, the fidelity
-    |<M|M'>|^2 (equal tableaux checked bit for bit)."""
+    layers, 64 T gates, chi_max = 1024, cutoff 1e-12, seeds 1..S, each circuit up to its --prec-prefix-th T
+    gate, one circuit at a time (a handle of this shape reserves about 37 GB).  Per seed and form: W warm-up and
+    K timed launches (device time, L2 flushed before each).  value = T-gates/s of the precision form over all
+    seeds; fp64 = the same for the FP64 form.  Errors of the precision run against the FP64 run: |<W>|
+    differences for the probe strings (each form in its own Clifford frame), and, replaying the FP64 decisions,
+    the fidelity |<M|M'>|^2 (equal tableaux checked bit for bit)."""
     import numpy as np
     import torch
     rank, world, local = dist_env()
@@ -698,116 +718,171 @@ def run_precision(args):
     import paper_2511_06672_gb300 as G
     from synth import brickwork_circuit
     seeds = [1 + s + rank * args.prec_seeds for s in range(args.prec_seeds)]
-    ops, begin = [], [0]
+    dev = f"cuda:{local}"
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    probes = weyl_probes(PREC_N)
+    acc = {0: {"t": 0.0, "tg": 0, "max_chi": 0, "visits": 0, "exact": 0, "tensor_flops": 0.0},
+           1: {"t": 0.0, "tg": 0, "max_chi": 0, "visits": 0, "exact": 0, "tensor_flops": 0.0}}
+    werr, fid_err, same_dec, e2e_t, e2e_tg, per_seed = 0.0, 0.0, 0, 0.0, 0, []
+    clocks = ClockSampler(local)
+    clocks.start()
     for sd in seeds:
         o = G.ops_from_gates(brickwork_circuit(PREC_N, 3, PREC_LAYERS, PREC_T, sd), 3)
-        ops.append(o)
-        begin.append(begin[-1] + len(o))
-    ops = np.concatenate(ops)
-    begin = np.array(begin, dtype=np.int32)
-    dev = f"cuda:{local}"
-    ops_dev = torch.from_numpy(ops.view(np.uint8)).to(dev)
-    begin_dev = torch.from_numpy(begin).to(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    S = len(seeds)
-    lines = {}
-    sims = {}
-    for prec in (0, 1):
-        stream = torch.cuda.Stream()
-        sim = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, batch=S, stream=stream, cluster_size=16,
-                          precision=prec)
-        sims[prec] = sim
-        for _ in range(args.warmup):
-            sim.reset()
-            sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
-        sim.sync()
-        times = []
-        clocks = ClockSampler(local)
-        clocks.start()
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.reset()
-            sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-        clk = clocks.stop()
-        st = [sim.stats(c) for c in range(S)]
-        if any(x["status"] for x in st):
-            raise RuntimeError(f"device status {[x['status'] for x in st]}")
-        tg = sum(x["t_gates"] for x in st)
-        lines[prec] = {"value": tg * args.steps / sum(times), "ms_per_step": 1e3 * sum(times) / args.steps,
-                       "max_chi": max(x["max_chi"] for x in st), "bond_visits": sum(x["bonds_visited"] for x in st),
-                       "exact_evaluations": sum(x["vn_evaluations"] for x in st),
-                       "tensor_flops_per_step": sum(x["tensor_flops"] for x in st), "clocks": clk,
-                       "launch_s": sum(times) / args.steps}
-    # errors of the precision run against the FP64 run
-    probes = weyl_probes(PREC_N)
-    werr = 0.0
-    same_dec = 0
-    for c in range(S):
+        ends = np.nonzero(o["kind"] == G.OP_DISENTANGLE)[0]
+        if 0 < args.prec_prefix < len(ends):   # the circuit up to the disentangling after its prefix-th T gate
+            o = o[: ends[args.prec_prefix - 1] + 1]
+        tg = int(np.sum(o["kind"] == G.OP_NONCLIFFORD))
+        ops_dev = torch.from_numpy(o.view(np.uint8)).to(dev)
+        begin_dev = torch.tensor([0, len(o)], dtype=torch.int32, device=dev)
+        sims, secs = {}, {}
+        for prec in (0, 1):
+            stream = torch.cuda.Stream()
+            sim = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, stream=stream, cluster_size=16,
+                              precision=prec)
+            for _ in range(args.warmup):
+                sim.reset()
+                sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
+            sim.sync()
+            times = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.reset()
+                sim.run_device(ops_dev.data_ptr(), begin_dev.data_ptr())
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            st = sim.stats()
+            if st["status"]:
+                raise RuntimeError(f"device status {st['status']} (seed {sd}, precision {prec})")
+            a = acc[prec]
+            a["t"] += sum(times)
+            a["tg"] += tg * args.steps
+            a["max_chi"] = max(a["max_chi"], st["max_chi"])
+            a["visits"] += st["bonds_visited"]
+            a["exact"] += st["vn_evaluations"]
+            a["tensor_flops"] += st["tensor_flops"] * args.steps
+            sims[prec], secs[prec] = sim, sum(times) / args.steps
         for x, z in probes:
-            werr = max(werr, abs(sims[1].expect_weyl(x, z, c) - sims[0].expect_weyl(x, z, c)))
-        same_dec += sims[1].decisions(c) == sims[0].decisions(c)
-    rep = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, batch=S, cluster_size=16, precision=1)
-    for c in range(S):
-        rep.set_replay(sims[0].decisions(c), c)
-    rep.run(ops, begin)
-    rep.sync()
-    fid_err = 0.0
-    for c in range(S):
-        ea, pa = sims[0].tableau(c)
-        eb, pb = rep.tableau(c)
-        if not (np.array_equal(ea, eb) and np.array_equal(pa, pb)):
-            raise RuntimeError("replayed tableau differs")
-        fid_err = max(fid_err, 1.0 - abs(sims[0].overlap(rep, c, c)) ** 2)
-    rep.close()
-    # e2e of the precision form through the C ABI: host gate list copied in, bond dimensions read back
-    e2e_t = []
-    for _ in range(max(2, args.steps)):
+            werr = max(werr, abs(sims[1].expect_weyl(x, z) - sims[0].expect_weyl(x, z)))
+        dec0 = sims[0].decisions()
+        same_dec += sims[1].decisions() == dec0
+        # e2e of the precision form through the C ABI: host gate list copied in, bond dimensions read back
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sims[1].reset()
-        sims[1].run(ops, begin)
-        dims = [sims[1].bond_dims(c) for c in range(S)]
-        e2e_t.append(time.perf_counter() - t0)
-    tg = PREC_T * S
+        sims[1].run(o)
+        dims = sims[1].bond_dims()
+        e2e_t += time.perf_counter() - t0
+        e2e_tg += tg
+        sims[1].close()
+        rep = G.Simulator(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF, cluster_size=16, precision=1)
+        rep.set_replay(dec0)
+        rep.run(o)
+        rep.sync()
+        ea, pa = sims[0].tableau()
+        eb, pb = rep.tableau()
+        if not (np.array_equal(ea, eb) and np.array_equal(pa, pb)):
+            raise RuntimeError("replayed tableau differs")
+        fid_err = max(fid_err, 1.0 - abs(sims[0].overlap(rep)) ** 2)
+        rep.close()
+        sims[0].close()
+        per_seed.append({"seed": sd, "t_gates": tg, "fp64_s": round(secs[0], 4), "precision_s": round(secs[1], 4)})
+        progress(f"precision workload seed {sd}: fp64 {secs[0]:.3f} s, precision {secs[1]:.3f} s")
+    clk = clocks.stop()
+    v = {p: acc[p]["tg"] / acc[p]["t"] for p in (0, 1)}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             bf16 = float(json.load(fh)["bf16_tflops"])
         tf32_peak, tf32_src = bf16 * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16 ratio (1.1/2.25)"
     except (OSError, ValueError, KeyError):
         tf32_peak, tf32_src = 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16 ratio"
-    tc_ach = lines[1]["tensor_flops_per_step"] / lines[1]["launch_s"] / 1e12
+    tc_ach = acc[1]["tensor_flops"] / acc[1]["t"] / 1e12
+    summary = lambda p: {"value": v[p], "seconds": acc[p]["t"], "max_chi": acc[p]["max_chi"],  # noqa: E731
+                         "bond_visits": acc[p]["visits"], "exact_evaluations": acc[p]["exact"],
+                         "tensor_flops_per_step": acc[p]["tensor_flops"] / args.steps}
     line = {
-        "metric": "T-gates/s (precision form)", "value": lines[1]["value"], "unit": "T-gates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": lines[1]["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 contractions (tf32x3 tensor cores), f64 eigen/SVD/score",
-        "data": "synthetic",
+        "metric": "T-gates/s (precision form)", "value": v[1], "unit": "T-gates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * acc[1]["t"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 contractions (tf32x3 tensor cores), f64 eigen/SVD/score", "data": "synthetic",
         "config": {"workload": PREC_WORKLOAD, "n": PREC_N, "layers": PREC_LAYERS, "t_gates": PREC_T,
                    "chi_max": PREC_CHI, "cutoff": CUTOFF, "d": 3, "seeds": seeds,
-                   "l2": "512 MiB flush before every timed step"},
-        "fp64": {k: v for k, v in lines[0].items() if k != "launch_s"},
-        "precision": {k: v for k, v in lines[1].items() if k != "launch_s"},
-        "speedup_vs_fp64": lines[1]["value"] / lines[0]["value"],
+                   "t_gate_prefix": args.prec_prefix if args.prec_prefix > 0 else PREC_T,
+                   "l2": "512 MiB flush before every timed launch", "step": "one launch per seed, in turn"},
+        "fp64": summary(0), "precision": summary(1), "speedup_vs_fp64": v[1] / v[0], "per_seed": per_seed,
         "errors_vs_fp64": {"max_abs_weyl_expectation": werr, "probes_per_circuit": len(probes),
                            "replay_fidelity_error": fid_err, "circuits_with_identical_decisions": same_dec},
         "roofline": {"bound": "tensor", "achieved": tc_ach, "peak": tf32_peak, "unit": "TFLOP/s",
                      "frac": tc_ach / tf32_peak, "traffic": None, "peak_source": tf32_src,
                      "kernel": "k_run_tc (tensor-core Grams of CTA-level class evaluations)"},
-        "e2e": {"value": tg * len(e2e_t) / sum(e2e_t), "unit": "T-gates/s", "h2d_bytes_per_step": ops.nbytes + begin.nbytes,
-                "d2h_bytes_per_step": sum(len(x) * 4 for x in dims)},
-        "gpu_launches": 2 * args.steps,
-        "clocks": lines[1]["clocks"],
+        "e2e": {"value": e2e_tg / e2e_t, "unit": "T-gates/s", "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": 4 * (PREC_N - 1), "note": "one C-ABI run per seed, gate list from host"},
+        "gpu_launches": 2 * len(seeds) * args.steps,
+        "clocks": clk,
     }
-    for sim in sims.values():
-        sim.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", RANK="0", WORLD_SIZE="1")
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                            "precision", "--ref-budget-s", "20", "--prec-seeds", str(args.prec_seeds), "--prec-prefix",
+                            str(args.prec_prefix), "--steps", "1", "--warmup", "0"], env=env, capture_output=True,
+                           text=True, timeout=900)
+        ref = json.loads(r.stdout.strip().splitlines()[-1])
+        line["cpu_baseline"] = {k: ref["cpu_baseline"][k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def precision_oracle_sample(seeds, prefix, budget_s=None):
+    """The FP64 oracle (one thread) on the precision workload's circuits, each up to its prefix-th T gate, seeds in
+    order (those that start within budget_s seconds).  Returns (T gates / s, seconds, seeds run)."""
+    from synth import brickwork_circuit
+    from oracle.gcamps import GCAMPS
+    t0 = time.perf_counter()
+    tg, done = 0, []
+    for sd in seeds:
+        if budget_s is not None and done and time.perf_counter() - t0 > budget_s:
+            break
+        g = GCAMPS(PREC_N, 3, chi_max=PREC_CHI, cutoff=CUTOFF)
+        k = 0
+        for gt in brickwork_circuit(PREC_N, 3, PREC_LAYERS, PREC_T, sd):
+            g.apply_gate(gt)
+            if not hasattr(gt, "sp_index"):
+                g.disentangle()
+                k += 1
+                if 0 < prefix <= k:
+                    break
+        tg += k
+        done.append(sd)
+    el = time.perf_counter() - t0
+    return tg / el, el, done
+
+
+def run_precision_reference(args):
+    """--impl reference --workload precision: the oracle on the precision workload (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    seeds = [1 + s for s in range(args.prec_seeds)]
+    rate, el, done = precision_oracle_sample(seeds, args.prec_prefix, args.ref_budget_s)
+    line = {
+        "impl": "reference", "metric": "T-gates/s (precision form)", "value": rate, "unit": "T-gates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": PREC_WORKLOAD, "n": PREC_N, "layers": PREC_LAYERS, "t_gates": PREC_T,
+                   "chi_max": PREC_CHI, "cutoff": CUTOFF, "d": 3, "seeds": seeds,
+                   "t_gate_prefix": args.prec_prefix if args.prec_prefix > 0 else PREC_T,
+                   "l2": "512 MiB flush before every timed launch", "step": "one launch per seed, in turn"},
+        "cpu_baseline": {"value": rate, "unit": "T-gates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"seeds {done} up to T gate {args.prec_prefix} ({el:.1f} s, 1 thread)"},
+        "e2e": {"value": rate, "unit": "T-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -852,7 +927,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcamps", choices=["gcamps", "reference"])
-    ap.add_argument("--prec-seeds", type=int, default=4, help="precision workload: circuits per rank")
+    ap.add_argument("--prec-seeds", type=int, default=8, help="precision workload: circuits per rank")
+    ap.add_argument("--grad-prefix", type=int, default=0,
+                    help="gradient workload: parametrised gates run (0: all 48)")
+    ap.add_argument("--prec-prefix", type=int, default=48,
+                    help="precision workload: T gates run per circuit (0: all 64; past about 48 T gates most seeds "
+                         "reach 243 x 243 two-site tensors, where one T gate takes tens of seconds in FP64)")
     ap.add_argument("--workload", default="bench",
                     choices=["bench", "batched", "gradient", "chi-layers", "case", "precision"],
                     help="bench: the 16-circuit n=32 workload; batched: uneven qutrit circuits in one launch; "
@@ -867,6 +947,7 @@ def main():
     ap.add_argument("--case-batch", type=int, default=1)
     ap.add_argument("--case-repeat", type=int, default=2)
     ap.add_argument("--case-t-prefix", type=int, default=0, help="run only up to the K-th T gate (0: all)")
+    ap.add_argument("--case-precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 precision form")
     ap.add_argument("--chi-layers-d", default="2,3")
     ap.add_argument("--chi-layers-n", default="6,8")
     ap.add_argument("--chi-layers-factor", type=int, default=2, help="layers = this x n")
@@ -889,6 +970,8 @@ def main():
             return run_chi_layers_reference(args)
         if args.workload == "batched":
             return run_batched_reference(args)
+        if args.workload == "precision":
+            return run_precision_reference(args)
         if args.workload == "gradient":
             if dist_env()[0] == 0:
                 print(json.dumps({"impl": "reference", "unavailable": "the oracle's gradient is a dense "

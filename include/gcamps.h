@@ -82,8 +82,9 @@ typedef struct {
   int64_t candidates_scored;  /* (bond, class) entanglement scores evaluated                */
   int64_t accepted;           /* disentanglers applied                                      */
   int64_t sweeps;             /* disentangling sweeps                                       */
-  int64_t vn_evaluations;     /* exact von Neumann entropies computed (the others were      */
-                              /* excluded by the Renyi-2 lower bound S2 <= S_vN)            */
+  int64_t vn_evaluations;     /* exact (FP64) von Neumann entropies computed; the other     */
+                              /* classes were excluded by the Renyi-2 lower bound S2 <= S_vN */
+                              /* or by their FP32 estimate's error bound                    */
   int64_t svd_calls;          /* truncating SVDs (one-sided Jacobi)                         */
   int64_t jacobi_sweeps;      /* Jacobi sweeps over all SVDs                                */
   int64_t jacobi_max_sweeps;  /* most sweeps one SVD needed                                 */

@@ -2182,7 +2182,7 @@ __device__ void gram_fp32<BlockGroup>(const BlockGroup& g, const Ctx& C, const f
 // kS2Exact: S2 in FP64 only (class 0 still gets kExact: its eigenvalues certify QR moves).
 // kEstimate: the FP32 von Neumann estimate and its bound (lead->vest, lead->vbd; CTA-level sizes only).
 enum ScoreMode { kExact = 0, kScreen = 1, kS2Exact = 2, kEstimate = 3 };
-__device__ __noinline__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
+__device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* theta, int cl, int cr,
                               const int* list, int cnt, int mode) {
   const Engine& e = *C.e;
   const int d = C.d, dd = d * d;
@@ -2291,7 +2291,7 @@ __device__ __noinline__ void score_classes(Smem& s, Smem* lead, const Ctx& C, co
 // leader's s.vn / s.evald hold the evaluated entropies and *nev their count.
 // The decision over the exactly evaluated classes of the leader's shared memory (select_class), and the
 // record of the visit's scores; -1 on the other CTAs.
-__device__ __noinline__ int decide_class(Smem& s, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out, long long& tp) {
+__device__ int decide_class(Smem& s, const Ctx& C, const double2* theta, int cl, int cr, int* nev_out, long long& tp) {
   const Engine& e = *C.e;
   const bool leader = C.rank == 0;
   const int d = C.d, kind = e.score_kind;

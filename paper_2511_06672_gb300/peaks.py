@@ -1,6 +1,7 @@
 """Measured arithmetic peaks of this GPU for the engine's roofline (gcamps_measure_peaks).
 
-    python -m paper_2511_06672_gb300.peaks            # prints them and writes profiles/arith_peaks_gb300.json
+    python -m paper_2511_06672_gb300.peaks [out.json]   # prints them and writes out.json
+                                                        # (default profiles/arith_peaks_gb300.json)
 
 FP64 and FP32 fused multiply-add rates and the FP64 tensor-core (m8n8k4) rate, from CUDA-event timings of
 long multiply-add chains, with the SM clocks sampled while they run.  bench.py divides the engine's FP64
@@ -12,6 +13,7 @@ import ctypes as C
 import json
 import os
 import subprocess
+import sys
 import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -70,8 +72,9 @@ def main():
                   "2 flops per multiply-add; second of two launches timed")
     res["when"] = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
     print(json.dumps(res))
-    os.makedirs(os.path.dirname(PEAKS_FILE), exist_ok=True)
-    with open(PEAKS_FILE, "w") as fh:
+    path = sys.argv[1] if len(sys.argv) > 1 else PEAKS_FILE
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "w") as fh:
         json.dump(res, fh, indent=1)
         fh.write("\n")
 
