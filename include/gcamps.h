@@ -96,6 +96,9 @@ typedef struct {
   double screen_flops;        /* algorithmic FP32 flops of the Renyi-2 screen (see below)   */
   double tensor_flops;        /* algorithmic flops of the Grams run on the tensor cores     */
                               /* (precision form: 8 m^2 K per m x m Gram of K columns)      */
+  double algorithmic_flops;   /* the exhaustive search's flops: every class of every visit  */
+                              /* with m > 1 scored exactly (the per-class FP64 count below), */
+                              /* whether or not the bounds excluded it                      */
 } gcamps_stats;
 /* Per class at a bond with R = chi_l d rows and C = d chi_r columns (m = min(R, C),
  * M = max(R, C)): scoring_flops adds 8 d^2 R C (Q theta) + 4 m (m + 1) M (Hermitian Gram) +
@@ -314,7 +317,8 @@ int gcamps_overlap(gcamps_t* h1, int circuit1, gcamps_t* h2, int circuit2, doubl
  *   [9] truncated SVD splits               [10] QR centre moves after a visit that applies nothing
  *   [12 + b] bond visits, [17 + b] their cycles, [22 + b] their exact evaluations, [27 + b] their FP32
  *   von Neumann estimates, for the visit size buckets b = 0..4 of m = min(chi_l d, d chi_r): m <= 9, <= 27,
- *   <= 54, <= 81, larger.  Words 11 and 31 are zero. */
+ *   <= 54, <= 81, larger; [11] cycles and [31] count of the warp-level exact evaluations run by the leader
+ *   CTA's first warp (the duration of one evaluation, free of the cluster's waits). */
 #define GCAMPS_PROF_WORDS 32
 int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count);
 /* Scores (Sec. 3) of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:

@@ -337,7 +337,8 @@ class Simulator:
         cnt = C.c_int32()
         self._c(self._lib.gcamps_get_profile(self._h, circuit, p.ctypes.data_as(C.POINTER(C.c_int64)), N.PROF_WORDS,
                                              C.byref(cnt)))
-        out = {"cycles": {k: int(p[i]) for i, k in enumerate(N.PROF_PHASES)}, "buckets": {}}
+        out = {"cycles": {k: int(p[i]) for i, k in enumerate(N.PROF_PHASES)}, "buckets": {},
+               "leader_warp_exact": {"cycles": int(p[11]), "count": int(p[31])}}
         for b, name in enumerate(N.PROF_BUCKETS):
             out["buckets"][name] = {"visits": int(p[12 + b]), "cycles": int(p[17 + b]), "exact": int(p[22 + b]),
                                     "estimates": int(p[27 + b])}

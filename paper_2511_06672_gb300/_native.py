@@ -35,7 +35,8 @@ class Stats(C.Structure):
                 ("vn_evaluations", C.c_int64), ("svd_calls", C.c_int64), ("jacobi_sweeps", C.c_int64),
                 ("jacobi_max_sweeps", C.c_int64), ("qr_calls", C.c_int64),
                 ("max_chi", C.c_int32), ("status", C.c_int32), ("discarded_weight", C.c_double),
-                ("scoring_flops", C.c_double), ("screen_flops", C.c_double), ("tensor_flops", C.c_double)]
+                ("scoring_flops", C.c_double), ("screen_flops", C.c_double), ("tensor_flops", C.c_double),
+                ("algorithmic_flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -203,7 +203,7 @@ __device__ Ctx make_ctx(const Engine& e, int c, int rank = 0) {
   C.meta = e.meta + (long long)c * M_COUNT;
   C.stats = e.stats + (long long)c * S_COUNT;
   C.prof = e.prof ? e.prof + (long long)c * P_COUNT : nullptr;
-  C.dstats = e.dstats + (long long)c * 4;
+  C.dstats = e.dstats + (long long)c * kDStats;
   C.dec = e.dec + (long long)c * kDecCap * 2;
   C.weyl = e.weyl + (long long)c * 2 * e.n;
   C.scr = e.scr + (long long)c * e.sl.total;
@@ -1287,6 +1287,37 @@ __device__ __forceinline__ long long order_key(double v) {
   return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
 }
 
+// The smallest value of v over the warp, compared through order_key (integer work only).
+__device__ __forceinline__ double warp_min_double(double v) {
+  long long k = order_key(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long o2 = __shfl_xor_sync(0xffffffffu, k, o);
+    k = o2 < k ? o2 : k;
+  }
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ int warp_min_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Called by one whole warp: appends to list[start..] every k in [k0, K) with flag(k), in increasing k;
+// returns the new length (the same on every lane).
+template <class F>
+__device__ __forceinline__ int warp_list(int* list, int start, int K, int k0, F flag) {
+  const int lane = threadIdx.x & 31;
+  int cnt = start;
+  for (int base = k0; base < K; base += 32) {
+    const int k = base + lane;
+    const bool f = k < K && flag(k);
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    if (f) list[cnt + __popc(b & ((1u << lane) - 1u))] = k;
+    cnt += __popc(b);
+  }
+  return cnt;
+}
+
 // Number of eigenvalues below x of the symmetric tridiagonal (dg, e2 = off-diagonal squared): the
 // number of sign changes along the leading principal minors f_0 = 1, f_1, ..., f_m of T - x I,
 // f_{i+1} = (d_i - x) f_i - e2_{i-1} f_{i-1} (Sturm sequence; a sign change is a negative LDL^T pivot
@@ -1696,13 +1727,14 @@ __device__ void s2_fp32(const Grp& g, const Ctx& C, const float2* th, int cl, in
 // |S^ - S| <= T ln(m - 1) + H2(T).  The bound used is twice that with ln m (room for the rounding of S^
 // itself); 1e300 (no information) when T >= 1/2.
 __device__ double vn_est_bound(int d, int m, int M) {
-  const double u = 5.960464477539063e-08;
-  const double e1 = d * (d * d + 6) * u;
-  const double eta = 2.0 * e1 + e1 * e1 + (2.0 * M + 4.0) * u * (1.0 + e1) * (1.0 + e1);
-  const double T = sqrt((double)m) * (eta + u + 2.0 * (double)m * (double)m * u * (1.0 + eta)) + 9.0 * m * u;
-  if (!(T < 0.5)) return 1e300;
-  const double h2 = T > 0.0 ? -T * log(T) - (1.0 - T) * log1p(-T) : 0.0;
-  return 2.0 * (T * log((double)(m > 1 ? m : 2)) + h2);
+  // evaluated in FP32 (off the narrow FP64 pipe) and rounded up by 0.1 %, far more than its rounding error
+  const float u = 5.9604645e-08f;
+  const float e1 = d * (d * d + 6) * u;
+  const float eta = 2.f * e1 + e1 * e1 + (2.f * M + 4.f) * u * (1.f + e1) * (1.f + e1);
+  const float T = (sqrtf((float)m) * (eta + u + 2.f * (float)m * (float)m * u * (1.f + eta)) + 9.f * m * u) * 1.001f;
+  if (!(T < 0.5f)) return 1e300;
+  const float h2 = T > 0.f ? -T * logf(T) - (1.f - T) * log1pf(-T) : 0.f;
+  return (double)(2.f * (T * logf((float)(m > 1 ? m : 2)) + h2) * 1.001f);
 }
 
 __device__ __forceinline__ float fabs2f(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
@@ -2221,9 +2253,14 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
         continue;
       }
       const bool want_vn = mode == kExact || k == 0;
+      const long long t0 = (C.prof && C.rank == 0 && warp == 0 && lane == 0) ? clock64() : 0;
       const Score sc = score_class(g, C, theta, cl, cr, e.candU + (long long)k * dd * dd,
                                    e.candU32 + (long long)k * dd * dd, ws, kSmall, want_vn, s.wtri[warp],
                                    s.wtri32[warp], 32);
+      if (C.prof && C.rank == 0 && warp == 0 && lane == 0 && want_vn) {   // the leader's own exact evaluations
+        C.prof[P_LEAD_EXACT_CYC] += clock64() - t0;
+        C.prof[P_LEAD_EXACT_N] += 1;
+      }
       if (lane == 0) {
         lead->s2[k] = sc.s2;
         lead->evald[k] = 1;
@@ -2297,30 +2334,39 @@ __device__ int decide_class(Smem& s, const Ctx& C, const double2* theta, int cl,
   const int d = C.d, kind = e.score_kind;
   const int rows = cl * d, cols = d * cr;
   if (!leader) return -1;
-  if (threadIdx.x == 0) {
-    // the decision over the exactly evaluated classes: key = S_vN (kind 0), S2 (kind 1), or the
-    // weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
+  if (threadIdx.x < 32) {
+    // the decision over the exactly evaluated classes, on the first warp: key = S_vN (kind 0), S2 (kind 1),
+    // or the weight rank first and S_vN second (kind 2); ties within tie_tol go to the lowest index, and a
     // class is applied only if it beats the identity
+    const int lane = threadIdx.x;
     int nev = 0, rmin = 1 << 30;
-    for (int k = 0; k < C.K; ++k)
+    for (int k = lane; k < C.K; k += 32)
       if (s.evald[k]) {
         ++nev;
-        if (s.rk[k] < rmin) rmin = s.rk[k];
+        rmin = min(rmin, s.rk[k]);
       }
+    nev = warp_sum_int(nev);
+    rmin = warp_min_int(rmin);
     auto key = [&](int k) { return kind == 1 ? s.s2[k] : s.vn[k]; };
-    double best = 1e300;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin)) best = fmin(best, key(k));
+    auto in = [&](int k) { return s.evald[k] && (kind != 2 || s.rk[k] == rmin); };
+    double b = 1e300;
+    for (int k = lane; k < C.K; k += 32)
+      if (in(k)) b = fmin(b, key(k));
+    const double best = warp_min_double(b) + e.tie_tol;
     int kb = 0;
-    for (int k = 0; k < C.K; ++k)
-      if (s.evald[k] && (kind != 2 || s.rk[k] == rmin) && key(k) <= best + e.tie_tol) {
-        kb = k;
+    for (int base = 0; base < C.K; base += 32) {
+      const int k = base + lane;
+      const unsigned hit = __ballot_sync(0xffffffffu, k < C.K && in(k) && key(k) <= best);
+      if (hit) {
+        kb = base + __ffs(hit) - 1;
         break;
       }
-    const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
-    if (!better) kb = 0;
-    s.ival[4] = kb;
-    s.ival[5] = nev;
+    }
+    if (lane == 0) {
+      const bool better = (kind == 2 && s.rk[kb] < s.rk[0]) || key(kb) < key(0) - e.tie_tol;
+      s.ival[4] = better ? kb : 0;
+      s.ival[5] = nev;
+    }
   }
   {
     double* out = e.lastsc + (long long)C.c * (3 * kMaxK + 2 + 2 * kSmall);
@@ -2377,18 +2423,19 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
     score_classes(s, lead, C, theta, cl, cr, nullptr, C.K, kEstimate);
     cluster_sync();
     prof_lap(C, P_EST, tp);
-    if (leader && threadIdx.x == 0) {
-      double U = 1e300;
-      for (int k = 0; k < C.K; ++k) {
+    if (leader && threadIdx.x < 32) {   // the leader's first warp builds the exact list
+      double u = 1e300;
+      for (int k = threadIdx.x; k < C.K; k += 32) {
         s.evald[k] = 0;
-        U = fmin(U, s.vest[k] + s.vbd[k]);
+        u = fmin(u, s.vest[k] + s.vbd[k]);
       }
-      int cnt = 1;
-      s.list[0] = 0;
-      for (int k = 1; k < C.K; ++k)
-        if (s.vest[k] - s.vbd[k] <= U + e.tie_tol + 1e-12) s.list[cnt++] = k;
-      s.nlist = cnt;
-      s.ival[6] = C.K;
+      const double U = warp_min_double(u) + e.tie_tol + 1e-12;
+      if (threadIdx.x == 0) s.list[0] = 0;
+      const int cnt = warp_list(s.list, 1, C.K, 1, [&](int k) { return s.vest[k] - s.vbd[k] <= U; });
+      if (threadIdx.x == 0) {
+        s.nlist = cnt;
+        s.ival[6] = C.K;
+      }
     }
     cluster_sync();
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
@@ -2432,44 +2479,43 @@ __device__ int select_class(Smem& s, Smem* lead, const Ctx& C, const double2* th
         s.ord[k] = r;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        int cnt = 1;
-        s.list[0] = 0;
-        for (int k = 1; k < C.K; ++k)
-          if (s.ord[k] < L) s.list[cnt++] = k;
-        s.nlist = cnt;
+      if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) s.list[0] = 0;
+        const int cnt = warp_list(s.list, 1, C.K, 1, [&](int k) { return s.ord[k] < L; });
+        if (threadIdx.x == 0) s.nlist = cnt;
       }
     }
     cluster_sync();
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kEstimate);
     cluster_sync();
-    if (leader && threadIdx.x == 0) {
-      double U = 1e300;
-      for (int k = 0; k < C.K; ++k)
-        if (s.estd[k]) U = fmin(U, s.vest[k] + s.vbd[k]);
-      int cnt = 0;
-      for (int k = 0; k < C.K; ++k)
-        if (!s.estd[k] && s.s2lo[k] <= U + e.tie_tol + 1e-12) s.list[cnt++] = k;
-      s.nlist = cnt;
+    if (leader && threadIdx.x < 32) {
+      double u = 1e300;
+      for (int k = threadIdx.x; k < C.K; k += 32)
+        if (s.estd[k]) u = fmin(u, s.vest[k] + s.vbd[k]);
+      const double U = warp_min_double(u) + e.tie_tol + 1e-12;
+      const int cnt = warp_list(s.list, 0, C.K, 0, [&](int k) { return !s.estd[k] && s.s2lo[k] <= U; });
+      if (threadIdx.x == 0) s.nlist = cnt;
     }
     cluster_sync();
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kEstimate);
     cluster_sync();
     prof_lap(C, P_EST, tp);
-    if (leader && threadIdx.x == 0) {
-      double U = 1e300;
+    if (leader && threadIdx.x < 32) {
+      double u = 1e300;
       int nest = 0;
-      for (int k = 0; k < C.K; ++k)
+      for (int k = threadIdx.x; k < C.K; k += 32)
         if (s.estd[k]) {
-          U = fmin(U, s.vest[k] + s.vbd[k]);
+          u = fmin(u, s.vest[k] + s.vbd[k]);
           ++nest;
         }
-      int cnt = 1;
-      s.list[0] = 0;
-      for (int k = 1; k < C.K; ++k)
-        if (s.estd[k] && s.vest[k] - s.vbd[k] <= U + e.tie_tol + 1e-12) s.list[cnt++] = k;
-      s.nlist = cnt;
-      s.ival[6] = nest;
+      const double U = warp_min_double(u) + e.tie_tol + 1e-12;
+      nest = warp_sum_int(nest);
+      if (threadIdx.x == 0) s.list[0] = 0;
+      const int cnt = warp_list(s.list, 1, C.K, 1, [&](int k) { return s.estd[k] && s.vest[k] - s.vbd[k] <= U; });
+      if (threadIdx.x == 0) {
+        s.nlist = cnt;
+        s.ival[6] = nest;
+      }
     }
     cluster_sync();
     score_classes(s, lead, C, theta, cl, cr, lead->list, lead->nlist, kExact);
@@ -2619,6 +2665,7 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
       const double tri = (16.0 / 3.0) * mm * mm * mm;
       // exact evaluations, FP64 (Renyi-2 scores need no eigenvalues except the identity's)
       C.dstats[1] += e.score_kind == 1 ? nev * per_class + tri : nev * (per_class + tri);
+      if (m > kPruneMin) C.dstats[4] += C.K * (per_class + tri);   // every class scored exactly (the algorithm)
       if (m > kPruneMin) C.dstats[2] += C.K * per_class;                // FP32 screen of every class
     }
     const int nd = C.meta[M_NDEC];

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_reset(Engine e) {
   if (threadIdx.x < M_COUNT) C.meta[threadIdx.x] = 0;
   if (threadIdx.x < S_COUNT) C.stats[threadIdx.x] = (threadIdx.x == S_MAXCHI) ? 1 : 0;
   if (C.prof && threadIdx.x < P_COUNT) C.prof[threadIdx.x] = 0;
-  if (threadIdx.x < 4) C.dstats[threadIdx.x] = 0.0;
+  if (threadIdx.x < kDStats) C.dstats[threadIdx.x] = 0.0;
 }
 
 // ------------------------------------------------------------------------------ readouts

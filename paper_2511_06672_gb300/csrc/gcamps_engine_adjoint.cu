@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) k_adjoint(Engine e, int cf
   for (int j = 0; j < n; ++j) block_copy(site_ptr(B, j), site_ptr(F, j), (long long)F.dims[j] * d * F.dims[j + 1]);
   for (int j = threadIdx.x; j <= n; j += blockDim.x) B.dims[j] = F.dims[j];
   if (threadIdx.x < M_COUNT) B.meta[threadIdx.x] = 0;
-  if (threadIdx.x < 4) B.dstats[threadIdx.x] = 0.0;
+  if (threadIdx.x < kDStats) B.dstats[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x == 0) B.meta[M_OC] = F.meta[M_OC];
   conj_weyl(s, F, xz, ax, az, &ar);

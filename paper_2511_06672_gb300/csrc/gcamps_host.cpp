@@ -645,7 +645,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   const size_t o_prof = bytes;
   bytes = align(bytes + (size_t)nslots * gcx::P_COUNT * sizeof(long long));
   const size_t o_dstats = bytes;
-  bytes = align(bytes + (size_t)nslots * 4 * sizeof(double));
+  bytes = align(bytes + (size_t)nslots * gcx::kDStats * sizeof(double));
   const size_t o_dec = bytes;
   bytes = align(bytes + (size_t)nslots * gcx::kDecCap * 2 * sizeof(int));
   const size_t o_weyl = bytes;
@@ -990,7 +990,7 @@ int gcamps_expect_gradient(gcamps_t* h, int circuit, const int32_t* x, const int
   double wdisc = 0.0;
   GC_CUDA(h, cudaMemcpyAsync(wmeta, h->e.meta + (long long)ws * gcx::M_COUNT, sizeof wmeta, cudaMemcpyDeviceToHost,
                              h->stream));
-  GC_CUDA(h, cudaMemcpyAsync(&wdisc, h->e.dstats + (long long)ws * 4, sizeof(double), cudaMemcpyDeviceToHost,
+  GC_CUDA(h, cudaMemcpyAsync(&wdisc, h->e.dstats + (long long)ws * gcx::kDStats, sizeof(double), cudaMemcpyDeviceToHost,
                              h->stream));
   const int ncopy = std::min(K, (int)cap_gates);
   std::vector<double> g((size_t)std::max(ncopy, 1) * d);
@@ -1176,10 +1176,10 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   if (rc) return rc;
   if (!st) return fail(h, GCAMPS_EINVAL, "null output");
   long long s[gcx::S_COUNT];
-  double ds[4];
+  double ds[gcx::kDStats];
   int meta[gcx::M_COUNT];
   GC_CUDA(h, cudaMemcpyAsync(s, h->e.stats + (long long)circuit * gcx::S_COUNT, sizeof s, cudaMemcpyDeviceToHost, h->stream));
-  GC_CUDA(h, cudaMemcpyAsync(ds, h->e.dstats + (long long)circuit * 4, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
+  GC_CUDA(h, cudaMemcpyAsync(ds, h->e.dstats + (long long)circuit * gcx::kDStats, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
   GC_CUDA(h, cudaMemcpyAsync(meta, h->e.meta + (long long)circuit * gcx::M_COUNT, sizeof meta, cudaMemcpyDeviceToHost,
                              h->stream));
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1200,6 +1200,7 @@ int gcamps_get_stats(gcamps_t* h, int circuit, gcamps_stats* st) {
   st->scoring_flops = ds[1];
   st->screen_flops = ds[2];
   st->tensor_flops = ds[3];
+  st->algorithmic_flops = ds[4];
   return device_status(h);
 }
 

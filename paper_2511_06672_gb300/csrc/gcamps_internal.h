@@ -25,6 +25,7 @@ constexpr int kSmallStride = 2 * kSmall + 64;
 constexpr int kMaxN = 128;                // qudits per circuit
 constexpr int kMaxK = 90;                 // disentangler classes (d = 3)
 constexpr int kDecCap = 1 << 16;          // decisions recorded per circuit
+constexpr int kDStats = 8;                // doubles of counters per circuit (dstats)
 
 // meta[] words per circuit
 enum Meta { M_OC = 0, M_F, M_L, M_STATUS, M_NDEC, M_WEYL_R, M_HAVE_SPAN, M_DIAG_WHERE, M_DIAG_A, M_DIAG_B,
@@ -42,9 +43,11 @@ enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN,
             S_QR, S_COUNT };
 // prof[] counters per circuit (int64, the layout gcamps_get_profile documents): SM cycles of the leader CTA
 // per phase, then per bond-visit size bucket (m = min(chi_l d, d chi_r) <= 9, 27, 54, 81, larger) the
-// visits, their cycles, their exact (FP64) evaluations and their FP32 von Neumann estimates.
+// visits, their cycles, their exact (FP64) evaluations and their FP32 von Neumann estimates; and the cycles
+// and count of the warp-level exact evaluations run by the leader's first warp.
 enum Prof { P_CLIFF = 0, P_MPO, P_CENTER, P_THETA, P_SCREEN, P_EST, P_EXACT, P_DECIDE, P_APPLYQ, P_SPLIT,
-            P_QRMOVE, P_VISITS = 12, P_VCYC = 17, P_VEXACT = 22, P_VEST = 27, P_COUNT = 32 };
+            P_QRMOVE, P_LEAD_EXACT_CYC, P_VISITS = 12, P_VCYC = 17, P_VEXACT = 22, P_VEST = 27,
+            P_LEAD_EXACT_N = 31, P_COUNT = 32 };
 constexpr int kProfBuckets = 5;
 static_assert(P_COUNT == GCAMPS_PROF_WORDS, "profile layout stated in gcamps.h");
 
@@ -89,7 +92,8 @@ struct Engine {
   int* meta;                                // [batch][M_COUNT]
   long long* stats;                         // [batch][S_COUNT]
   long long* prof;                          // [batch][P_COUNT]
-  double* dstats;                           // [batch][4]: discarded weight, FP64 scoring flops, FP32 screen flops, spare
+  double* dstats;                           // [batch][kDStats]: discarded weight, FP64 scoring flops, FP32 screen flops,
+                                            // tensor-core Gram flops, algorithmic scoring flops
   int* dec;                                 // [batch][kDecCap][2]
   // replay (null when unused): circuit c with replay_n[c] > 0 applies the recorded (bond, class) pairs
   // replay[c][k] at its bond visits in order instead of choosing
