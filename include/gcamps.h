@@ -317,9 +317,11 @@ int gcamps_overlap(gcamps_t* h1, int circuit1, gcamps_t* h2, int circuit2, doubl
  *   [9] truncated SVD splits               [10] QR centre moves after a visit that applies nothing
  *   [12 + b] bond visits, [17 + b] their cycles, [22 + b] their exact evaluations, [27 + b] their FP32
  *   von Neumann estimates, for the visit size buckets b = 0..4 of m = min(chi_l d, d chi_r): m <= 9, <= 27,
- *   <= 54, <= 81, larger; [11] cycles and [31] count of the warp-level exact evaluations run by the leader
- *   CTA's first warp (the duration of one evaluation, free of the cluster's waits). */
-#define GCAMPS_PROF_WORDS 32
+ *   <= 54, <= 81, larger; [11] cycles and [32] count of the warp-level exact evaluations run by the leader
+ *   CTA's first warp (the duration of one evaluation, free of the cluster's waits); [33 + 11 b + p] the
+ *   cycles of phase p (0..10 as above) spent inside the visits of bucket b; [95] internal (0 between
+ *   launches). */
+#define GCAMPS_PROF_WORDS 96
 int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count);
 /* Scores (Sec. 3) of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
  * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact

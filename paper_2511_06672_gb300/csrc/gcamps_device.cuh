@@ -219,6 +219,8 @@ __device__ __forceinline__ void prof_lap(const Ctx& C, int slot, long long& t) {
   if (prof_thread(C)) {
     const long long now = clock64();
     C.prof[slot] += now - t;
+    const long long cb = C.prof[P_CURB];
+    if (cb > 0) C.prof[P_BPHASE + (cb - 1) * kProfPhases + slot] += now - t;
     t = now;
   }
 }
@@ -2607,6 +2609,10 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   double2* tmp = C.scr + e.sl.tmp;
   const long long tv = prof_start(C);
   long long tp = tv;
+  if (prof_thread(C)) {
+    const int ml = C.dims[i] * d, mr = d * C.dims[i + 2];
+    C.prof[P_CURB] = 1 + prof_bucket(ml < mr ? ml : mr);
+  }
   if (leader) {
     const int cl0 = C.dims[i], ch = C.dims[i + 1], cr0 = C.dims[i + 2];
     block_matmul(theta, site_ptr(C, i), site_ptr(C, i + 1), cl0 * d, ch, d * cr0);
@@ -2713,7 +2719,10 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
     note_chi(C, chim);
     __syncthreads();
     prof_lap(C, P_QRMOVE, tp);
-    if (prof_thread(C)) C.prof[P_VCYC + prof_bucket(m)] += clock64() - tv;
+    if (prof_thread(C)) {
+      C.prof[P_VCYC + prof_bucket(m)] += clock64() - tv;
+      C.prof[P_CURB] = 0;
+    }
     return;
   }
   Factor F;
@@ -2759,7 +2768,10 @@ __device__ void visit_bond(Smem& s, Smem* lead, const Ctx& C, int i, bool ltr, i
   note_chi(C, k);
   __syncthreads();
   prof_lap(C, P_SPLIT, tp);
-  if (prof_thread(C)) C.prof[P_VCYC + prof_bucket(m)] += clock64() - tv;
+  if (prof_thread(C)) {
+    C.prof[P_VCYC + prof_bucket(m)] += clock64() - tv;
+    C.prof[P_CURB] = 0;
+  }
 }
 
 // Alternating sweeps over the bonds of the last span; every CTA of the cluster runs the loop, only

@@ -43,12 +43,15 @@ enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN,
             S_QR, S_COUNT };
 // prof[] counters per circuit (int64, the layout gcamps_get_profile documents): SM cycles of the leader CTA
 // per phase, then per bond-visit size bucket (m = min(chi_l d, d chi_r) <= 9, 27, 54, 81, larger) the
-// visits, their cycles, their exact (FP64) evaluations and their FP32 von Neumann estimates; and the cycles
-// and count of the warp-level exact evaluations run by the leader's first warp.
+// visits, their cycles, their exact (FP64) evaluations and their FP32 von Neumann estimates; the cycles
+// and count of the warp-level exact evaluations run by the leader's first warp; the phase cycles of each
+// bucket's visits; and (P_CURB, internal) 1 + the bucket of the visit in progress, 0 outside visits.
 enum Prof { P_CLIFF = 0, P_MPO, P_CENTER, P_THETA, P_SCREEN, P_EST, P_EXACT, P_DECIDE, P_APPLYQ, P_SPLIT,
             P_QRMOVE, P_LEAD_EXACT_CYC, P_VISITS = 12, P_VCYC = 17, P_VEXACT = 22, P_VEST = 27,
-            P_LEAD_EXACT_N = 31, P_COUNT = 32 };
+            P_LEAD_EXACT_N = 32, P_BPHASE = 33, P_CURB = 95, P_COUNT = 96 };
+constexpr int kProfPhases = 11;
 constexpr int kProfBuckets = 5;
+static_assert(P_BPHASE + kProfBuckets * kProfPhases <= P_CURB, "bucket phase words fit");
 static_assert(P_COUNT == GCAMPS_PROF_WORDS, "profile layout stated in gcamps.h");
 
 // Scratch areas of one circuit, as element offsets (double2) from its scratch base.
