@@ -662,6 +662,8 @@ def run_case(args):
     ops = np.concatenate(ops)
     sim = G.Simulator(args.case_n, args.case_d, chi_max=args.case_chi, cutoff=CUTOFF, batch=args.case_batch,
                       cluster_size=args.cluster, precision=args.case_precision)
+    if args.exact_cta is not None:
+        sim.set_exact_cta(args.exact_cta)
     for r in range(args.case_repeat):
         sim.reset()
         t0 = time.perf_counter()
@@ -961,6 +963,8 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=None,
                     help="bench reference arm: only the circuits that start within this many seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--exact-cta", type=int, default=None,
+                    help="exact class evaluations of m <= 27 one per CTA from this m on (library default 10)")
     ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
     ap.add_argument("--cluster-qubit", type=int, default=4, help="CTAs per qubit circuit (0: --cluster)")
     ap.add_argument("--cluster-qutrit", type=int, default=16, help="CTAs per qutrit circuit (0: --cluster)")
@@ -1008,6 +1012,8 @@ def main():
     for d in (2, 3):
         sims[d] = G.Simulator(N, d, chi_max=CHI, cutoff=CUTOFF, batch=SEEDS_PER_D, stream=streams[d],
                               cluster_size=cluster[d])
+        if args.exact_cta is not None:
+            sims[d].set_exact_cta(args.exact_cta)
         o, b = workload_ops(G, d, rank)
         # e2e inputs live in pinned host memory
         o_pin = torch.from_numpy(o.view(np.uint8).copy()).pin_memory().numpy().view(G.OP_DTYPE)

@@ -202,6 +202,14 @@ int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
  * this library, settable so that the failure path can be exercised.  EINVAL outside 1..1000. */
 int gcamps_set_jacobi_cap(gcamps_t* h, int sweeps);
 
+/* Where the exact FP64 class evaluations of a bond visit with m = min(chi_l d, d chi_r) <= 27 run: on one
+ * warp each (many at once), or, when the visit's exact list has no more classes than the cluster has CTAs
+ * and m >= min_m, on one CTA each.  The choice changes the summation order only (the same class is chosen
+ * up to ties within rounding).  Default 10; 0 puts every such list on CTAs, a value above 27 keeps the
+ * warps.  No counterpart in the paper: a launch-shape setting of this library (Sec. 3's class scores are
+ * its subject).  Synchronises the handle's stream.  EINVAL if min_m < 0. */
+int gcamps_set_exact_cta(gcamps_t* h, int min_m);
+
 /* C <- G C for a one- or two-qudit Clifford G (Sec. 3, top loop of Fig. 3): the tableau rows
  * are conjugated (Table 1 generalised to any Clifford given by its images).  Applied to every
  * circuit of the handle. */

@@ -180,6 +180,10 @@ class Simulator:
     def set_cluster_size(self, cluster_size: int):
         self._c(self._lib.gcamps_set_cluster_size(self._h, cluster_size))
 
+    def set_exact_cta(self, min_m: int):
+        """Exact class evaluations at warp-level sizes one per CTA from m = min_m on (gcamps_set_exact_cta)."""
+        self._c(self._lib.gcamps_set_exact_cta(self._h, min_m))
+
     def set_jacobi_cap(self, sweeps: int):
         """Most sweeps of one Jacobi SVD before the engine reports GCAMPS_ENOCONV (default 60)."""
         self._c(self._lib.gcamps_set_jacobi_cap(self._h, sweeps))

@@ -44,16 +44,16 @@ class Stats(C.Structure):
 
 EXPORTS = [
     "gcamps_default_opts", "gcamps_num_candidates", "gcamps_sp4_images", "gcamps_candidate",
-    "gcamps_named_images", "gcamps_apply_named",
-    "gcamps_create",
-    "gcamps_create_batch", "gcamps_create_batch_uneven", "gcamps_batch_create",
-    "gcamps_batch_expect_weyl", "gcamps_batch_amplitude", "gcamps_batch_get_tableau", "gcamps_batch_get_bond_dims", "gcamps_destroy", "gcamps_num_qudits",
-    "gcamps_set_cluster_size", "gcamps_set_jacobi_cap", "gcamps_apply_clifford", "gcamps_apply_nonclifford",
-    "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
-    "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau", "gcamps_get_inverse_tableau",
-    "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site", "gcamps_get_last_weyl",
-    "gcamps_get_stats", "gcamps_get_profile", "gcamps_set_replay", "gcamps_overlap",
-    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta", "gcamps_estimate_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
+    "gcamps_named_images", "gcamps_apply_named", "gcamps_create", "gcamps_create_batch",
+    "gcamps_create_batch_uneven", "gcamps_batch_create", "gcamps_batch_expect_weyl", "gcamps_batch_amplitude",
+    "gcamps_batch_get_tableau", "gcamps_batch_get_bond_dims", "gcamps_destroy", "gcamps_num_qudits",
+    "gcamps_set_cluster_size", "gcamps_set_jacobi_cap", "gcamps_set_exact_cta", "gcamps_apply_clifford",
+    "gcamps_apply_nonclifford", "gcamps_disentangle", "gcamps_run", "gcamps_run_device", "gcamps_expect_weyl",
+    "gcamps_expect_gradient", "gcamps_statevector", "gcamps_amplitude", "gcamps_get_tableau",
+    "gcamps_get_inverse_tableau", "gcamps_get_bond_dims", "gcamps_get_schmidt", "gcamps_get_site",
+    "gcamps_get_last_weyl", "gcamps_get_stats", "gcamps_get_profile", "gcamps_set_replay", "gcamps_overlap",
+    "gcamps_get_decisions", "gcamps_get_last_scores", "gcamps_get_last_theta", "gcamps_score_theta",
+    "gcamps_estimate_theta", "gcamps_score_theta_noalloc", "gcamps_sync", "gcamps_reset", "gcamps_last_error",
     "gcamps_measure_peaks",
 ]
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
         "gcamps_num_qudits": (C.c_int, [vp, C.c_int]),
         "gcamps_set_cluster_size": (C.c_int, [vp, C.c_int]),
         "gcamps_set_jacobi_cap": (C.c_int, [vp, C.c_int]),
+        "gcamps_set_exact_cta": (C.c_int, [vp, C.c_int]),
         "gcamps_apply_clifford": (C.c_int, [vp, C.c_int, C.c_int, i32p]),
         "gcamps_apply_nonclifford": (C.c_int, [vp, C.c_int, dp]),
         "gcamps_disentangle": (C.c_int, [vp, C.POINTER(Stats)]),

@@ -1237,11 +1237,24 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
     if (g.tid == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
     g.sync();
     const double hinv = 1.0 / h;
-    for (int i = g.tid; i < r; i += g.n) {
+    // p = A v / h: kc lanes of one warp share a row (kc a power of two, kc r <= group size), each summing
+    // every kc-th column, then a shuffle tree; every thread runs the same passes, so the shuffles see
+    // full warps
+    int kc = 1;
+    while (kc < 32 && 2 * kc * r <= g.n && 2 * kc <= r) kc *= 2;
+    const int rows_in_flight = g.n / kc;
+    for (int base = 0; base < r; base += rows_in_flight) {
+      const int i = base + g.tid / kc, c = g.tid & (kc - 1);
       double2 acc = cz();
-      const double2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
-      for (int j = 0; j < r; ++j) acc = cfma(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
-      A[(long long)k * m + k + 1 + i] = cscale(acc, hinv);
+      if (i < r) {
+        const double2* arow = A + (long long)(k + 1 + i) * m + (k + 1);
+        for (int j = c; j < r; j += kc) acc = cfma(arow[j], A[(long long)(k + 1 + j) * m + k], acc);
+      }
+      for (int o = kc >> 1; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (i < r && c == 0) A[(long long)k * m + k + 1 + i] = cscale(acc, hinv);
     }
     g.sync();
     double kr = 0;
@@ -2222,7 +2235,10 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
   const int d = C.d, dd = d * d;
   const int rows = cl * d, cols = d * cr;
   const int m = rows < cols ? rows : cols;
-  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall;
+  // exact evaluations at warp-level sizes run one per CTA when the list has no more entries than the
+  // cluster has CTAs and m >= exact_cta_min_m: a CTA spreads one evaluation over its four FP64 pipes
+  const bool cta_exact = mode == kExact && cnt <= C.csize && m >= e.exact_cta_min_m;
+  const bool small = (long long)rows * cols <= kSmall && m * m <= kSmall && !cta_exact;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (small) {
     WarpGroup g{lane};

@@ -549,6 +549,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
   e.max_sweeps = opts.max_sweeps;
   e.score_kind = opts.score_kind;
   e.jacobi_cap = 60;
+  e.exact_cta_min_m = 10;
   e.precision = opts.precision;
   e.tc_smem = opts.precision ? gcx::kTcSmemBytes : 0;
   e.cutoff = opts.cutoff;
@@ -909,6 +910,14 @@ int gcamps_set_jacobi_cap(gcamps_t* h, int sweeps) {
   if (sweeps < 1 || sweeps > 1000) return fail(h, GCAMPS_EINVAL, "Jacobi sweep cap outside 1..1000");
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
   h->e.jacobi_cap = sweeps;
+  return GCAMPS_OK;
+}
+
+int gcamps_set_exact_cta(gcamps_t* h, int min_m) {
+  if (!h) return GCAMPS_EINVAL;
+  if (min_m < 0) return fail(h, GCAMPS_EINVAL, "negative size threshold");
+  GC_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->e.exact_cta_min_m = min_m;
   return GCAMPS_OK;
 }
 

@@ -78,6 +78,7 @@ struct Engine {
   int n, d, K, chi_max, batch, max_sweeps, maxdim, csize;   // n: largest qudit count of the batch
   int score_kind;                 // 0 von Neumann, 1 Renyi-2, 2 weight rank then von Neumann
   int jacobi_cap;                 // most sweeps of one Jacobi SVD before GCAMPS_ENOCONV (60)
+  int exact_cta_min_m;            // warp-level-size exact evaluations one per CTA from this m on (10)
   int precision;                  // 0 FP64 contractions; 1 FP32 contractions (tensor cores at CTA-level sizes)
   int tc_smem;                    // dynamic shared memory of the engine kernels (bytes; 0 without tensor cores)
   double cutoff, tie_tol, strict_weight;

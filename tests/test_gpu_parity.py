@@ -282,6 +282,30 @@ def test_cluster_sizes_give_identical_decisions(G, csize):
     assert st["vn_evaluations"] <= st["candidates_scored"]
 
 
+@pytest.mark.parametrize("min_m", [0, 100])
+def test_exact_evaluations_on_ctas_or_warps_give_oracle_decisions(G, min_m):
+    """Exact class evaluations at warp-level sizes (m <= 27) run one per CTA (min_m = 0: every short
+    exact list) or one per warp (min_m = 100): either way the decisions, bond dimensions and Schmidt values
+    are the oracle's (qutrits, n = 12, chi up to 27, 16-CTA clusters)."""
+    d, n = 3, 12
+    gates = brickwork_circuit(n, d, 12, 16, 31)
+    sim = G.Simulator(n, d, chi_max=64, cutoff=1e-12, max_sweeps=8, cluster_size=16)
+    sim.set_exact_cta(min_m)
+    sim.run(G.ops_from_gates(gates, d))
+    sim.sync()
+    ref = oracle_run(gates, n, d, 64, 1e-12)
+    assert sim.decisions() == ref.decisions
+    assert sim.bond_dims() == ref.mps.bond_dims()
+    for b in range(n - 1):
+        s = sim.schmidt_values(b)
+        s = s[s > 1e-13]
+        want = ref.mps.schmidt_values(b)
+        want = want[want > 1e-13]
+        assert len(s) == len(want) and np.max(np.abs(s - want)) < TOL
+    with pytest.raises(G.GcampsError):
+        sim.set_exact_cta(-1)
+
+
 def test_renyi2_pruning_is_exact_on_large_bonds(G):
     """Bonds with Gram size > 9 use the Renyi-2 bound: decisions still equal the oracle's, which
     scores every class by SVD."""
