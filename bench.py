@@ -963,6 +963,7 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=None,
                     help="bench reference arm: only the circuits that start within this many seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sm-ids", action="store_true", help="print the SM each CTA of each circuit ran on")
     ap.add_argument("--exact-cta", type=int, default=None,
                     help="exact class evaluations of m <= 27 one per CTA from this m on (library default 10)")
     ap.add_argument("--cluster", type=int, default=8, help="CTAs per circuit (thread-block cluster)")
@@ -1115,6 +1116,10 @@ def main():
                                 "peak_source": "FP32 fma, " + peak_src}}
 
     progress(f"timed steps: {[round(t, 3) for t in times]}")
+    if args.sm_ids:
+        for d in (2, 3):
+            for c in range(SEEDS_PER_D):
+                progress(f"d{d} circuit {c} SM ids: {sims[d].profile(c)['sm_ids']}")
     # end to end: host gate lists, copies and readback inside the timed region
     torch.cuda.synchronize()
     if world > 1:

@@ -67,7 +67,7 @@ typedef struct {
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a handle-owned stream            */
   /* The fields above are the contract's options, in its order; the ones below extend it.           */
   double strict_weight;/* if > 0: GCAMPS_ECHI when one truncation discards more than this      */
-  int cluster_size;    /* CTAs (one thread-block cluster) per circuit: 1, 2, 4, 8 or 16; 0 = 8   */
+  int cluster_size;    /* CTAs (one thread-block cluster) per circuit: 1 to 16; 0 = 8            */
   int64_t snapshot_entries;   /* per circuit: complex entries of the arena that keeps the MPS  */
                               /* after every non-Clifford gate for gcamps_expect_gradient    */
                               /* (0 = no snapshots, no gradients; default 0)                 */
@@ -190,8 +190,8 @@ int gcamps_create_batch_uneven(int batch, const int32_t* n, int d, int chi_max, 
 void gcamps_destroy(gcamps_t* h);
 /* Qudits of circuit `circuit` (-1 for a bad handle or index).  No counterpart in the paper. */
 int gcamps_num_qudits(gcamps_t* h, int circuit);
-/* CTAs per circuit for the following launches: a power of two up to the cluster size the handle was
- * created with (its per-CTA scratch is laid out for that many).  Synchronises the handle's stream.
+/* CTAs per circuit for the following launches: 1 up to the cluster size the handle was created with
+ * (its per-CTA scratch is laid out for that many).  Synchronises the handle's stream.
  * Used to pick the fastest cluster size for a workload by measurement.  No counterpart in the paper
  * (a launch shape of this library).  EINVAL for other sizes. */
 int gcamps_set_cluster_size(gcamps_t* h, int cluster_size);
@@ -327,9 +327,12 @@ int gcamps_overlap(gcamps_t* h1, int circuit1, gcamps_t* h2, int circuit2, doubl
  *   von Neumann estimates, for the visit size buckets b = 0..4 of m = min(chi_l d, d chi_r): m <= 9, <= 27,
  *   <= 54, <= 81, larger; [11] cycles and [32] count of the warp-level exact evaluations run by the leader
  *   CTA's first warp (the duration of one evaluation, free of the cluster's waits); [33 + 11 b + p] the
- *   cycles of phase p (0..10 as above) spent inside the visits of bucket b; [95] internal (0 between
- *   launches). */
-#define GCAMPS_PROF_WORDS 96
+ *   cycles of phase p (0..10 as above) spent inside the visits of bucket b; [88 + 6 (5 g + b) + j] the
+ *   leader CTA's own exact evaluations at warp level (g = 0, its first warp) or CTA level (g = 1) in bucket
+ *   b: j = 0 their count, 1 their cycles, of which 2 forming theta' and its Gram, 3 the Householder
+ *   reduction, 4 the eigenvalues, 5 the entropy; [160 + r] 1 + the SM id that cluster rank r (r < 16) ran
+ *   on in the last gate-list launch (0: none); [191] internal (0 between launches). */
+#define GCAMPS_PROF_WORDS 192
 int gcamps_get_profile(gcamps_t* h, int circuit, int64_t* out, int32_t cap, int32_t* count);
 /* Scores (Sec. 3) of the last disentangler bond visit of the circuit: s2[k] (Renyi-2 entropy of every class:
  * FP64 where evaluated[k] = 1, else the FP32 screening value, within 4 eta sqrt(m) + 4 eta of the exact

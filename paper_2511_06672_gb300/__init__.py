@@ -342,12 +342,18 @@ class Simulator:
         self._c(self._lib.gcamps_get_profile(self._h, circuit, p.ctypes.data_as(C.POINTER(C.c_int64)), N.PROF_WORDS,
                                              C.byref(cnt)))
         out = {"cycles": {k: int(p[i]) for i, k in enumerate(N.PROF_PHASES)}, "buckets": {},
-               "leader_warp_exact": {"cycles": int(p[11]), "count": int(p[32])}}
+               "leader_warp_exact": {"cycles": int(p[11]), "count": int(p[32])},
+               "sm_ids": [int(v) - 1 for v in p[160:176] if v > 0]}
         nph = len(N.PROF_PHASES)
         for b, name in enumerate(N.PROF_BUCKETS):
             out["buckets"][name] = {"visits": int(p[12 + b]), "cycles": int(p[17 + b]), "exact": int(p[22 + b]),
                                     "estimates": int(p[27 + b]),
                                     "phases": {k: int(p[33 + nph * b + i]) for i, k in enumerate(N.PROF_PHASES)}}
+            for g, level in enumerate(("warp", "cta")):
+                w = 88 + 6 * (5 * g + b)
+                out["buckets"][name]["exact_" + level] = {
+                    "count": int(p[w]), "cycles": int(p[w + 1]), "gram": int(p[w + 2]), "householder": int(p[w + 3]),
+                    "eigenvalues": int(p[w + 4]), "entropy": int(p[w + 5])}
         return out
 
     def score_theta(self, theta: np.ndarray):

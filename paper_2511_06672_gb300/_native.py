@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libg
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ECHI, ESIZE, ESNAP = 0, 1, 2, 3, 4, 5, 6, 7
 NOALLOC_MAX_SIDE = 81
-PROF_WORDS = 96
+PROF_WORDS = 192
 PROF_PHASES = ("clifford", "mpo", "center", "theta", "screen", "vn_estimate", "exact", "decide", "apply_q", "split",
                "qr_move")
 PROF_BUCKETS = ("m<=9", "m<=27", "m<=54", "m<=81", "m>81")

@@ -150,6 +150,7 @@ struct Smem {
   int flag;
   int ival[8];
   double dval[4];
+  double pub;                 // BlockGroup::publish
   uint64_t tc_mbar;           // tensor-core Gram: completion barrier of its MMAs
   uint32_t tc_tmem;           // its TMEM accumulator (column base)
   uint32_t tc_commits;        // commits on tc_mbar so far (its phase parity)
@@ -241,16 +242,18 @@ __device__ void set_failure(const Ctx& C, int code, int where, int a, int b) {
   }
 }
 
+static_assert((kWarps & (kWarps - 1)) == 0 && kWarps <= 32, "block_sum's shuffle tree");
 __device__ double block_sum(double v, Smem& s) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) s.red[w] = v;
   __syncthreads();
-  double t = 0.0;
+  // the kWarps partial sums by a shuffle tree (three FP64 adds per warp instead of kWarps)
+  double t = l < kWarps ? s.red[l] : 0.0;
 #pragma unroll
-  for (int i = 0; i < kWarps; ++i) t += s.red[i];
-  return t;
+  for (int o = kWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return __shfl_sync(0xffffffffu, t, 0);
 }
 
 // FP32 sums for the FP32 paths (the screen and the estimates): GB300 runs FP64 adds on a narrow pipe, so
@@ -1187,6 +1190,11 @@ struct WarpGroup {
   __device__ double sum(double v) const { return warp_sum(v); }
   __device__ float sumf(float v) const { return warp_sum_f(v); }
   __device__ double bcast(double v) const { return __shfl_sync(0xffffffffu, v, 0); }
+  // thread 0's v (after its memory writes) to every thread of the group
+  __device__ double publish(double v) const {
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
 };
 struct BlockGroup {
   Smem* s;
@@ -1201,6 +1209,13 @@ struct BlockGroup {
     const double r = s->dval[2];
     __syncthreads();
     return r;
+  }
+  // thread 0's v (after its memory writes) to every thread of the CTA, one barrier; the caller keeps
+  // two publishes apart by at least one more barrier (no thread still reads the previous value)
+  __device__ double publish(double v) const {
+    if (tid == 0) s->pub = v;
+    __syncthreads();
+    return s->pub;
   }
 };
 
@@ -1221,27 +1236,53 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
     double tail2 = 0;
     for (int i = 1 + g.tid; i < r; i += g.n) tail2 += cabs2(A[(long long)(k + 1 + i) * m + k]);
     tail2 = g.sum(tail2);
-    const double2 x0 = A[(long long)(k + 1) * m + k];
-    const double ax0 = hypot(x0.x, x0.y);
-    const double nrm2 = tail2 + ax0 * ax0;
-    if (g.tid == 0) dg[k] = A[(long long)k * m + k].x;
-    g.sync();
-    const double alpha = sqrt(nrm2);
-    if (tail2 <= 1e-32 * fro2) {
-      if (g.tid == 0) od[k] = ax0;
+    // the step's scalars on thread 0 alone (every warp computing them would put each FP64 pipe through
+    // them twice): |x0|, alpha = |x|, the reflector's head x0 + phase(x0) alpha, h = v^H v / 2; published
+    // as 1 / h, or -1 for a column that is already reduced
+    double pub = 0.0;
+    if (g.tid == 0) {
+      const double2 x0 = A[(long long)(k + 1) * m + k];
+      const double ax0 = hypot(x0.x, x0.y);
+      dg[k] = A[(long long)k * m + k].x;
+      if (tail2 <= 1e-32 * fro2) {
+        od[k] = ax0;
+        pub = -1.0;
+      } else {
+        const double alpha = sqrt(tail2 + ax0 * ax0);
+        const double2 ph = unit_phase(x0);
+        A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+        od[k] = alpha;
+        pub = 1.0 / (alpha * (alpha + ax0));
+      }
+    }
+    const double hinv = g.publish(pub);
+    if (hinv < 0.0) {
       g.sync();
       continue;
     }
-    const double2 ph = unit_phase(x0);
-    const double h = alpha * (alpha + ax0);  // v^H v / 2
-    if (g.tid == 0) A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
-    g.sync();
-    const double hinv = 1.0 / h;
     // p = A v / h: kc lanes of one warp share a row (kc a power of two, kc r <= group size), each summing
     // every kc-th column, then a shuffle tree; every thread runs the same passes, so the shuffles see
     // full warps
+    // kc chosen for the FP64 pipes: per pass of g.n / kc rows, the busiest pipe issues (its warps) x
+    // (4 ceil(r / kc) + 2 log2 kc) FP64 instructions
     int kc = 1;
-    while (kc < 32 && 2 * kc * r <= g.n && 2 * kc <= r) kc *= 2;
+    {
+      int best = 1 << 30;
+      for (int q = 1, lg = 0; q <= 32 && q <= r; q *= 2, ++lg) {
+        const int rif = g.n / q;
+        if (rif < 1) break;
+        int cost = 0;
+        for (int b0 = 0; b0 < r; b0 += rif) {
+          const int rows_p = r - b0 < rif ? r - b0 : rif;
+          const int warps = (rows_p * q + 31) / 32;
+          cost += ((warps + 3) / 4) * (4 * ((r + q - 1) / q) + 2 * lg);
+        }
+        if (cost < best) {
+          best = cost;
+          kc = q;
+        }
+      }
+    }
     const int rows_in_flight = g.n / kc;
     for (int base = 0; base < r; base += rows_in_flight) {
       const int i = base + g.tid / kc, c = g.tid & (kc - 1);
@@ -1282,7 +1323,6 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
       *a = nv;
       if (j != i) A[(long long)(k + 1 + j) * m + (k + 1 + i)] = cconj(nv);
     }
-    if (g.tid == 0) od[k] = alpha;
     g.sync();
   }
   if (g.tid == 0) {
@@ -1350,12 +1390,17 @@ __device__ __forceinline__ int sturm_count(const double* dg, const double* e2, i
     const long long b2 = __double_as_longlong(f2);
     const int ex1 = (int)((b1 >> 52) & 0x7ff), ex2 = (int)((b2 >> 52) & 0x7ff);
     const int ex = ex1 > ex2 ? ex1 : ex2;
-    if (ex > 1023 + 500) {
-      f1 *= 3.054936363499605e-151;   // 2^-500
-      f2 *= 3.054936363499605e-151;
-    } else if (ex < 1023 - 500) {
-      f1 *= 3.273390607896142e+150;   // 2^500
-      f2 *= 3.273390607896142e+150;
+    const bool out = ex > 1023 + 500 || ex < 1023 - 500;
+    // a warp-uniform branch around the (rare) rescaling: predicated FP64 multiplies would still occupy
+    // the FP64 pipe on every step
+    if (__any_sync(__activemask(), out)) {
+      if (ex > 1023 + 500) {
+        f1 *= 3.054936363499605e-151;   // 2^-500
+        f2 *= 3.054936363499605e-151;
+      } else if (ex < 1023 - 500) {
+        f1 *= 3.273390607896142e+150;   // 2^500
+        f2 *= 3.273390607896142e+150;
+      }
     }
     const long long c2 = __double_as_longlong(f2);
     const unsigned s2 = (c2 & 0x7fffffffffffffffLL) == 0 ? (s1 ^ 1u) : (unsigned)((unsigned long long)c2 >> 63);
@@ -1366,6 +1411,41 @@ __device__ __forceinline__ int sturm_count(const double* dg, const double* e2, i
     b1 = c2;
   }
   return cnt;
+}
+
+// det(T - x) and its derivative in x by the same three-term recurrence (f_i = (d_i - x) f_{i-1} -
+// e_{i-1}^2 f_{i-2}, f'_i = (d_i - x) f'_{i-1} - f_{i-1} - e_{i-1}^2 f'_{i-2}), the four running values
+// rescaled together by 2^-+500 when their largest exponent leaves [2^-500, 2^500]: f / f' is unchanged.
+__device__ __forceinline__ void sturm_newton(const double* dg, const double* e2, int m, double x, double& f,
+                                             double& fp) {
+  double f0 = 1.0, f1 = dg[0] - x, g0 = 0.0, g1 = -1.0;
+  for (int i = 1; i < m; ++i) {
+    const double t = dg[i] - x;
+    double f2 = fma(t, f1, -e2[i - 1] * f0);
+    double g2 = fma(t, g1, -fma(e2[i - 1], g0, f1));
+    const int ea = (int)((__double_as_longlong(f1) >> 52) & 0x7ff), eb = (int)((__double_as_longlong(f2) >> 52) & 0x7ff);
+    const int ec = (int)((__double_as_longlong(g1) >> 52) & 0x7ff), ed = (int)((__double_as_longlong(g2) >> 52) & 0x7ff);
+    const int ex = max(max(ea, eb), max(ec, ed));
+    if (__any_sync(__activemask(), ex > 1023 + 500 || ex < 1023 - 500)) {   // rare: see sturm_count
+      if (ex > 1023 + 500) {
+        f1 *= 3.054936363499605e-151;   // 2^-500
+        f2 *= 3.054936363499605e-151;
+        g1 *= 3.054936363499605e-151;
+        g2 *= 3.054936363499605e-151;
+      } else if (ex < 1023 - 500) {
+        f1 *= 3.273390607896142e+150;   // 2^500
+        f2 *= 3.273390607896142e+150;
+        g1 *= 3.273390607896142e+150;
+        g2 *= 3.273390607896142e+150;
+      }
+    }
+    f0 = f1;
+    f1 = f2;
+    g0 = g1;
+    g1 = g2;
+  }
+  f = f1;
+  fp = g1;
 }
 
 // FP32 version of sturm_count (rescaling by 2^-+40 outside [2^-40, 2^40]); it is exact for a matrix
@@ -1456,13 +1536,24 @@ __device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m
   // Multisection: P lanes of a warp share eigenvalue j and count at P interior points of its
   // interval, which then shrinks by P + 1 per step (P as large as the group's warps allow).  All
   // lanes of a warp run the same number of steps (the group's outcome is combined by a ballot).
+  // P is chosen for the FP64 pipes, not the lanes: a warp's Sturm count costs 3 m FP64 instructions whatever
+  // its active lanes, and the four warps w, w + 4 of a CTA share one pipe, so the cost of P is the passes
+  // over the eigenvalues x the busiest pipe's warps x the FP64 steps for P (ties to the larger P)
   const int nw = (g.n + 31) / 32;
+  constexpr int kIt64[9] = {0, 33, 21, 17, 15, 13, 12, 11, 11};   // ceil(33 / log2(P + 1))
   int P = 1;
-  for (int p = 8; p >= 1; --p)
-    if (nw * (32 / p) >= m) {
-      P = p;
-      break;
+  {
+    int best = 1 << 30;
+    for (int p = 8; p >= 1; --p) {
+      const int pw = 32 / p, need = (m + pw - 1) / pw, passes = (need + nw - 1) / nw;
+      const int busiest = passes > 1 ? (nw + 3) / 4 : (need + 3) / 4;
+      const int cost = passes * busiest * kIt64[p];
+      if (cost < best) {
+        best = cost;
+        P = p;
+      }
     }
+  }
   const int per_warp = 32 / P;
   const int lane = g.tid & 31, warp = g.tid >> 5;
   const int grp = lane / P, pidx = lane % P;
@@ -1493,20 +1584,63 @@ __device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m
       }
       const double pad = 40.0 * 5.960464477539063e-08 * span;   // 40 FP32 units
       const double a = (double)lo32 - pad, b = (double)hi32 + pad;
-      bool ok;
+      // FP64 counts at the padded ends (lane 0 of the group at a, lane 1 at b): ca <= j < cb confirms the
+      // bracket, and cb - ca eigenvalues lie in it
+      const int g0 = (lane / P) * P;
+      int ca = 0, cb = m;
       if (P == 1) {
-        ok = !active || (sturm_count(D, E, m, a) <= j && sturm_count(D, E, m, b) > j);
+        if (active) {
+          ca = sturm_count(D, E, m, a);
+          cb = sturm_count(D, E, m, b);
+        }
       } else {
-        bool mine = true;
-        if (active && pidx == 0) mine = sturm_count(D, E, m, a) <= j;
-        if (active && pidx == 1) mine = sturm_count(D, E, m, b) > j;
-        const unsigned fails = __ballot_sync(0xffffffffu, !mine) & gmask;
-        ok = !active || fails == 0u;
+        int c = 0;
+        if (active && pidx < 2) c = sturm_count(D, E, m, pidx == 0 ? a : b);
+        ca = __shfl_sync(0xffffffffu, c, g0);
+        cb = __shfl_sync(0xffffffffu, c, g0 + 1);
       }
-      if (__all_sync(0xffffffffu, ok)) {
+      if (__all_sync(0xffffffffu, !active || (ca <= j && cb > j))) {
         lo = a;
         hi = b;
         nit = it64;
+      }
+      // at m > 27 the small eigenvalues of decaying spectra share their FP32 brackets and the Newton
+      // attempt below rarely verifies: the multisection alone is cheaper there
+      if (m <= 27 && nit == it64) {
+        // Newton steps on det(T - x) from the bracket's midpoint, the step times k = cb - ca (the root is
+        // k-fold when the bracket holds a cluster far tighter than itself), kept inside [a, b].  Their
+        // result stands for every eigenvalue of the warp if FP64 counts place each within tol = 2^-51 span
+        // of it (the guarantee the multisection gives); otherwise the multisection below runs.
+        const double tol = 4.440892098500626e-16 * span;
+        const double k = active ? (double)(cb - ca) : 1.0;
+        double x = active ? 0.5 * (a + b) : 0.0;
+        bool bad = false;
+        for (int it = 0; it < 4; ++it) {
+          double f, fp;
+          sturm_newton(D, E, m, x, f, fp);
+          const double stp = k * f / fp;
+          if (!(fabs(stp) < 1e300)) bad = true;   // f' = 0 or a non-finite value
+          const double xn = bad ? x : fmin(fmax(x - stp, a), b);
+          const bool conv = fabs(xn - x) <= 0.25 * tol;
+          x = xn;
+          if (__all_sync(0xffffffffu, !active || bad || conv)) break;
+        }
+        int vlo = 0, vhi = m;
+        if (P == 1) {
+          if (active && !bad) {
+            vlo = sturm_count(D, E, m, x - tol);
+            vhi = sturm_count(D, E, m, x + tol);
+          }
+        } else {
+          int c = 0;
+          if (active && pidx < 2) c = sturm_count(D, E, m, pidx == 0 ? x - tol : x + tol);
+          vlo = __shfl_sync(0xffffffffu, c, g0);
+          vhi = __shfl_sync(0xffffffffu, c, g0 + 1);
+        }
+        if (__all_sync(0xffffffffu, !active || (!bad && vlo <= j && vhi > j))) {
+          if (active && pidx == 0) ev[j] = x;
+          continue;
+        }
       }
     }
     for (int it = 0; it < nit; ++it) {
@@ -1539,7 +1673,7 @@ __device__ void gram_fp32(const Grp& g, const Ctx& C, const float2* X, int rows,
 template <class Grp>
 __device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, double2* G, int m, double tr, double fro,
                                                 bool want_vn, double* dg, double* od, double* tri, float* tri32,
-                                                int tricap);
+                                                int tricap, long long* xw = nullptr);
 
 // The precision form's class evaluation: theta' = Q theta and its Gram in FP32 (tensor cores at CTA level),
 // promoted to FP64 for the reduction, the eigenvalues and the score.  Kept out of line so that the FP64 path
@@ -1593,6 +1727,11 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   double* od = dg + m;
   if (C.e->precision && m > kPruneMin && Q != C.e->candU)
     return score_class_fp32(g, C, cl, cr, Q32, ws, gram_off, want_vn, tri, tri32, tricap);
+  // the leader's own exact evaluations, timed part by part (thread 0: warp 0's or the CTA's)
+  long long* xw = (want_vn && C.prof && C.rank == 0 && threadIdx.x == 0)
+                      ? C.prof + P_XPARTS + kXParts * (kProfBuckets * (g.n > 32 ? 1 : 0) + prof_bucket(m))
+                      : nullptr;
+  const long long tx0 = xw ? clock64() : 0;
   for (long long idx = g.tid; idx < (long long)rows * cols; idx += g.n) {
     const int rr = (int)(idx / cols), col = (int)(idx % cols);
     const int a = rr / d, sd = rr % d, t = col / cr, b = col % cr;
@@ -1627,7 +1766,13 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
   }
   tr = g.sum(tr);
   fro = g.sum(fro);
-  return score_spectrum(g, C, G, m, tr, fro, want_vn, dg, od, tri, tri32, tricap);
+  if (xw) xw[2] += clock64() - tx0;
+  const Score sc = score_spectrum(g, C, G, m, tr, fro, want_vn, dg, od, tri, tri32, tricap, xw);
+  if (xw) {
+    xw[0] += 1;
+    xw[1] += clock64() - tx0;
+  }
+  return sc;
 }
 
 // S2 from the Gram's trace and squared Frobenius norm, and (want_vn) the von Neumann entropy and weight rank
@@ -1635,7 +1780,7 @@ __device__ Score score_class(const Grp& g, const Ctx& C, const double2* theta, i
 template <class Grp>
 __device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, double2* G, int m, double tr, double fro,
                                                 bool want_vn, double* dg, double* od, double* tri, float* tri32,
-                                                int tricap) {
+                                                int tricap, long long* xw) {
   Score sc;
   sc.ok = true;
   sc.s2 = (tr > 0.0 && fro > 0.0) ? -log(fro / (tr * tr)) : 0.0;
@@ -1643,9 +1788,20 @@ __device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, doub
   sc.rank = -1;
   if (!want_vn) return sc;
   g.sync();
+  long long tx = xw ? clock64() : 0;
   group_tridiag(g, G, m, dg, od);
+  if (xw) {
+    const long long now = clock64();
+    xw[3] += now - tx;
+    tx = now;
+  }
   double* ev = reinterpret_cast<double*>(G);   // G is dead after the reduction
   tridiag_bisect(g, dg, od, m, ev, tri, tri32, tricap);
+  if (xw) {
+    const long long now = clock64();
+    xw[4] += now - tx;
+    tx = now;
+  }
   // entropy -sum p ln p (p = lambda / tr) and the numerical rank, summed over the group
   double tot = 0;
   for (int i = g.tid; i < m; i += g.n) tot += fmax(ev[i], 0.0);
@@ -1663,6 +1819,7 @@ __device__ __forceinline__ Score score_spectrum(const Grp& g, const Ctx& C, doub
   sc.vn = g.sum(ent);
   sc.rank = (int)g.sum(rk);
   sc.ok = true;
+  if (xw) xw[5] += clock64() - tx;
   return sc;
 }
 
@@ -2900,6 +3057,11 @@ __device__ __forceinline__ void run_body(const Engine& e, const gcamps_op* ops, 
   Ctx C = make_ctx(e, c, rank);
   Smem* lead = cg::this_cluster().map_shared_rank(&s, 0);
   init_tau(s, e.d);
+  if (C.prof && threadIdx.x == 0 && rank < kProfSmids) {   // where the cluster's CTAs run (1 + SM id)
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    C.prof[P_SMID + rank] = 1 + (long long)sm;
+  }
   if (GCAMPS_TC && e.tc_smem) tc_setup(s);
   for (int i = first; i < stop; ++i) run_op(s, lead, C, ops[i]);
   cluster_sync();

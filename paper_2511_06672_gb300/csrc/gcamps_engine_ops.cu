@@ -1,5 +1,5 @@
-// Single-operation and all-circuits launches of libgcamps (arxiv 2511.06672, Sec. 3), and the
-// Schmidt-value readout of one bond (Sec. 2.4).
+// All-circuits launches of libgcamps (arxiv 2511.06672, Sec. 3) and the Schmidt-value readout of one bond
+// (Sec. 2.4); the single-operation launch is in gcamps_engine_single.cu.
 
 #include "gcamps_device.cuh"
 
@@ -9,8 +9,6 @@ namespace {
 __global__ void __launch_bounds__(kThreads, kMinCtas) k_run_all(Engine e, const gcamps_op* ops, int nops) {
   run_body(e, ops, 0, nops, blockIdx.x / e.csize, blockIdx.x % e.csize);
 }
-
-__global__ void __launch_bounds__(kThreads, kMinCtas) k_single(Engine e, gcamps_op op) { single_body(e, op); }
 
 
 // Schmidt values of one bond: move the centre next to it and take the singular values.
@@ -33,11 +31,6 @@ __global__ void __launch_bounds__(kThreads) k_schmidt(Engine e, int c, int bond,
 cudaError_t launch_run_all(const Engine& e, const gcamps_op* ops_dev, int nops, cudaStream_t st) {
   if (e.precision) return launch_run_all_tc(e, ops_dev, nops, st);
   return launch_cluster(k_run_all, e, st, e, ops_dev, nops);
-}
-
-cudaError_t launch_single(const Engine& e, const gcamps_op& op, cudaStream_t st) {
-  if (e.precision) return launch_single_tc(e, op, st);
-  return launch_cluster(k_single, e, st, e, op);
 }
 
 cudaError_t launch_schmidt(const Engine& e, int circuit, int bond, double* s_dev, int* cnt_dev, cudaStream_t st) {

@@ -534,8 +534,7 @@ int gcamps_create_batch_uneven(int batch, const int32_t* nqs, int d, int chi_max
       !(opts.tie_tol >= 0.0))
     return GCAMPS_EINVAL;
   if (opts.cluster_size == 0) opts.cluster_size = 8;
-  if (opts.cluster_size < 1 || opts.cluster_size > gcx::kMaxCluster ||
-      (opts.cluster_size & (opts.cluster_size - 1)))
+  if (opts.cluster_size < 1 || opts.cluster_size > gcx::kMaxCluster)
     return GCAMPS_EINVAL;
   gcamps_t* h = new (std::nothrow) gcamps;
   if (!h) return GCAMPS_ENOMEM;
@@ -923,8 +922,8 @@ int gcamps_set_exact_cta(gcamps_t* h, int min_m) {
 
 int gcamps_set_cluster_size(gcamps_t* h, int cluster_size) {
   if (!h) return GCAMPS_EINVAL;
-  if (cluster_size < 1 || cluster_size > h->csize_alloc || (cluster_size & (cluster_size - 1)))
-    return fail(h, GCAMPS_EINVAL, "cluster size must be a power of two up to the one the handle was created with");
+  if (cluster_size < 1 || cluster_size > h->csize_alloc)
+    return fail(h, GCAMPS_EINVAL, "cluster size must be 1 up to the one the handle was created with");
   GC_CUDA(h, cudaStreamSynchronize(h->stream));
   h->e.csize = cluster_size;
   return GCAMPS_OK;

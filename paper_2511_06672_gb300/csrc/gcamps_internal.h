@@ -48,10 +48,17 @@ enum Stat { S_T = 0, S_CLIFF, S_BONDS, S_CANDS, S_ACC, S_SWEEPS, S_MAXCHI, S_VN,
 // bucket's visits; and (P_CURB, internal) 1 + the bucket of the visit in progress, 0 outside visits.
 enum Prof { P_CLIFF = 0, P_MPO, P_CENTER, P_THETA, P_SCREEN, P_EST, P_EXACT, P_DECIDE, P_APPLYQ, P_SPLIT,
             P_QRMOVE, P_LEAD_EXACT_CYC, P_VISITS = 12, P_VCYC = 17, P_VEXACT = 22, P_VEST = 27,
-            P_LEAD_EXACT_N = 32, P_BPHASE = 33, P_CURB = 95, P_COUNT = 96 };
+            P_LEAD_EXACT_N = 32, P_BPHASE = 33, P_XPARTS = 88, P_SMID = 160, P_CURB = 191, P_COUNT = 192 };
+constexpr int kProfSmids = 16;   // 1 + the SM id of cluster ranks 0..15 in the last gate-list launch
 constexpr int kProfPhases = 11;
 constexpr int kProfBuckets = 5;
-static_assert(P_BPHASE + kProfBuckets * kProfPhases <= P_CURB, "bucket phase words fit");
+// parts of the leader's own exact evaluations: [P_XPARTS + 6 (5 g + b) + j], g = 0 warp-level, 1 CTA-level,
+// b the size bucket, j = 0 count, 1 cycles, 2 theta' and Gram, 3 Householder reduction, 4 eigenvalues,
+// 5 entropy
+constexpr int kXParts = 6;
+static_assert(P_BPHASE + kProfBuckets * kProfPhases <= P_XPARTS, "bucket phase words fit");
+static_assert(P_XPARTS + 2 * kProfBuckets * kXParts <= P_SMID, "exact-part words fit");
+static_assert(P_SMID + 16 <= P_CURB, "SM id words fit");
 static_assert(P_COUNT == GCAMPS_PROF_WORDS, "profile layout stated in gcamps.h");
 
 // Scratch areas of one circuit, as element offsets (double2) from its scratch base.

@@ -106,9 +106,10 @@ def test_create_without_gpu_fails_cleanly(lib):
 
 
 def test_create_rejects_bad_options_before_touching_the_gpu(lib):
-    """Option validation (score_kind 0..2, power-of-two cluster size) happens on the host first."""
+    """Option validation (score_kind 0..2, cluster size 1..16) happens on the host first."""
     from paper_2511_06672_gb300 import _native as N
-    for field, value in (("score_kind", 3), ("score_kind", -1), ("cluster_size", 3), ("max_sweeps", -1)):
+    for field, value in (("score_kind", 3), ("score_kind", -1), ("cluster_size", 17), ("cluster_size", -2),
+                         ("max_sweeps", -1)):
         o = N.Opts()
         lib.gcamps_default_opts(C.byref(o))
         setattr(o, field, value)

@@ -268,7 +268,7 @@ def test_reset(G):
     assert sim.decisions() == ref.decisions
 
 
-@pytest.mark.parametrize("csize", [1, 2, 4, 16])
+@pytest.mark.parametrize("csize", [1, 2, 4, 12, 14, 16])
 def test_cluster_sizes_give_identical_decisions(G, csize):
     """The disentangler decisions do not depend on how many CTAs score the classes (qutrits,
     n = 12, chi up to 27, where the Renyi-2 pruning path is taken)."""
