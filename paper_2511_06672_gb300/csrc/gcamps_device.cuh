@@ -1242,14 +1242,19 @@ __device__ void group_tridiag(const Grp& g, double2* A, int m, double* dg, doubl
     double pub = 0.0;
     if (g.tid == 0) {
       const double2 x0 = A[(long long)(k + 1) * m + k];
-      const double ax0 = hypot(x0.x, x0.y);
+      // |x0|^2 in the normal range: one reciprocal square root gives |x0| and the phase x0 / |x0| (each
+      // within two units of the last place); outside it, hypot and unit_phase with their rescaling
+      const double s0 = fma(x0.x, x0.x, x0.y * x0.y);
+      const bool fast = s0 > 0x1p-1000 && s0 < 0x1p+1000;
+      const double rs = fast ? rsqrt(s0) : 0.0;
+      const double ax0 = fast ? s0 * rs : hypot(x0.x, x0.y);
       dg[k] = A[(long long)k * m + k].x;
       if (tail2 <= 1e-32 * fro2) {
         od[k] = ax0;
         pub = -1.0;
       } else {
         const double alpha = sqrt(tail2 + ax0 * ax0);
-        const double2 ph = unit_phase(x0);
+        const double2 ph = fast ? make_double2(x0.x * rs, x0.y * rs) : unit_phase(x0);
         A[(long long)(k + 1) * m + k] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
         od[k] = alpha;
         pub = 1.0 / (alpha * (alpha + ax0));
