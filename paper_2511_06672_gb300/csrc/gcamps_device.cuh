@@ -139,6 +139,10 @@ struct Smem {
   double btri[2 * kBTri];     // CTA-level: diagonal | off-diagonal squared
   float btri32[2 * kBTri];
   float2 hv[kBTri], hw[kBTri];  // FP32 Householder reduction: reflector v and w = p - K v of the current column
+  // the second half-CTA group's copies (two FP32 estimates at once, HalfGroup) and both halves' partial sums
+  float2 hv2[kBTri], hw2[kBTri];
+  float btri32b[2 * kBTri];
+  float redh[2][kWarps / 2];
   float2 whv[kWarps][32], whw[kWarps][32];   // the same per warp (warp-level estimates, m <= 32)
   int bcast;
   int jmode, jm, jn;          // cluster split of a bond visit: 0 none, 2 cluster Jacobi; its matrix shape (leader)
@@ -1196,6 +1200,29 @@ struct WarpGroup {
     return __shfl_sync(0xffffffffu, v, 0);
   }
 };
+// Half a CTA: kThreads / 2 threads (warps 0-3 or 4-7, one warp per SM sub-partition), synchronised by the
+// named barrier 1 + half, with its own partial-sum slots; two halves score two classes at once.
+struct HalfGroup {
+  Smem* s;
+  int tid, n, half;
+  __device__ void sync() const {   // immediate barrier ids: a register id would reserve all sixteen
+    if (half == 0) asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+  }
+  __device__ float sumf(float v) const {
+    v = warp_sum_f(v);
+    const int w = tid >> 5, l = tid & 31;
+    sync();
+    if (l == 0) s->redh[half][w] = v;
+    sync();
+    float t = l < kWarps / 2 ? s->redh[half][l] : 0.f;
+#pragma unroll
+    for (int o = kWarps / 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return __shfl_sync(0xffffffffu, t, 0);
+  }
+};
+static_assert(kThreads == 32 * kWarps && kWarps >= 4, "two half-CTA groups of whole warps");
+
 struct BlockGroup {
   Smem* s;
   int tid, n;
@@ -2453,6 +2480,29 @@ __device__ void score_classes(Smem& s, Smem* lead, const Ctx& C, const double2* 
   } else {
     BlockGroup g{&s, (int)threadIdx.x, (int)blockDim.x};
     double2* ws = C.cta + e.cl.block;
+    // FP32 estimates of more classes than the cluster has CTAs: two at once per CTA, one per half (each
+    // half's scratch after the other's, when both fit the CTA-level buffer of 2 scap + 64 complex doubles)
+    const long long half_off = ((long long)rows * cols + (long long)m * m + 2LL * m + 63) & ~31LL;   // float2
+    if (mode == kEstimate && cnt > C.csize && half_off <= 2 * e.scap + 64) {
+      const int half = (int)threadIdx.x / (kThreads / 2);
+      HalfGroup hg{&s, (int)threadIdx.x % (kThreads / 2), kThreads / 2, half};
+      float2* wsh = reinterpret_cast<float2*>(ws) + half * half_off;
+      for (int t = C.rank + half * C.csize; t < cnt; t += 2 * C.csize) {
+        const int k = list ? list[t] : t;
+        float est = 0.f;
+        const bool ok = vn_est32(hg, C, C.th32, cl, cr, e.candU32 + (long long)k * dd * dd, wsh,
+                                 half ? s.hv2 : s.hv, half ? s.hw2 : s.hw, kBTri, half ? s.btri32b : s.btri32,
+                                 kBTri, &est, (float*)nullptr, (float*)nullptr);
+        if (hg.tid == 0) {
+          lead->vest[k] = est;
+          lead->vbd[k] = ok ? lead->dval[3] : 1e300;   // the visit's bound (select_class), or none
+          lead->estd[k] = 1;
+        }
+        hg.sync();
+      }
+      __syncthreads();
+      return;
+    }
     for (int t = C.rank; t < cnt; t += C.csize) {
       const int k = list ? list[t] : t;
       if (mode == kScreen) {
