@@ -1568,9 +1568,10 @@ __device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m
   // Multisection: P lanes of a warp share eigenvalue j and count at P interior points of its
   // interval, which then shrinks by P + 1 per step (P as large as the group's warps allow).  All
   // lanes of a warp run the same number of steps (the group's outcome is combined by a ballot).
-  // P is chosen for the FP64 pipes, not the lanes: a warp's Sturm count costs 3 m FP64 instructions whatever
-  // its active lanes, and the four warps w, w + 4 of a CTA share one pipe, so the cost of P is the passes
-  // over the eigenvalues x the busiest pipe's warps x the FP64 steps for P (ties to the larger P)
+  // P is chosen for the FP64 pipes, not the lanes: a warp's Sturm step issues 3 FP64 instructions (64 cycles
+  // of its sub-partition's pipe each) whatever its active lanes, and takes about 340 cycles alone (latency);
+  // warps w, w + 4 of a CTA share one pipe.  The cost of P: passes over the eigenvalues x FP64 steps for P x
+  // max(192 x the busiest pipe's warps, 340) (ties to the larger P)
   const int nw = (g.n + 31) / 32;
   constexpr int kIt64[9] = {0, 33, 21, 17, 15, 13, 12, 11, 11};   // ceil(33 / log2(P + 1))
   int P = 1;
@@ -1579,7 +1580,7 @@ __device__ void tridiag_bisect(const Grp& g, const double* dg, double* od, int m
     for (int p = 8; p >= 1; --p) {
       const int pw = 32 / p, need = (m + pw - 1) / pw, passes = (need + nw - 1) / nw;
       const int busiest = passes > 1 ? (nw + 3) / 4 : (need + 3) / 4;
-      const int cost = passes * busiest * kIt64[p];
+      const int cost = passes * kIt64[p] * max(192 * busiest, 340);
       if (cost < best) {
         best = cost;
         P = p;
