@@ -817,26 +817,33 @@ __device__ __noinline__ int block_qr(Smem& s, double2* B, int m, int n, double2*
     double nrm2 = 0;
     for (int r = j + threadIdx.x; r < m; r += blockDim.x) nrm2 += cabs2(x[r]);
     nrm2 = block_sum(nrm2, s);
-    const double2 x0 = x[j];
-    const double ax0 = hypot(x0.x, x0.y);
-    const double alpha = sqrt(nrm2);
-    __syncthreads();
-    if (nrm2 <= tiny) {
-      if (threadIdx.x == 0) {
+    // the column's scalars on thread 0 alone (as in group_tridiag), published as beta (0: left unreflected)
+    if (threadIdx.x == 0) {
+      const double2 x0 = x[j];
+      if (nrm2 <= tiny) {
         beta[j] = 0.0;
         rdiag[j] = x0;
+        s.pub = 0.0;
+      } else {
+        const double s0 = fma(x0.x, x0.x, x0.y * x0.y);
+        const bool fast = s0 > 0x1p-1000 && s0 < 0x1p+1000;
+        const double rs = fast ? rsqrt(s0) : 0.0;
+        const double ax0 = fast ? s0 * rs : hypot(x0.x, x0.y);
+        const double alpha = sqrt(nrm2);
+        const double2 ph = fast ? make_double2(x0.x * rs, x0.y * rs) : unit_phase(x0);
+        const double b = 1.0 / (alpha * (alpha + ax0));
+        x[j] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
+        beta[j] = b;
+        rdiag[j] = make_double2(-ph.x * alpha, -ph.y * alpha);
+        s.pub = b;
       }
+    }
+    __syncthreads();
+    const double bt = s.pub;
+    if (bt == 0.0) {
       __syncthreads();
       continue;
     }
-    const double2 ph = unit_phase(x0);
-    const double bt = 1.0 / (alpha * (alpha + ax0));
-    if (threadIdx.x == 0) {
-      x[j] = make_double2(x0.x + ph.x * alpha, x0.y + ph.y * alpha);
-      beta[j] = bt;
-      rdiag[j] = make_double2(-ph.x * alpha, -ph.y * alpha);
-    }
-    __syncthreads();
     for (int c = j + 1 + warp; c < n; c += kWarps) {
       double2* y = B + (long long)c * m;
       double wr = 0, wi = 0;   // w = v^H y
