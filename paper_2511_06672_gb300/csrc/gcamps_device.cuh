@@ -975,13 +975,47 @@ __device__ void move_left_qr(Smem& s, const Ctx& C, int j) {
 
 // Centre j -> j-1: A_j = U S Vh, A_j <- Vh, A_{j-1} <- A_{j-1} U S.  With truncation (cap, renorm)
 // this is one step of the right-to-left compression sweep.
-__device__ double move_left(Smem& s, const Ctx& C, int j, int cap, bool renorm) {
+// The truncated SVD of M with its Jacobi rotations on the whole cluster when lead is given (the leader's
+// shared memory, seen from the leader) and the matrix has at least kClusterJacobiMin Jacobi columns: the
+// leader publishes the request (jmode 2 and the shape) and meets the cluster at one barrier, then every CTA
+// runs jacobi_cluster.  Called by the leader only, while the other CTAs serve such requests (run_op).
+__device__ Factor svd_factor_cluster(Smem& s, Smem* lead, const Ctx& C, const double2* M, int rows, int cols,
+                                     int cap, bool renorm) {
+  const Engine& e = *C.e;
+  const SvdPrep p = svd_prepare(s, C, M, rows, cols);
+  double2* B = C.scr + e.sl.b;
+  double2* W = C.scr + e.sl.w;
+  int sweeps;
+  if (lead == nullptr || C.csize <= 1 || p.n < kClusterJacobiMin) {
+    sweeps = jacobi_orthogonalize(s, B, p.mm, p.n, W, e.jacobi_cap);
+  } else {
+    for (long long idx = threadIdx.x; idx < (long long)p.n * p.n; idx += blockDim.x)
+      W[idx] = ((idx % p.n) == (idx / p.n)) ? make_double2(1.0, 0.0) : cz();
+    double fro = 0;
+    for (long long idx = threadIdx.x; idx < (long long)p.mm * p.n; idx += blockDim.x) fro += cabs2(B[idx]);
+    fro = block_sum(fro, s);
+    if (threadIdx.x == 0) {
+      s.jfro = fro;
+      s.jflag[0] = s.jflag[1] = 0;
+      s.jm = p.mm;
+      s.jn = p.n;
+      s.jmode = 2;
+    }
+    __syncthreads();
+    cluster_sync();
+    sweeps = jacobi_cluster(lead, C, B, p.mm, p.n, W, e.jacobi_cap);
+  }
+  return svd_finish(s, C, p, sweeps, rows, cols, cap, renorm);
+}
+
+__device__ double move_left(Smem& s, const Ctx& C, int j, int cap, bool renorm, Smem* lead = nullptr) {
   const int d = C.d;
   const int cl = C.dims[j], cr = C.dims[j + 1], cl2 = C.dims[j - 1];
   double2* A = site_ptr(C, j);
   double2* A0 = site_ptr(C, j - 1);
   const int bb = C.bond_bound[j];
-  Factor F = svd_factor(s, C, A, cl, d * cr, cap < bb ? cap : bb, renorm);
+  Factor F = lead ? svd_factor_cluster(s, lead, C, A, cl, d * cr, cap < bb ? cap : bb, renorm)
+                  : svd_factor(s, C, A, cl, d * cr, cap < bb ? cap : bb, renorm);
   const int k = F.k;
   block_copy(A, F.Vh, (long long)k * d * cr);
   for (long long idx = threadIdx.x; idx < (long long)cl * k; idx += blockDim.x)
@@ -1016,7 +1050,10 @@ __device__ void move_center(Smem& s, const Ctx& C, int target) {
 // (X^a Z^b)_{s s'} = omega^{b s'} delta_{s, s'+a}, so each MPO tensor is a gather with phases.
 // record: this is the circuit's non-Clifford step (span, string and counters are kept); the adjoint
 // passes false.  The identity string (f > l) sets EINVAL.
-__device__ __noinline__ void mpo_apply(Smem& s, const Ctx& C, const uint8_t* row, int r, bool record) {
+// lead: the leader's shared memory when the other CTAs of the cluster serve cluster-Jacobi requests during
+// the step (run_op); null for a leader-only compression
+__device__ __noinline__ void mpo_apply(Smem& s, const Ctx& C, const uint8_t* row, int r, bool record,
+                                       Smem* lead = nullptr) {
   const int n = C.n, d = C.d;
   // support span and sum_j x_j z_j
   if (threadIdx.x == 0) {
@@ -1119,7 +1156,7 @@ __device__ __noinline__ void mpo_apply(Smem& s, const Ctx& C, const uint8_t* row
     for (int j = f; j < l; ++j) move_right(s, C, j);
     double disc = 0;
     for (int j = l; j > f; --j) {
-      disc += move_left(s, C, j, C.e->chi_max, true);
+      disc += move_left(s, C, j, C.e->chi_max, true, lead);
       note_chi(C, C.dims[j]);
     }
     if (threadIdx.x == 0) {
@@ -1173,7 +1210,7 @@ __device__ void take_snapshot(Smem& s, const Ctx& C, int site, const double* pha
 // Diagonal non-Clifford gate diag(e^{i phases[j]}) on `site`: P = C^dag Z_site C is row `site` of the
 // inverse tableau; diag(t) = sum_m c_m Z^m with c_m = (1/d) sum_j t_j omega^{-mj}; C^dag diag(t) C =
 // sum_m c_m P^m goes through mpo_apply.
-__device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double* phases) {
+__device__ void apply_nonclifford(Smem& s, Smem* lead, const Ctx& C, int site, const double* phases) {
   const int n = C.n, d = C.d;
   if (threadIdx.x == 0)
     for (int m = 0; m < d; ++m) {
@@ -1187,7 +1224,7 @@ __device__ void apply_nonclifford(Smem& s, const Ctx& C, int site, const double*
       s.coef[m] = make_double2(re / d, im / d);
     }
   __syncthreads();
-  mpo_apply(s, C, C.ix + (long long)site * 2 * n, C.ir[site], true);
+  mpo_apply(s, C, C.ix + (long long)site * 2 * n, C.ir[site], true, lead);
   if (C.e->snap && C.meta[M_STATUS] == 0) take_snapshot(s, C, site, phases);
 }
 
@@ -3069,7 +3106,23 @@ __device__ void run_op(Smem& s, Smem* lead, const Ctx& C, const gcamps_op& op) {
       prof_lap(C, P_CLIFF, tp);
       break;
     case GCAMPS_OP_NONCLIFFORD:
-      if (C.rank == 0 && C.meta[M_STATUS] == 0) apply_nonclifford(s, C, op.q0, op.phases);
+      // the leader applies the MPO; its compression SVDs with many Jacobi columns rotate on the whole
+      // cluster: the other CTAs serve its requests until it releases them, on every path, with jmode 0 at
+      // one last barrier (each request is one barrier plus jacobi_cluster's, the same on every CTA)
+      if (C.rank == 0) {
+        if (C.meta[M_STATUS] == 0) apply_nonclifford(s, C.csize > 1 ? lead : nullptr, C, op.q0, op.phases);
+        if (C.csize > 1) {
+          if (threadIdx.x == 0) s.jmode = 0;
+          __syncthreads();
+          cluster_sync();
+        }
+      } else {
+        for (;;) {
+          cluster_sync();
+          if (lead->jmode != 2) break;
+          jacobi_cluster(lead, C, C.scr + C.e->sl.b, lead->jm, lead->jn, C.scr + C.e->sl.w, C.e->jacobi_cap);
+        }
+      }
       prof_lap(C, P_MPO, tp);
       break;
     case GCAMPS_OP_DISENTANGLE:
