@@ -172,3 +172,14 @@ def test_noalloc_size_check_cannot_wrap(lib):
     for d, cl, cr in [(3, 715827883, 1), (3, 1, 715827883), (2, 1073741825, 1), (3, 28, 1), (2, 1, 41)]:
         rc = lib.gcamps_score_theta_noalloc(d, cl, cr, fake, fake, fake, fake, 1e-10, None)
         assert rc == N.ESIZE, (d, cl, cr, rc)
+
+
+def test_handle_setters_reject_a_null_handle(lib):
+    """The launch-shape and iteration-cap setters refuse a null handle before any CUDA call."""
+    from paper_2511_06672_gb300 import _native as N
+    assert lib.gcamps_set_exact_cta(None, 10) == N.EINVAL
+    assert lib.gcamps_set_exact_cta(None, -1) == N.EINVAL
+    assert lib.gcamps_set_jacobi_cap(None, 60) == N.EINVAL
+    assert lib.gcamps_set_cluster_size(None, 12) == N.EINVAL
+    cnt = C.c_int32(-7)
+    assert lib.gcamps_get_profile(None, 0, None, 0, C.byref(cnt)) == N.EINVAL
