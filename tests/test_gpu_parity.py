@@ -572,3 +572,45 @@ def test_layer_by_layer_runs_match_oracle(G, d, n, layers):
     err, _ = sv.same_up_to_phase(sim.statevector(), sv.run(gates, n, d))
     assert err < TOL
     sim.close()
+
+
+def _spectrum_theta(kind, d, cl, cr, seed):
+    """theta whose matrix (chi_l d x d chi_r) has a planted Schmidt spectrum, between random isometries:
+    'flat' rank 3 with equal weights (a 3-fold degenerate eigenvalue and zeros), 'decay' weights 2^-k
+    down to 2^-(m-1) (many small eigenvalues inside one FP32 bracket), 'pairs' eigenvalues in pairs
+    split by one part in 1e9, 'zeros' rank 2 (the rest of the Gram's eigenvalues are rounding noise)."""
+    rng = np.random.default_rng(seed)
+    rows, cols = cl * d, d * cr
+    m = min(rows, cols)
+    if kind == "flat":
+        w = np.zeros(m)
+        w[:3] = 1.0
+    elif kind == "decay":
+        w = 2.0 ** -np.arange(m)
+    elif kind == "pairs":
+        base = 1.5 ** -np.arange((m + 1) // 2)
+        w = np.repeat(base, 2)[:m] * np.tile([1.0, 1.0 + 1e-9], (m + 1) // 2)[:m]
+    else:
+        w = np.zeros(m)
+        w[:2] = [0.7, 0.3]
+    qa, _ = np.linalg.qr(rng.standard_normal((rows, m)) + 1j * rng.standard_normal((rows, m)))
+    qb, _ = np.linalg.qr(rng.standard_normal((cols, m)) + 1j * rng.standard_normal((cols, m)))
+    M = (qa * np.sqrt(w / w.sum())) @ qb.conj().T
+    return M.reshape(cl, d, d, cr)
+
+
+@pytest.mark.parametrize("kind", ["flat", "decay", "pairs", "zeros"])
+@pytest.mark.parametrize("cl,cr", [(3, 3), (9, 9), (27, 27)])
+def test_score_theta_spectra_that_stress_the_eigenvalue_refinement(G, kind, cl, cr):
+    """Every class's von Neumann entropy for thetas whose spectra exercise the FP64 refinement of the
+    FP32 eigenvalue brackets (Newton steps kept only where Sturm counts verify them, multisection
+    otherwise) at warp-level (m = 9), CTA-level short-list (m = 27) and CTA-level (m = 81) sizes, against
+    the oracle's SVD entropies at 1e-10; the chosen class is the oracle's."""
+    d = 3
+    theta = _spectrum_theta(kind, d, cl, cr, 100 + cl + cr)
+    ref = GCAMPS(8, d, chi_max=81)
+    want = ref.score_bond(theta)
+    sim = G.Simulator(8, d, chi_max=81)
+    s2, vn, choice, nev = sim.score_theta(theta)
+    assert np.max(np.abs(vn - want)) < TOL, (kind, cl, float(np.max(np.abs(vn - want))))
+    assert choice == ref.choose(want)
