@@ -183,3 +183,20 @@ def test_handle_setters_reject_a_null_handle(lib):
     assert lib.gcamps_set_cluster_size(None, 12) == N.EINVAL
     cnt = C.c_int32(-7)
     assert lib.gcamps_get_profile(None, 0, None, 0, C.byref(cnt)) == N.EINVAL
+
+
+def test_create_accepts_every_cluster_size_up_to_16(lib):
+    """Cluster sizes 1..16 (not only powers of two) pass the host's option check; 0 means the default.
+    Without a GPU the call then fails at its first CUDA call, never with EINVAL."""
+    import torch
+    from paper_2511_06672_gb300 import _native as N
+    if torch.cuda.is_available():
+        pytest.skip("checks the host-side path only")
+    for cs in (0, 1, 3, 12, 14, 16):
+        o = N.Opts()
+        lib.gcamps_default_opts(C.byref(o))
+        o.cluster_size = cs
+        h = C.c_void_p()
+        rc = lib.gcamps_create(4, 3, 8, C.byref(o), C.byref(h))
+        assert rc not in (N.OK, N.EINVAL), (cs, rc)
+        assert not h.value
